@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Throughput of the batched Nested Slice Sampling sweep on GB300.
+
+Metric: NS dead points per second (all deaths, including the final live
+set) and logical likelihood evaluations per second.  One step is one whole
+pass of the hot path -- initial prior draw, every outer iteration (selection,
+evidence, metric, parents, HRSS sweep with the likelihood fused in,
+replacement, termination test) and the post-hoc volume simulation -- over one
+batch of independent runs of the workload:
+
+  gmm_d32: d = 32, uniform prior on [0,1]^32, equal-weight mixture of 4
+  isotropic Gaussians (sigma 0.02, means uniform in [0.2,0.8]^32 drawn from
+  the seed), n_live = 1000, k = 500, p = 3d = 96; 20 seeds per batch.
+
+`value` is measured with the inputs resident on the device (context created
+before the timed region); `e2e` goes through the public API from host
+buffers: create (problem upload), run, dead-point read-back, destroy.
+Multi-GPU: independent replicas (one batch of different seeds per rank), no
+data-path collective.  `--impl reference` times the FP64 CPU checker of the
+same workload on the host cores (the slow reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NS dead points/s and logL evals/s vs plain path at |\u0394logZ|\u22640.1 nat, % roofline"
+UNIT = "dead points/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--runs", type=int, default=20, help="independent seeds per batch (per rank)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-run-at-a-time comparator")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU checker baseline")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="no timing: the bench batch for a few iterations, small dead stores "
+                         "(the case captured by ncu)")
+    return ap.parse_args()
+
+
+def gmm_logZ(mu, sigma):
+    """Closed-form evidence of the equal-weight mixture under the [0,1]^d box."""
+    from scipy import special
+    lo = special.log_ndtr((0.0 - mu) / sigma)
+    hi = special.log_ndtr((1.0 - mu) / sigma)
+    per = np.sum(hi + np.log1p(-np.exp(lo - hi)), axis=1)
+    return float(special.logsumexp(per) - np.log(len(per)))
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2601_23252_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_sweep_gmm_d32.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def sweep_flops(wl, evals, chain_steps):
+    """Algorithmic FP32 operations of the sweep: per logical evaluation the
+    line point (2d) and K squared distances (3Kd) plus the K scalings and
+    log-sum-exp adds (2K); per HRSS step the whitening L z (d(d+1)) and the
+    norms and scaling (4d)."""
+    d, K = wl.d, (wl.mu.shape[0] if wl.mu is not None else 1)
+    return evals * (2 * d + 3 * K * d + 2 * K) + chain_steps * (d * (d + 1) + 4 * d)
+
+
+def cpu_checker_rate(budget_s=12.0, seed=0):
+    """The FP64 checker on one seed of the workload, from the start, for about
+    budget_s seconds of iterations: dead points per second on one core."""
+    import oracle as O
+    from paper_2601_23252_gb300 import workloads as W
+    wl = W.gmm_d32(seed=seed)
+    pb = O.Problem((wl.prior, wl.a, wl.b), wl.lik, **wl.oracle_kwargs())
+    op = O.make_opts(wl.n_live, wl.k, wl.p, seed=wl.seed)
+    t0 = time.perf_counter()
+    x, l, b = O.init_live(pb, op)
+    st, it, ev = (x, l, b, -np.inf, 0.0), 0, 0
+    while time.perf_counter() - t0 < budget_s:
+        st, tr = O.step(pb, op, it, *st)
+        ev += int(tr["evals"].sum())
+        it += 1
+    dt = time.perf_counter() - t0
+    return {"value": wl.k * it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"gmm_d32 seed {seed}: prior draw + first {it} iterations ({wl.k * it} dead points, "
+                      f"{ev} evals) in {dt:.1f} s, one thread", "evals_per_s": ev / dt}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_checker_rate(budget_s=1.0, seed=99)
+    rates, evr, samples = [], [], []
+    for s in range(args.steps):
+        r = cpu_checker_rate(budget_s=8.0, seed=s)
+        rates.append(r["value"])
+        evr.append(r["evals_per_s"])
+        samples.append(r["sample"])
+    v = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 8000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "gmm_d32 (d=32, 4-component mixture, m=1000, "
+                                            "k=500, p=96)", "sample_per_step": "8 s of checker iterations"},
+            "evals_per_s": float(np.mean(evr)),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": samples[0]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_native(args):
+    import torch
+    from paper_2601_23252_gb300 import native
+    from paper_2601_23252_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    nrun = args.runs
+    seeds = [rank * nrun + s for s in range(nrun)]
+    wls = [W.gmm_d32(seed=s) for s in seeds]
+    truth = np.array([gmm_logZ(w.mu, w.sigma) for w in wls])
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    sampler = native.Sampler(wls, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        sampler.reset()
+        sampler.run()
+    torch.cuda.synchronize()
+    sampler.set_profiling(True)
+    clocks = Clocks(local)
+    times, dead, evals, flops, launches = [], 0, 0, 0.0, 0
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    res = None
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))          # L2 flush between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sampler.reset()
+        res = sampler.run()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        for wl, r in zip(wls, res):
+            dead += r["n_dead"]
+            evals += r["evals"]
+            flops += sweep_flops(wl, r["evals"], r["iters"] * wl.k * wl.p)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof = sampler.profile()
+    total_ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms, dead, evals], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        total_ms_all, dead_all, evals_all = float(mx[0]), float(sm[1]), float(sm[2])
+    else:
+        total_ms_all, dead_all, evals_all = total_ms, float(dead), float(evals)
+    value = dead_all / (total_ms_all / 1e3)
+    dlogZ = np.array([r["logZ"] for r in res]) - truth
+    errs = np.array([r["logZ_err"] for r in res])
+
+    # dominant kernel: the sweep
+    sweep_ms = prof["ms"]["sweep"]
+    sweep_launches = max(1, prof["launches"]["sweep"])
+    peaks, src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp32_peak) if achieved else None, "traffic": ncu_traffic(),
+                "kernel": "k_sweep<8> (HRSS sweep, fused mixture likelihood)",
+                "peak_source": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x "
+                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src} max clock)",
+                "avg_launch_ms": sweep_ms / sweep_launches,
+                "share_of_step": sweep_ms / total_ms if total_ms > 0 else None}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "gmm_d32", "d": 32, "n_comp": 4, "sigma": 0.02, "n_live": 1000,
+                       "k": 500, "p": 96, "runs_per_gpu": nrun, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "evidence_accumulation": "f64"},
+            "evals_per_s": evals_all / (total_ms_all / 1e3),
+            "gate": {"mean_dlogZ": float(dlogZ.mean()), "max_abs_dlogZ_over_err": float(np.max(np.abs(dlogZ) / errs)),
+                     "mean_err": float(errs.mean()), "pass": bool(abs(dlogZ.mean()) <= 0.1)},
+            "roofline": roofline, "gpu_launches": prof["total_launches"] // 1,
+            "clocks": clk,
+            "kernel_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items() if v > 0}}
+    sampler.close()
+
+    # end to end through the public API from host buffers
+    if rank == 0 or world > 1:
+        e2e_t, e2e_dead, h2d, d2h = [], 0, 0, 0
+        for s in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with native.Sampler(wls, stream=stream.cuda_stream) as sm:
+                rr = sm.run()
+                for r in range(nrun):
+                    n = rr[r]["n_dead"]
+                    out = {"x": torch.empty((n, 32), dtype=torch.float32).pin_memory(),
+                           "logL": torch.empty(n, dtype=torch.float32).pin_memory(),
+                           "log_w": torch.empty(n, dtype=torch.float64).pin_memory()}
+                    sm.dead(r, out=out)
+                p = sm.profile()
+                h2d, d2h = p["h2d_bytes"], p["d2h_bytes"]
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+            e2e_dead = sum(r["n_dead"] for r in rr)
+        line["e2e"] = {"value": e2e_dead / float(np.mean(e2e_t)), "unit": UNIT,
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": 1e3 * float(np.mean(e2e_t))}
+
+    # plain comparator: the same runs one at a time (single-run contexts)
+    if rank == 0 and world == 1 and not args.no_plain:
+        t_plain, dead_plain = 0.0, 0
+        for wl in wls[:4]:
+            with native.Sampler(wl, stream=stream.cuda_stream) as sp:
+                sp.run()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                sp.reset()
+                e0.record(stream)
+                r = sp.run()[0]
+                e1.record(stream)
+                e1.synchronize()
+                t_plain += e0.elapsed_time(e1)
+                dead_plain += r["n_dead"]
+        line["single_run_path"] = {"value": dead_plain / (t_plain / 1e3), "unit": UNIT,
+                                   "what": "the same kernels, one run per context, 4 seeds one after another"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_checker_rate()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_ncu_case(args):
+    """The bench's batch of runs for 6 outer iterations, then exit; dead
+    stores sized for those iterations so the device footprint stays small."""
+    from paper_2601_23252_gb300 import native
+    from paper_2601_23252_gb300 import workloads as W
+    wls = [W.gmm_d32(seed=s).with_(extra={"options": {"dead_capacity": 8 * 500 + 1000}})
+           for s in range(args.runs)]
+    with native.Sampler(wls) as s:
+        for _ in range(6):
+            s.step()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.ncu_case:
+        return run_ncu_case(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,270 @@
+/*
+ * nss.h -- C ABI of the GB300 (sm_103a) Nested Slice Sampling library
+ * (libnss_gb300.so).
+ *
+ * The library implements the batched constrained-update sweep of Nested
+ * Slice Sampling (Yallup, Kroupa & Handley, arxiv 2601.23252):
+ *   (i)   delete the k lowest-likelihood live points, threshold logL* = the
+ *         largest of them                              (Sec. 3.1 (i); Alg. 1)
+ *   (ii)  resample k parents uniformly from the m-k survivors (Sec. 3.1 (ii))
+ *   (iii) whiten directions with the Cholesky factor of the regularised
+ *         live-set covariance                          (Sec. 3.2 "Direction metric")
+ *         and run k Hit-and-Run Slice Sampling chains of p steps each, with
+ *         stepping-out (<= 10 per side) and shrinkage (<= 100, then a null
+ *         move), the likelihood evaluated inside the sweep (Sec. 3.2; App. B.4)
+ *   (iv)  replace the dead slots                       (Sec. 3.1 (iv))
+ * plus the unrolled evidence bookkeeping (Eq. eq:marginal, Eq. eq:dlnX,
+ * App. D.1) and the post-hoc volume-shrinkage simulation, posterior weights
+ * and evidence error (App. D.2).
+ *
+ * Conventions
+ *   - log-likelihood throughout (the paper's energy is E = -log L); the
+ *     constraint E < E_batch reads logL > logL* (strict).
+ *   - Positions, likelihoods and slice arithmetic are FP32; the evidence,
+ *     log prior volume and volume simulation accumulate in FP64.
+ *   - Random numbers: Philox4x32-10 keyed by (seed_lo32, seed_hi32 ^ run_id);
+ *     counter (iteration, chain, step, word/4) for the HRSS draws, with the
+ *     word layout of each step: [0, 2*ceil(d/2)) Box-Muller pairs, then the
+ *     bracket position U, the prior slice height, one reserved word, and the
+ *     shrinkage proposals r = 0..99.  Uniforms u = (2*(w>>9)+1) * 2^-24.
+ *
+ * Ownership: the library allocates and owns all device state of a context.
+ * Input arrays (prior bounds, likelihood parameters and data) are read from
+ * host memory and copied during nss_create*; the caller may free them after
+ * the call returns.  Output arrays are caller-owned and may be host or
+ * device pointers (unified addressing decides the copy direction).
+ *
+ * Errors: every entry point returns an nss_status; nothing aborts, throws or
+ * resets device state.  A CUDA error is reported as NSS_ERR_CUDA and leaves
+ * the context unusable except for nss_destroy; nss_last_error() gives text.
+ * No device code waits on another block, so no kernel can hang.
+ *
+ * Threading and streams: a context is used by one host thread at a time.
+ * All device work of a context is enqueued on the stream given in
+ * nss_options.cuda_stream (NULL = the legacy default stream).
+ */
+#ifndef NSS_GB300_H
+#define NSS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NSS_ABI_VERSION 1
+
+typedef struct nss_ctx nss_ctx;
+
+typedef enum {
+    NSS_OK = 0,
+    NSS_DONE = 1,            /* the termination test holds for every run     */
+    NSS_ERR_ARG = -1,        /* invalid argument; nothing was done           */
+    NSS_ERR_CUDA = -2,       /* CUDA runtime error (text in nss_last_error)  */
+    NSS_ERR_OOM = -3,        /* device allocation failed                      */
+    NSS_ERR_CAPACITY = -4,   /* the dead-point store of a run is full         */
+    NSS_ERR_TIMEOUT = -5,    /* max_iter reached before termination           */
+    NSS_ERR_NUMERIC = -6,    /* non-finite evidence                            */
+    NSS_ERR_STATE = -7       /* call out of order (e.g. trace before a step)  */
+} nss_status;
+
+/* Prior Pi (Eq. eq:target).  Box: uniform on [a_i, b_i]; Gaussian: independent
+   N(a_i, b_i^2).  a and b are host arrays of length d. */
+enum { NSS_PRIOR_UNIFORM_BOX = 0, NSS_PRIOR_GAUSS_DIAG = 1 };
+typedef struct {
+    int kind;
+    int d;
+    const double *a;
+    const double *b;
+} nss_prior;
+
+/* Likelihood L = exp(-E) (Eq. eq:target).  Kinds and their fields:
+ *   GAUSS_ISO       normalised N(x; mu, sigma^2 I); mu [d]
+ *   GMM_ISO_EQUAL   (1/n_comp) sum_c N(x; mu_c, sigma^2 I); mu [n_comp][d]
+ *   LOGREG          sum_n [y_n z_n - softplus(z_n)], z = X x; X [n_data][d]
+ *                   row-major FP32 (values are used as given, rounded to
+ *                   bfloat16 on the device: pass bf16-exact data), y [n_data]
+ *   GP_RBF_WHITE    theta = (ln lengthscale, ln amplitude, ln noise); GP
+ *                   marginal likelihood of gp_y [n_data] at gp_t [n_data]
+ *   FLAT            logL = 0 (pure prior / plateau tests)
+ *   TEST_FAULT      isotropic Gaussian whose value is replaced by NaN
+ *                   (fault_mode 1) or +inf (fault_mode 2) where x_0 <
+ *                   fault_param; NaN is read as -inf and counted.
+ * All pointers are host pointers, copied at create. */
+enum {
+    NSS_LOGLIK_GAUSS_ISO = 0,
+    NSS_LOGLIK_GMM_ISO_EQUAL = 1,
+    NSS_LOGLIK_LOGREG = 2,
+    NSS_LOGLIK_GP_RBF_WHITE = 3,
+    NSS_LOGLIK_FLAT = 4,
+    NSS_LOGLIK_TEST_FAULT = 5
+};
+typedef struct {
+    int kind;
+    int n_comp;
+    int n_data;
+    double sigma;
+    const double *mu;
+    const float *X;
+    const float *y;
+    const double *gp_t;
+    const double *gp_y;
+    int fault_mode;
+    double fault_param;
+} nss_loglik;
+
+/* Direction normalisation: MAHAL v = L z / |z| (unit Mahalanobis length, the
+   slice width then acts in whitened units, App. B.3); EUCLID v = L z / |L z|
+   (the literal form of Sec. 3.2). */
+enum { NSS_DIR_MAHAL = 0, NSS_DIR_EUCLID = 1 };
+/* Slice-width rule: FIXED uses w as given (the paper's experiments use
+   w = 1.0, App. B.3); THEORY uses w = kappa_inf * E[l_d] for the uniform
+   whitened ball of radius sqrt(d+2) (Theorem "optimal slice width in an
+   ellipsoid"; Sec. 3.3 "Isotropic level sets"). */
+enum { NSS_W_FIXED = 0, NSS_W_THEORY = 1 };
+
+typedef struct {
+    uint64_t seed;
+    uint32_t run_id;
+    double w;                  /* slice width (NSS_W_FIXED)                      */
+    int w_rule;                /* NSS_W_FIXED or NSS_W_THEORY                    */
+    int dir_norm;              /* NSS_DIR_MAHAL or NSS_DIR_EUCLID                */
+    double tol;                /* stop when Z_live/(Z+Z_live) < tol (App. B.3)   */
+    int max_iter;              /* iteration cap; reaching it ends the run        */
+    long long dead_capacity;   /* dead points per run; 0 = 2000*k + m           */
+    int n_sim;                 /* volume-simulation trajectories R (App. D.2)    */
+    double cov_eps;            /* metric regularisation eps * tr(Sigma)/d        */
+    void *cuda_stream;         /* cudaStream_t; NULL = default stream            */
+} nss_options;
+
+/* Fills the paper's defaults: w = 1, MAHAL, tol = 1e-3, max_iter = 100000,
+   n_sim = 100, cov_eps = 1e-6, seed 0, run_id 0, default stream. */
+void nss_options_default(nss_options *opt);
+
+/* Per-run state after a step. */
+typedef struct {
+    int iter;                  /* iterations completed                           */
+    int done;                  /* termination test held                          */
+    float logLstar;            /* threshold of the last iteration                */
+    double logZ;               /* running Delta-X evidence (deterministic X)     */
+    double logX;               /* deterministic log prior volume, -sum 1/n       */
+    long long n_dead;
+    long long evals;           /* logical likelihood evaluations so far          */
+    long long nulls;           /* HRSS steps that hit the shrinkage cap          */
+    long long cap_out;         /* stepping-out sides stopped by the cap          */
+    long long nan_evals;       /* evaluations whose likelihood was NaN           */
+    int metric_status;         /* 0 ok, 1 identity fallback, 2 jitter retried    */
+    int status;                /* nss_status of the run                          */
+} nss_step_info;
+
+/* Result of a finished run (App. D.2): logZ = mean over the R simulated
+   volume trajectories, logZ_err = their standard deviation (ddof 1),
+   logZ_det = the running Delta-X estimate with deterministic volumes. */
+typedef struct {
+    double logZ;
+    double logZ_err;
+    double logZ_det;
+    long long n_dead;
+    int iters;
+    long long evals;
+    long long nulls;
+    long long cap_out;
+    long long nan_evals;
+    int status;
+} nss_result;
+
+/* State of one run for export/import (checkpoint/resume and parity tests). */
+typedef struct {
+    int iter;
+    double logZ;
+    double logX;
+    long long n_dead;
+} nss_state;
+
+/* Per-chain record of the last iteration of one run; host pointers of
+   length k (L: d*d, row-major lower triangle, zeros above). */
+typedef struct {
+    int *dead_idx;       /* slots deleted, worst first                  */
+    int *parent;         /* parent slot of each chain                    */
+    float *L;            /* Cholesky factor of the metric                */
+    int *evals, *accepts, *nulls, *expansions, *shrinks, *cap_out;
+    float *new_x;        /* [k][d] final chain positions                 */
+    float *new_logL;     /* [k]                                          */
+    float logLstar;
+} nss_trace;
+
+/* Per-kernel timing collected while profiling is on (CUDA events on the
+   context's stream around every launch of that kernel). */
+typedef struct {
+    long long launches[8];
+    double ms[8];          /* summed event time                           */
+    long long total_launches;
+    long long h2d_bytes;   /* host-to-device bytes copied by the library   */
+    long long d2h_bytes;   /* device-to-host bytes copied by the library   */
+} nss_profile;
+enum { NSS_K_INIT = 0, NSS_K_PROLOGUE = 1, NSS_K_SWEEP = 2, NSS_K_TERMINATE = 3,
+       NSS_K_FINAL_SORT = 4, NSS_K_VOLSIM = 5, NSS_K_WEIGHTS = 6, NSS_K_OTHER = 7 };
+
+/* Create a single-run context: copies the problem to the device and draws
+   the m initial live points from the prior (Sec. 2.1).  n_live = m >= 2,
+   1 <= k < m, p >= 1, 1 <= d <= 128. */
+nss_status nss_create(const nss_prior *prior, const nss_loglik *loglik, int n_live, int k, int p,
+                      const nss_options *opt, nss_ctx **out);
+
+/* Create a context of n_runs independent runs advanced together (one launch
+   per kernel for all runs).  prior, loglik, n_live, k, p and opt are arrays of
+   length n_runs; the stream of opt[0] is used for all runs. */
+nss_status nss_create_batch(int n_runs, const nss_prior *prior, const nss_loglik *loglik,
+                            const int *n_live, const int *k, const int *p,
+                            const nss_options *opt, nss_ctx **out);
+
+/* One outer iteration (i)-(iv) for every run that has not terminated, then
+   the termination test.  info: array of n_runs entries or NULL.  Returns
+   NSS_DONE when every run has terminated. */
+nss_status nss_step(nss_ctx *ctx, nss_step_info *info);
+
+/* Iterate until every run terminates (or hits max_iter), kill the final
+   live points (n = m, ..., 1), run the volume simulation and weights.
+   res: array of n_runs entries or NULL. */
+nss_status nss_run(nss_ctx *ctx, nss_result *res);
+
+/* Start every run of the context again from a fresh prior draw (same
+   problem, same sizes, no reallocation).  seeds: n_runs new seeds, or NULL to
+   keep the current ones.  Counters and the dead-point store are cleared. */
+nss_status nss_reset(nss_ctx *ctx, const uint64_t *seeds);
+
+/* Finalise runs that were stepped to termination with nss_step. */
+nss_status nss_finalise(nss_ctx *ctx, nss_result *res);
+
+/* Dead points of run `run` in death order.  Any output pointer may be NULL;
+   x is [n][d], log_w are normalised log posterior weights (valid after
+   nss_run/nss_finalise), nlive the live count at each death.  cap = 0 only
+   reports the count in *n_out. */
+nss_status nss_get_dead(nss_ctx *ctx, int run, float *x, float *logL, double *log_w, float *birth,
+                        int *nlive, size_t cap, size_t *n_out);
+
+/* Live set of a run: x [m][d], logL [m], birth [m] (any may be NULL). */
+nss_status nss_export_state(nss_ctx *ctx, int run, float *x, float *logL, float *birth,
+                            nss_state *st);
+nss_status nss_import_state(nss_ctx *ctx, int run, const float *x, const float *logL,
+                            const float *birth, const nss_state *st);
+
+/* Per-chain record of the last nss_step of run `run`. */
+nss_status nss_step_trace(nss_ctx *ctx, int run, nss_trace *tr);
+
+nss_status nss_set_profiling(nss_ctx *ctx, int on);
+nss_status nss_get_profile(nss_ctx *ctx, nss_profile *prof);
+
+int nss_n_runs(const nss_ctx *ctx);
+/* Slice width actually used by a run (after the width rule). */
+double nss_run_width(const nss_ctx *ctx, int run);
+void nss_destroy(nss_ctx *ctx);
+const char *nss_status_string(nss_status s);
+const char *nss_last_error(const nss_ctx *ctx);
+int nss_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSS_GB300_H */

@@ -1,0 +1,908 @@
+// nss_api.cu -- the C ABI of include/nss.h: context creation, the host loop of
+// outer iterations, finalisation, state import/export and traces.
+//
+// The host never touches sampler arithmetic: it validates arguments, lays out
+// the per-run pools, uploads the problem, enqueues kernels on the context's
+// stream and copies results out.  The only host-side numerics are constants
+// of the problem (likelihood normalisations, the unrolled live-count tables
+// of App. D.1 and the slice-width rule of App. E), computed once at create.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nss.h"
+#include "nss_internal.h"
+#include "nss_kernels.h"
+
+using nss::RunDesc;
+using nss::RunState;
+using nss::WorkItem;
+
+struct EvRec {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+struct nss_ctx {
+  int n_runs = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 1;
+  std::vector<RunDesc> desc;
+  std::vector<double> widths;
+  std::vector<uint32_t> run_ids;
+  RunDesc* d_desc = nullptr;
+  RunState* d_state = nullptr;
+  RunState* h_state = nullptr;  // pinned mirror
+  float* fpool = nullptr;
+  int* ipool = nullptr;
+  double* dpool = nullptr;
+  long long nf = 0, ni = 0, nd = 0;
+  std::vector<WorkItem> init_items[nss::kNumClasses], sweep_items[nss::kNumClasses];
+  WorkItem* d_init[nss::kNumClasses] = {};
+  WorkItem* d_sweep[nss::kNumClasses] = {};
+  int* d_queue = nullptr;
+  int sweep_grid[nss::kNumClasses] = {};
+  size_t prologue_smem = 0, final_smem = 0;
+  // volume simulation scratch
+  int R = 100;
+  int vol_cap_tiles = 0;
+  double* d_vol = nullptr;
+  int2* d_tiles = nullptr;
+  int* d_vbase = nullptr;
+  // profiling
+  bool profiling = false;
+  std::vector<EvRec> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  nss_profile prof{};
+  long long launches = 0;
+  bool broken = false;
+  std::string err;
+};
+
+namespace {
+
+long long align16(long long n) { return (n + 15) & ~15LL; }
+
+nss_status set_err(nss_ctx* c, nss_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+nss_status cuda_fail(nss_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->broken = true;
+  return set_err(c, e == cudaErrorMemoryAllocation ? NSS_ERR_OOM : NSS_ERR_CUDA, "%s: %s", where,
+                 cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+nss::Dev dev_of(nss_ctx* c) {
+  nss::Dev D;
+  D.desc = c->d_desc;
+  D.st = c->d_state;
+  D.f = c->fpool;
+  D.i = c->ipool;
+  D.dd = c->dpool;
+  return D;
+}
+
+int class_of(int d) {
+  if (d <= 4) return 0;
+  if (d <= 8) return 1;
+  if (d <= 16) return 2;
+  if (d <= 32) return 3;
+  if (d <= 64) return 4;
+  return 5;
+}
+
+// ---- slice-width rule helpers (App. E), host FP64 -------------------------
+// Gauss-Legendre nodes on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-15) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// integral of f over [a, b] by `panels` panels of an n-point rule
+template <class F>
+double integrate(F f, double a, double b, int panels, const std::vector<double>& gx,
+                 const std::vector<double>& gw) {
+  double s = 0.0, h = (b - a) / panels;
+  for (int p = 0; p < panels; ++p) {
+    const double c = a + (p + 0.5) * h;
+    for (size_t i = 0; i < gx.size(); ++i) s += gw[i] * f(c + 0.5 * h * gx[i]);
+  }
+  return s * 0.5 * h;
+}
+
+// kappa_inf = 1/2 + E[R ln(1 + kappa/R)], R = q / E[q], q ~ chi_3 (the
+// square root of the Gamma(3/2, 2) variable of the ellipsoid theorem).
+double kappa_inf_host() {
+  std::vector<double> gx, gw;
+  gauss_legendre(20, gx, gw);
+  const double c = 2.0 * std::sqrt(2.0 / M_PI);
+  auto dens = [](double q) { return std::sqrt(2.0 / M_PI) * q * q * std::exp(-0.5 * q * q); };
+  double k = 1.0;
+  for (int it = 0; it < 500; ++it) {
+    auto f = [&](double q) { return q <= 0 ? 0.0 : (q / c) * std::log1p(k * c / q) * dens(q); };
+    const double nk = 0.5 + integrate(f, 0.0, 14.0, 200, gx, gw);
+    if (std::fabs(nk - k) < 1e-14) return nk;
+    k = nk;
+  }
+  return k;
+}
+
+// mean chord of a uniform point in a d-ball of radius Rb along a uniform
+// direction, with rho = (r/Rb)^d uniform and theta weighted by sin^(d-2).
+double mean_chord_host(int d, double Rb) {
+  if (d == 1) return 2.0 * Rb;
+  std::vector<double> gx, gw;
+  gauss_legendre(16, gx, gw);
+  auto wt = [&](double th) { return d == 2 ? 1.0 : std::pow(std::sin(th), d - 2); };
+  const double norm = integrate(wt, 0.0, M_PI, 200, gx, gw);
+  auto inner = [&](double th) {
+    const double s2 = std::sin(th) * std::sin(th);
+    auto g = [&](double rho) {
+      const double v = 1.0 - std::pow(rho, 2.0 / d) * s2;
+      return 2.0 * Rb * std::sqrt(v > 0 ? v : 0.0);
+    };
+    return wt(th) * integrate(g, 0.0, 1.0, 100, gx, gw);
+  };
+  return integrate(inner, 0.0, M_PI, 200, gx, gw) / norm;
+}
+
+nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m, int k, int p,
+                    const nss_options& o, int run) {
+  if (pr.d < 1 || pr.d > nss::kMaxD) return set_err(c, NSS_ERR_ARG, "run %d: d=%d outside [1,%d]", run, pr.d, nss::kMaxD);
+  if (m < 2 || m > nss::kMaxLive) return set_err(c, NSS_ERR_ARG, "run %d: n_live=%d outside [2,%d]", run, m, nss::kMaxLive);
+  if (k < 1 || k >= m) return set_err(c, NSS_ERR_ARG, "run %d: k=%d outside [1,n_live)", run, k);
+  if (p < 1) return set_err(c, NSS_ERR_ARG, "run %d: p=%d < 1", run, p);
+  if (!pr.a || !pr.b) return set_err(c, NSS_ERR_ARG, "run %d: prior bounds missing", run);
+  if (pr.kind != NSS_PRIOR_UNIFORM_BOX && pr.kind != NSS_PRIOR_GAUSS_DIAG)
+    return set_err(c, NSS_ERR_ARG, "run %d: unknown prior kind %d", run, pr.kind);
+  for (int i = 0; i < pr.d; ++i) {
+    if (!std::isfinite(pr.a[i]) || !std::isfinite(pr.b[i]))
+      return set_err(c, NSS_ERR_ARG, "run %d: non-finite prior bound", run);
+    if (pr.kind == NSS_PRIOR_UNIFORM_BOX && !(pr.a[i] < pr.b[i]))
+      return set_err(c, NSS_ERR_ARG, "run %d: empty box in dimension %d", run, i);
+    if (pr.kind == NSS_PRIOR_GAUSS_DIAG && !(pr.b[i] > 0))
+      return set_err(c, NSS_ERR_ARG, "run %d: prior sd <= 0 in dimension %d", run, i);
+  }
+  switch (lk.kind) {
+    case NSS_LOGLIK_GAUSS_ISO:
+    case NSS_LOGLIK_TEST_FAULT:
+      if (!lk.mu || !(lk.sigma > 0)) return set_err(c, NSS_ERR_ARG, "run %d: Gaussian needs mu and sigma > 0", run);
+      if (lk.kind == NSS_LOGLIK_TEST_FAULT && lk.fault_mode != 1 && lk.fault_mode != 2)
+        return set_err(c, NSS_ERR_ARG, "run %d: fault_mode must be 1 or 2", run);
+      break;
+    case NSS_LOGLIK_GMM_ISO_EQUAL:
+      if (!lk.mu || !(lk.sigma > 0) || lk.n_comp < 1)
+        return set_err(c, NSS_ERR_ARG, "run %d: mixture needs mu, sigma > 0, n_comp >= 1", run);
+      break;
+    case NSS_LOGLIK_FLAT:
+      break;
+    case NSS_LOGLIK_LOGREG:
+    case NSS_LOGLIK_GP_RBF_WHITE:
+      return set_err(c, NSS_ERR_ARG, "run %d: likelihood kind %d is not built in this library", run, lk.kind);
+    default:
+      return set_err(c, NSS_ERR_ARG, "run %d: unknown likelihood kind %d", run, lk.kind);
+  }
+  if (!(o.tol > 0 && o.tol < 1)) return set_err(c, NSS_ERR_ARG, "run %d: tol outside (0,1)", run);
+  if (o.max_iter < 1) return set_err(c, NSS_ERR_ARG, "run %d: max_iter < 1", run);
+  if (o.w_rule == NSS_W_FIXED && !(o.w > 0)) return set_err(c, NSS_ERR_ARG, "run %d: w <= 0", run);
+  if (o.w_rule != NSS_W_FIXED && o.w_rule != NSS_W_THEORY) return set_err(c, NSS_ERR_ARG, "run %d: unknown w_rule", run);
+  if (o.dir_norm != NSS_DIR_MAHAL && o.dir_norm != NSS_DIR_EUCLID) return set_err(c, NSS_ERR_ARG, "run %d: unknown dir_norm", run);
+  if (o.n_sim < 2 || o.n_sim > 1024) return set_err(c, NSS_ERR_ARG, "run %d: n_sim outside [2,1024]", run);
+  if (!(o.cov_eps >= 0)) return set_err(c, NSS_ERR_ARG, "run %d: cov_eps < 0", run);
+  if (o.dead_capacity < 0) return set_err(c, NSS_ERR_ARG, "run %d: dead_capacity < 0", run);
+  return NSS_OK;
+}
+
+void free_ctx(nss_ctx* c) {
+  if (!c) return;
+  cudaFree(c->d_desc);
+  cudaFree(c->d_state);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  cudaFree(c->fpool);
+  cudaFree(c->ipool);
+  cudaFree(c->dpool);
+  for (int q = 0; q < nss::kNumClasses; ++q) {
+    cudaFree(c->d_init[q]);
+    cudaFree(c->d_sweep[q]);
+  }
+  cudaFree(c->d_queue);
+  cudaFree(c->d_vol);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_vbase);
+  for (auto& e : c->pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+// ---- profiling: an event pair around each launch while enabled -------------
+cudaEvent_t take_event(nss_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Rec {
+  nss_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  Rec(nss_ctx* c_, int k_) : c(c_), kind(k_) {
+    c->launches++;
+    c->prof.total_launches++;
+    c->prof.launches[kind]++;
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~Rec() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({a, b, kind});
+    }
+  }
+};
+
+void harvest(nss_ctx* c) {  // after a stream synchronisation
+  for (auto& e : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) c->prof.ms[e.kind] += ms;
+    c->ev_pool.push_back(e.a);
+    c->ev_pool.push_back(e.b);
+  }
+  c->pending.clear();
+}
+
+nss_status sync_state(nss_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(RunState) * c->n_runs, cudaMemcpyDeviceToHost,
+                     c->stream), "state readback");
+  c->prof.d2h_bytes += (long long)sizeof(RunState) * c->n_runs;
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+  harvest(c);
+  return NSS_OK;
+}
+
+nss_status enqueue_iteration(nss_ctx* c) {
+  nss::Dev D = dev_of(c);
+  {
+    Rec r(c, NSS_K_PROLOGUE);
+    CK(nss::launch_prologue(D, c->n_runs, c->prologue_smem, c->stream), "prologue launch");
+  }
+  for (int q = 0; q < nss::kNumClasses; ++q) {
+    if (c->sweep_items[q].empty()) continue;
+    CK(cudaMemsetAsync(c->d_queue + q, 0, sizeof(int), c->stream), "queue reset");
+    Rec r(c, NSS_K_SWEEP);
+    CK(nss::launch_sweep(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->d_queue + q,
+                         c->sweep_grid[q], c->stream), "sweep launch");
+  }
+  {
+    Rec r(c, NSS_K_TERMINATE);
+    CK(nss::launch_terminate(D, c->n_runs, c->stream), "terminate launch");
+  }
+  return NSS_OK;
+}
+
+void clear_states(nss_ctx* c) {
+  for (int r = 0; r < c->n_runs; ++r) {
+    RunState& s = c->h_state[r];
+    std::memset(&s, 0, sizeof s);
+    s.logZ = -INFINITY;
+    s.logX = 0.0;
+    s.logLstar = -INFINITY;
+  }
+}
+
+nss_status launch_inits(nss_ctx* c) {
+  nss::Dev D = dev_of(c);
+  for (int q = 0; q < nss::kNumClasses; ++q) {
+    if (c->init_items[q].empty()) continue;
+    Rec rr(c, NSS_K_INIT);
+    CK(nss::launch_init(q, D, c->d_init[q], (int)c->init_items[q].size(), c->stream), "init launch");
+  }
+  return NSS_OK;
+}
+
+bool all_done(const nss_ctx* c) {
+  for (int r = 0; r < c->n_runs; ++r)
+    if (!c->h_state[r].done) return false;
+  return true;
+}
+
+void fill_info(const nss_ctx* c, nss_step_info* info) {
+  if (!info) return;
+  for (int r = 0; r < c->n_runs; ++r) {
+    const RunState& s = c->h_state[r];
+    nss_step_info& o = info[r];
+    o.iter = s.iter;
+    o.done = s.done;
+    o.logLstar = s.logLstar;
+    o.logZ = s.logZ;
+    o.logX = s.logX;
+    o.n_dead = s.n_dead;
+    o.evals = s.evals;
+    o.nulls = s.nulls;
+    o.cap_out = s.cap_out;
+    o.nan_evals = s.nan_evals;
+    o.metric_status = s.metric_status;
+    o.status = s.status;
+  }
+}
+
+nss_status finalise_impl(nss_ctx* c, nss_result* res) {
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  if (!all_done(c)) return set_err(c, NSS_ERR_STATE, "finalise before every run terminated");
+  nss::Dev D = dev_of(c);
+  {
+    Rec r(c, NSS_K_FINAL_SORT);
+    CK(nss::launch_final_sort(D, c->n_runs, c->final_smem, c->stream), "final sort launch");
+  }
+  if ((st = sync_state(c)) != NSS_OK) return st;
+  // tiles of kVolTile dead points, runs contiguous
+  std::vector<int2> tiles;
+  std::vector<int> vbase(c->n_runs);
+  for (int r = 0; r < c->n_runs; ++r) {
+    vbase[r] = (int)tiles.size();
+    const long long n = c->h_state[r].n_dead;
+    for (long long i = 0; i < n; i += nss::kVolTile) tiles.push_back(make_int2(r, (int)i));
+  }
+  const int nt = (int)tiles.size();
+  if (nt > 0) {
+    if (nt > c->vol_cap_tiles) {
+      cudaFree(c->d_vol);
+      cudaFree(c->d_tiles);
+      c->d_vol = nullptr;
+      c->d_tiles = nullptr;
+      const int cap = nt + nt / 4 + 16;
+      CK(cudaMalloc(&c->d_vol, sizeof(double) * 4 * (size_t)c->R * cap), "volume scratch");
+      CK(cudaMalloc(&c->d_tiles, sizeof(int2) * cap), "tile list");
+      c->vol_cap_tiles = cap;
+    }
+    CK(cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int2) * nt, cudaMemcpyHostToDevice, c->stream), "tiles upload");
+    c->prof.h2d_bytes += (long long)(sizeof(int2) * nt + sizeof(int) * c->n_runs);
+    CK(cudaMemcpyAsync(c->d_vbase, vbase.data(), sizeof(int) * c->n_runs, cudaMemcpyHostToDevice, c->stream), "vbase upload");
+    nss::VolLaunch V;
+    V.tiles = c->d_tiles;
+    V.vbase = c->d_vbase;
+    V.n_tiles = nt;
+    V.R = c->R;
+    const size_t blk = (size_t)c->R * nt;
+    V.tsum = c->d_vol;
+    V.toff = c->d_vol + blk;
+    V.tmax = c->d_vol + 2 * blk;
+    V.tacc = c->d_vol + 3 * blk;
+    Rec r(c, NSS_K_VOLSIM);
+    CK(nss::launch_volsim(D, V, c->n_runs, c->stream), "volume simulation launch");
+  }
+  if ((st = sync_state(c)) != NSS_OK) return st;
+  nss_status worst = NSS_OK;
+  for (int r = 0; r < c->n_runs; ++r) {
+    const RunState& s = c->h_state[r];
+    if (res) {
+      nss_result& o = res[r];
+      o.logZ = s.logZ_mean;
+      o.logZ_err = s.logZ_std;
+      o.logZ_det = s.logZ;
+      o.n_dead = s.n_dead;
+      o.iters = s.iter;
+      o.evals = s.evals;
+      o.nulls = s.nulls;
+      o.cap_out = s.cap_out;
+      o.nan_evals = s.nan_evals;
+      o.status = s.status;
+    }
+    if (s.status == NSS_ERR_CAPACITY) worst = NSS_ERR_CAPACITY;
+    if (s.status == NSS_ERR_NUMERIC && worst == NSS_OK) worst = NSS_ERR_NUMERIC;
+  }
+  if (worst != NSS_OK) return set_err(c, worst, "a run ended with status %d", (int)worst);
+  return NSS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void nss_options_default(nss_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->seed = 0;
+  o->run_id = 0;
+  o->w = 1.0;
+  o->w_rule = NSS_W_FIXED;
+  o->dir_norm = NSS_DIR_MAHAL;
+  o->tol = 1e-3;
+  o->max_iter = 100000;
+  o->dead_capacity = 0;
+  o->n_sim = 100;
+  o->cov_eps = 1e-6;
+  o->cuda_stream = nullptr;
+}
+
+int nss_abi_version(void) { return NSS_ABI_VERSION; }
+
+const char* nss_status_string(nss_status s) {
+  switch (s) {
+    case NSS_OK: return "ok";
+    case NSS_DONE: return "done";
+    case NSS_ERR_ARG: return "invalid argument";
+    case NSS_ERR_CUDA: return "CUDA error";
+    case NSS_ERR_OOM: return "out of device memory";
+    case NSS_ERR_CAPACITY: return "dead-point store full";
+    case NSS_ERR_TIMEOUT: return "iteration cap reached";
+    case NSS_ERR_NUMERIC: return "non-finite evidence";
+    case NSS_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* nss_last_error(const nss_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+int nss_n_runs(const nss_ctx* c) { return c ? c->n_runs : 0; }
+
+double nss_run_width(const nss_ctx* c, int run) {
+  if (!c || run < 0 || run >= c->n_runs) return NAN;
+  return c->widths[run];
+}
+
+nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik* loglik,
+                            const int* n_live, const int* kk, const int* pp, const nss_options* opt,
+                            nss_ctx** out) {
+  if (!out) return NSS_ERR_ARG;
+  *out = nullptr;
+  if (n_runs < 1 || !prior || !loglik || !n_live || !kk || !pp || !opt) return NSS_ERR_ARG;
+  nss_ctx* c = new nss_ctx();
+  c->n_runs = n_runs;
+  for (int r = 0; r < n_runs; ++r) {
+    nss_status s = validate(c, prior[r], loglik[r], n_live[r], kk[r], pp[r], opt[r], r);
+    if (s != NSS_OK) {
+      std::string msg = c->err;
+      delete c;
+      std::fprintf(stderr, "nss_create: %s\n", msg.c_str());
+      return s;
+    }
+  }
+  c->R = opt[0].n_sim;
+  for (int r = 1; r < n_runs; ++r)
+    if (opt[r].n_sim != c->R) {
+      delete c;
+      return NSS_ERR_ARG;
+    }
+  c->stream = static_cast<cudaStream_t>(opt[0].cuda_stream);
+
+  // ---- layout -------------------------------------------------------------
+  c->desc.resize(n_runs);
+  c->widths.resize(n_runs);
+  c->run_ids.resize(n_runs);
+  double kappa = -1.0;
+  for (int r = 0; r < n_runs; ++r) {
+    const nss_prior& pr = prior[r];
+    const nss_loglik& lk = loglik[r];
+    const nss_options& o = opt[r];
+    RunDesc& R = c->desc[r];
+    std::memset(&R, 0, sizeof R);
+    R.d = pr.d;
+    R.dpad = (pr.d + 3) & ~3;
+    R.m = n_live[r];
+    R.k = kk[r];
+    R.p = pp[r];
+    int m2 = 1;
+    while (m2 < R.m) m2 <<= 1;
+    R.m2 = m2;
+    R.prior_kind = pr.kind;
+    R.lik_kind = lk.kind;
+    R.n_comp = (lk.kind == NSS_LOGLIK_GMM_ISO_EQUAL) ? lk.n_comp : 1;
+    R.n_data = lk.n_data;
+    R.dir_norm = o.dir_norm;
+    R.cls = class_of(R.d);
+    R.fault_mode = lk.fault_mode;
+    R.fault_param = (float)lk.fault_param;
+    R.max_iter = o.max_iter;
+    double w = o.w;
+    if (o.w_rule == NSS_W_THEORY) {
+      if (kappa < 0) kappa = kappa_inf_host();
+      w = kappa * mean_chord_host(R.d, std::sqrt(R.d + 2.0));
+    }
+    c->widths[r] = (double)(float)w;
+    R.w = (float)w;
+    R.cov_eps = (float)o.cov_eps;
+    R.tol = o.tol;
+    R.key0 = (uint32_t)o.seed;
+    R.key1 = (uint32_t)(o.seed >> 32) ^ o.run_id;
+    c->run_ids[r] = o.run_id;
+    if (lk.kind == NSS_LOGLIK_GAUSS_ISO || lk.kind == NSS_LOGLIK_GMM_ISO_EQUAL ||
+        lk.kind == NSS_LOGLIK_TEST_FAULT) {
+      const double s2 = lk.sigma * lk.sigma;
+      R.inv2s2 = (float)(1.0 / (2.0 * s2));
+      R.lognorm = (float)(-0.5 * R.d * std::log(2.0 * M_PI * s2) - std::log((double)R.n_comp));
+    }
+    if (pr.kind == NSS_PRIOR_GAUSS_DIAG) {
+      double pc = 0.0;
+      for (int i = 0; i < R.d; ++i) pc += -std::log(pr.b[i]) - 0.5 * std::log(2.0 * M_PI);
+      R.prior_const = (float)pc;
+    }
+    long long cap = o.dead_capacity > 0 ? o.dead_capacity : (long long)R.k * 2000 + R.m;
+    cap = std::max(cap, (long long)R.m);
+    R.dead_cap = cap;
+    // FP32 pool
+    R.o_x = c->nf; c->nf += align16((long long)R.m * R.dpad);
+    R.o_logL = c->nf; c->nf += align16(R.m);
+    R.o_birth = c->nf; c->nf += align16(R.m);
+    R.o_dx = c->nf; c->nf += align16(cap * R.dpad);
+    R.o_dlogL = c->nf; c->nf += align16(cap);
+    R.o_dbirth = c->nf; c->nf += align16(cap);
+    R.o_a = c->nf; c->nf += align16(R.dpad);
+    R.o_b = c->nf; c->nf += align16(R.dpad);
+    R.o_mu = c->nf; c->nf += align16((long long)R.n_comp * R.dpad);
+    R.o_L = c->nf; c->nf += align16((long long)R.dpad * R.dpad);
+    // INT32 pool
+    R.o_dn = c->ni; c->ni += align16(cap);
+    R.o_dead = c->ni; c->ni += align16(R.k);
+    R.o_parent = c->ni; c->ni += align16(R.k);
+    R.o_stats = c->ni; c->ni += align16(6LL * R.k);
+    // FP64 pool
+    R.o_cum = c->nd; c->nd += align16(R.m + 1);
+    R.o_lnd = c->nd; c->nd += align16(R.m);
+    R.o_lw = c->nd; c->nd += align16(cap);
+    // shared memory of the prologue: sort keys + survivors/flags, or the
+    // covariance reductions and the two d x d matrices
+    const size_t sortb = (size_t)R.m2 * 8 + (size_t)R.m2 * 4 + (size_t)R.m * 4;
+    const int nt = R.dpad / 4, ntp = nt * (nt + 1) / 2, parts2 = std::max(1, 1024 / ntp);
+    const size_t covb = sizeof(float) * ((size_t)parts2 * ntp * 16 + 2 * (size_t)R.dpad * R.dpad);
+    const size_t meanb = sizeof(float) * 1024;
+    c->prologue_smem = std::max(c->prologue_smem, std::max(sortb, std::max(covb, meanb)));
+    c->final_smem = std::max(c->final_smem, (size_t)R.m2 * 8);
+  }
+  // work items: 32/G chains (or slots) of one run per warp, costliest first
+  for (int r = 0; r < n_runs; ++r) {
+    const RunDesc& R = c->desc[r];
+    const int per = 32 >> R.cls;
+    for (int s = 0; s < R.m; s += per) c->init_items[R.cls].push_back({r, s, std::min(s + per, R.m), 0});
+    for (int j = 0; j < R.k; j += per) c->sweep_items[R.cls].push_back({r, j, std::min(j + per, R.k), 0});
+  }
+  for (int q = 0; q < nss::kNumClasses; ++q) {
+    auto cost = [&](const WorkItem& w) { return (double)c->desc[w.run].p * c->desc[w.run].d; };
+    std::stable_sort(c->sweep_items[q].begin(), c->sweep_items[q].end(),
+                     [&](const WorkItem& a, const WorkItem& b) { return cost(a) > cost(b); });
+  }
+
+  // ---- device allocation and upload --------------------------------------
+  cudaError_t e;
+#define CKC(call, where)                                           \
+  do {                                                             \
+    e = (call);                                                    \
+    if (e != cudaSuccess) {                                        \
+      nss_status s_ = cuda_fail(c, e, where);                      \
+      std::fprintf(stderr, "nss_create: %s\n", c->err.c_str());    \
+      free_ctx(c);                                                 \
+      return s_;                                                   \
+    }                                                              \
+  } while (0)
+  CKC(cudaGetDevice(&c->device), "cudaGetDevice");
+  CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
+  CKC(cudaMalloc(&c->d_desc, sizeof(RunDesc) * n_runs), "descriptor allocation");
+  CKC(cudaMalloc(&c->d_state, sizeof(RunState) * n_runs), "state allocation");
+  CKC(cudaMallocHost(&c->h_state, sizeof(RunState) * n_runs), "pinned state allocation");
+  CKC(cudaMalloc(&c->fpool, sizeof(float) * std::max(c->nf, 16LL)), "FP32 pool allocation");
+  CKC(cudaMalloc(&c->ipool, sizeof(int) * std::max(c->ni, 16LL)), "INT32 pool allocation");
+  CKC(cudaMalloc(&c->dpool, sizeof(double) * std::max(c->nd, 16LL)), "FP64 pool allocation");
+  CKC(cudaMalloc(&c->d_queue, sizeof(int) * nss::kNumClasses), "queue allocation");
+  CKC(cudaMalloc(&c->d_vbase, sizeof(int) * n_runs), "vbase allocation");
+  CKC(cudaMemsetAsync(c->fpool, 0, sizeof(float) * std::max(c->nf, 16LL), c->stream), "pool clear");
+  CKC(cudaMemsetAsync(c->ipool, 0, sizeof(int) * std::max(c->ni, 16LL), c->stream), "pool clear");
+  CKC(cudaMemsetAsync(c->dpool, 0, sizeof(double) * std::max(c->nd, 16LL), c->stream), "pool clear");
+  // host staging of the problem constants
+  {
+    std::vector<float> hf;
+    std::vector<double> hd;
+    for (int r = 0; r < n_runs; ++r) {
+      const RunDesc& R = c->desc[r];
+      const nss_prior& pr = prior[r];
+      const nss_loglik& lk = loglik[r];
+      std::vector<float> seg((size_t)(R.o_L - R.o_a), 0.0f);
+      for (int i = 0; i < R.d; ++i) {
+        seg[i] = (float)pr.a[i];
+        seg[(R.o_b - R.o_a) + i] = (float)pr.b[i];
+      }
+      if (lk.kind != NSS_LOGLIK_FLAT)
+        for (int q = 0; q < R.n_comp; ++q)
+          for (int i = 0; i < R.d; ++i) seg[(R.o_mu - R.o_a) + (size_t)q * R.dpad + i] = (float)lk.mu[(size_t)q * R.d + i];
+      CKC(cudaMemcpy(c->fpool + R.o_a, seg.data(), sizeof(float) * seg.size(), cudaMemcpyHostToDevice), "problem upload");
+      c->prof.h2d_bytes += (long long)(sizeof(float) * seg.size() + sizeof(double) * (2 * R.m + 1));
+      // unrolled live-count tables (App. D.1)
+      std::vector<double> cum(R.m + 1), lnd(R.m);
+      double acc = 0.0;
+      for (int j = 0; j < R.m; ++j) {
+        cum[j] = acc;
+        const double n = (double)(R.m - j);
+        lnd[j] = std::log(-std::expm1(-1.0 / n));
+        acc += 1.0 / n;
+      }
+      cum[R.m] = acc;
+      CKC(cudaMemcpy(c->dpool + R.o_cum, cum.data(), sizeof(double) * cum.size(), cudaMemcpyHostToDevice), "table upload");
+      CKC(cudaMemcpy(c->dpool + R.o_lnd, lnd.data(), sizeof(double) * lnd.size(), cudaMemcpyHostToDevice), "table upload");
+    }
+    (void)hf;
+    (void)hd;
+  }
+  CKC(cudaMemcpy(c->d_desc, c->desc.data(), sizeof(RunDesc) * n_runs, cudaMemcpyHostToDevice), "descriptor upload");
+  c->prof.h2d_bytes += (long long)(sizeof(RunDesc) + sizeof(RunState)) * n_runs;
+  clear_states(c);
+  CKC(cudaMemcpy(c->d_state, c->h_state, sizeof(RunState) * n_runs, cudaMemcpyHostToDevice), "state upload");
+  for (int q = 0; q < nss::kNumClasses; ++q) {
+    if (!c->init_items[q].empty()) {
+      CKC(cudaMalloc(&c->d_init[q], sizeof(WorkItem) * c->init_items[q].size()), "work list allocation");
+      CKC(cudaMemcpy(c->d_init[q], c->init_items[q].data(), sizeof(WorkItem) * c->init_items[q].size(), cudaMemcpyHostToDevice), "work list upload");
+    }
+    if (!c->sweep_items[q].empty()) {
+      CKC(cudaMalloc(&c->d_sweep[q], sizeof(WorkItem) * c->sweep_items[q].size()), "work list allocation");
+      CKC(cudaMemcpy(c->d_sweep[q], c->sweep_items[q].data(), sizeof(WorkItem) * c->sweep_items[q].size(), cudaMemcpyHostToDevice), "work list upload");
+      const int per_sm = nss::sweep_blocks_per_sm(q);
+      const int warps_needed = (int)c->sweep_items[q].size();
+      const int blocks_needed = (warps_needed + 3) / 4;
+      c->sweep_grid[q] = std::max(1, std::min(blocks_needed, per_sm * c->num_sms));
+    }
+  }
+  // initial live points
+  {
+    nss_status si = launch_inits(c);
+    if (si != NSS_OK) {
+      std::fprintf(stderr, "nss_create: %s\n", c->err.c_str());
+      free_ctx(c);
+      return si;
+    }
+  }
+  CKC(cudaStreamSynchronize(c->stream), "init synchronize");
+  harvest(c);
+#undef CKC
+  *out = c;
+  return NSS_OK;
+}
+
+nss_status nss_create(const nss_prior* prior, const nss_loglik* loglik, int n_live, int k, int p,
+                      const nss_options* opt, nss_ctx** out) {
+  nss_options o;
+  if (opt) o = *opt; else nss_options_default(&o);
+  return nss_create_batch(1, prior, loglik, &n_live, &k, &p, &o, out);
+}
+
+nss_status nss_step(nss_ctx* c, nss_step_info* info) {
+  if (!c) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  if (!all_done(c)) {
+    if ((st = enqueue_iteration(c)) != NSS_OK) return st;
+    if ((st = sync_state(c)) != NSS_OK) return st;
+  }
+  fill_info(c, info);
+  for (int r = 0; r < c->n_runs; ++r)
+    if (c->h_state[r].status == NSS_ERR_CAPACITY) return set_err(c, NSS_ERR_CAPACITY, "run %d: dead store full", r);
+  return all_done(c) ? NSS_DONE : NSS_OK;
+}
+
+nss_status nss_run(nss_ctx* c, nss_result* res) {
+  if (!c) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  int chunk = 4;
+  while (!all_done(c)) {
+    for (int i = 0; i < chunk; ++i)
+      if ((st = enqueue_iteration(c)) != NSS_OK) return st;
+    if ((st = sync_state(c)) != NSS_OK) return st;
+    chunk = std::min(chunk * 2, 16);
+  }
+  return finalise_impl(c, res);
+}
+
+nss_status nss_reset(nss_ctx* c, const uint64_t* seeds) {
+  if (!c) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  if (seeds) {
+    for (int r = 0; r < c->n_runs; ++r) {
+      c->desc[r].key0 = (uint32_t)seeds[r];
+      c->desc[r].key1 = (uint32_t)(seeds[r] >> 32) ^ c->run_ids[r];
+    }
+    CK(cudaMemcpyAsync(c->d_desc, c->desc.data(), sizeof(RunDesc) * c->n_runs, cudaMemcpyHostToDevice,
+                       c->stream), "descriptor upload");
+    c->prof.h2d_bytes += (long long)sizeof(RunDesc) * c->n_runs;
+    CK(cudaStreamSynchronize(c->stream), "descriptor upload");
+  }
+  clear_states(c);
+  CK(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(RunState) * c->n_runs, cudaMemcpyHostToDevice,
+                     c->stream), "state upload");
+  c->prof.h2d_bytes += (long long)sizeof(RunState) * c->n_runs;
+  return launch_inits(c);
+}
+
+nss_status nss_finalise(nss_ctx* c, nss_result* res) {
+  if (!c) return NSS_ERR_ARG;
+  return finalise_impl(c, res);
+}
+
+nss_status nss_get_dead(nss_ctx* c, int run, float* x, float* logL, double* log_w, float* birth,
+                        int* nlive, size_t cap, size_t* n_out) {
+  if (!c || run < 0 || run >= c->n_runs) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  const RunDesc& R = c->desc[run];
+  const long long n = c->h_state[run].n_dead;
+  if (n_out) *n_out = (size_t)n;
+  if (cap == 0) return NSS_OK;
+  if (cap < (size_t)n) return set_err(c, NSS_ERR_ARG, "cap %zu < %lld dead points", cap, n);
+  if (n == 0) return NSS_OK;
+  c->prof.d2h_bytes += n * ((x ? (long long)sizeof(float) * R.d : 0) + (logL ? 4 : 0) + (birth ? 4 : 0) +
+                            (nlive ? 4 : 0) + (log_w ? 8 : 0));
+  if (x)
+    CK(cudaMemcpy2DAsync(x, sizeof(float) * R.d, c->fpool + R.o_dx, sizeof(float) * R.dpad,
+                         sizeof(float) * R.d, (size_t)n, cudaMemcpyDefault, c->stream), "dead x copy");
+  if (logL) CK(cudaMemcpyAsync(logL, c->fpool + R.o_dlogL, sizeof(float) * n, cudaMemcpyDefault, c->stream), "dead logL copy");
+  if (birth) CK(cudaMemcpyAsync(birth, c->fpool + R.o_dbirth, sizeof(float) * n, cudaMemcpyDefault, c->stream), "dead birth copy");
+  if (nlive) CK(cudaMemcpyAsync(nlive, c->ipool + R.o_dn, sizeof(int) * n, cudaMemcpyDefault, c->stream), "dead n copy");
+  if (log_w) {
+    if (!c->h_state[run].finalised) return set_err(c, NSS_ERR_STATE, "weights before finalisation");
+    CK(cudaMemcpyAsync(log_w, c->dpool + R.o_lw, sizeof(double) * n, cudaMemcpyDefault, c->stream), "weights copy");
+  }
+  CK(cudaStreamSynchronize(c->stream), "copy synchronize");
+  return NSS_OK;
+}
+
+nss_status nss_export_state(nss_ctx* c, int run, float* x, float* logL, float* birth, nss_state* s) {
+  if (!c || run < 0 || run >= c->n_runs) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  const RunDesc& R = c->desc[run];
+  if (x)
+    CK(cudaMemcpy2DAsync(x, sizeof(float) * R.d, c->fpool + R.o_x, sizeof(float) * R.dpad,
+                         sizeof(float) * R.d, (size_t)R.m, cudaMemcpyDefault, c->stream), "live x copy");
+  if (logL) CK(cudaMemcpyAsync(logL, c->fpool + R.o_logL, sizeof(float) * R.m, cudaMemcpyDefault, c->stream), "live logL copy");
+  if (birth) CK(cudaMemcpyAsync(birth, c->fpool + R.o_birth, sizeof(float) * R.m, cudaMemcpyDefault, c->stream), "live birth copy");
+  CK(cudaStreamSynchronize(c->stream), "copy synchronize");
+  if (s) {
+    const RunState& h = c->h_state[run];
+    s->iter = h.iter;
+    s->logZ = h.logZ;
+    s->logX = h.logX;
+    s->n_dead = h.n_dead;
+  }
+  return NSS_OK;
+}
+
+nss_status nss_import_state(nss_ctx* c, int run, const float* x, const float* logL, const float* birth,
+                            const nss_state* s) {
+  if (!c || run < 0 || run >= c->n_runs || !x || !logL || !s) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  const RunDesc& R = c->desc[run];
+  if (s->iter < 0 || s->n_dead < 0 || s->n_dead > R.dead_cap) return set_err(c, NSS_ERR_ARG, "invalid imported scalars");
+  for (int i = 0; i < R.m; ++i)
+    if (std::isnan(logL[i])) return set_err(c, NSS_ERR_ARG, "NaN logL in imported state");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  CK(cudaMemsetAsync(c->fpool + R.o_x, 0, sizeof(float) * (size_t)R.m * R.dpad, c->stream), "live clear");
+  CK(cudaMemcpy2DAsync(c->fpool + R.o_x, sizeof(float) * R.dpad, x, sizeof(float) * R.d,
+                       sizeof(float) * R.d, (size_t)R.m, cudaMemcpyDefault, c->stream), "live x upload");
+  CK(cudaMemcpyAsync(c->fpool + R.o_logL, logL, sizeof(float) * R.m, cudaMemcpyDefault, c->stream), "live logL upload");
+  if (birth) {
+    CK(cudaMemcpyAsync(c->fpool + R.o_birth, birth, sizeof(float) * R.m, cudaMemcpyDefault, c->stream), "live birth upload");
+  } else {
+    std::vector<float> nb(R.m, -INFINITY);
+    CK(cudaMemcpyAsync(c->fpool + R.o_birth, nb.data(), sizeof(float) * R.m, cudaMemcpyHostToDevice, c->stream), "live birth upload");
+    CK(cudaStreamSynchronize(c->stream), "upload synchronize");
+  }
+  RunState& h = c->h_state[run];
+  RunState ns;
+  std::memset(&ns, 0, sizeof ns);
+  ns.iter = s->iter;
+  ns.logZ = s->logZ;
+  ns.logX = s->logX;
+  ns.n_dead = s->n_dead;
+  ns.logLstar = -INFINITY;
+  ns.evals = h.evals;
+  CK(cudaMemcpyAsync(c->d_state + run, &ns, sizeof ns, cudaMemcpyHostToDevice, c->stream), "state upload");
+  return sync_state(c);
+}
+
+nss_status nss_step_trace(nss_ctx* c, int run, nss_trace* tr) {
+  if (!c || run < 0 || run >= c->n_runs || !tr) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  const RunState& h = c->h_state[run];
+  if (!h.stepped) return set_err(c, NSS_ERR_STATE, "no step since create or import");
+  const RunDesc& R = c->desc[run];
+  std::vector<int> dead(R.k), stats(6 * (size_t)R.k);
+  CK(cudaMemcpyAsync(dead.data(), c->ipool + R.o_dead, sizeof(int) * R.k, cudaMemcpyDeviceToHost, c->stream), "trace copy");
+  CK(cudaMemcpyAsync(stats.data(), c->ipool + R.o_stats, sizeof(int) * 6 * R.k, cudaMemcpyDeviceToHost, c->stream), "trace copy");
+  if (tr->parent) CK(cudaMemcpyAsync(tr->parent, c->ipool + R.o_parent, sizeof(int) * R.k, cudaMemcpyDefault, c->stream), "trace copy");
+  if (tr->L)
+    CK(cudaMemcpy2DAsync(tr->L, sizeof(float) * R.d, c->fpool + R.o_L, sizeof(float) * R.dpad,
+                         sizeof(float) * R.d, (size_t)R.d, cudaMemcpyDefault, c->stream), "trace copy");
+  std::vector<float> lx((size_t)R.m * R.dpad), ll(R.m);
+  CK(cudaMemcpyAsync(lx.data(), c->fpool + R.o_x, sizeof(float) * lx.size(), cudaMemcpyDeviceToHost, c->stream), "trace copy");
+  CK(cudaMemcpyAsync(ll.data(), c->fpool + R.o_logL, sizeof(float) * R.m, cudaMemcpyDeviceToHost, c->stream), "trace copy");
+  CK(cudaStreamSynchronize(c->stream), "trace synchronize");
+  if (tr->dead_idx) std::memcpy(tr->dead_idx, dead.data(), sizeof(int) * R.k);
+  int* dst[6] = {tr->evals, tr->accepts, tr->nulls, tr->expansions, tr->shrinks, tr->cap_out};
+  for (int q = 0; q < 6; ++q)
+    if (dst[q]) std::memcpy(dst[q], stats.data() + (size_t)q * R.k, sizeof(int) * R.k);
+  for (int j = 0; j < R.k; ++j) {
+    const int slot = dead[j];
+    if (tr->new_x) std::memcpy(tr->new_x + (size_t)j * R.d, lx.data() + (size_t)slot * R.dpad, sizeof(float) * R.d);
+    if (tr->new_logL) tr->new_logL[j] = ll[slot];
+  }
+  tr->logLstar = h.logLstar;
+  return NSS_OK;
+}
+
+nss_status nss_set_profiling(nss_ctx* c, int on) {
+  if (!c) return NSS_ERR_ARG;
+  c->profiling = on != 0;
+  if (on) std::memset(&c->prof, 0, sizeof c->prof);
+  return NSS_OK;
+}
+
+nss_status nss_get_profile(nss_ctx* c, nss_profile* p) {
+  if (!c || !p) return NSS_ERR_ARG;
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  *p = c->prof;
+  return NSS_OK;
+}
+
+void nss_destroy(nss_ctx* c) {
+  if (!c) return;
+  if (!c->broken) cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+}  // extern "C"

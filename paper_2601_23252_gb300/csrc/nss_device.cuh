@@ -1,0 +1,188 @@
+// nss_device.cuh -- device helpers shared by the Nested Slice Sampling kernels:
+// the counter-based generator, uniform and normal maps, group and block
+// reductions, and sort keys.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nss_internal.h"
+
+namespace nss {
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64-bit products with the published multipliers; the key is bumped by
+// the published Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 draw_block(const RunDesc& R, uint32_t c0, uint32_t c1, uint32_t c2,
+                                            uint32_t blk) {
+  return philox4x32_10(make_uint4(c0, c1, c2, blk), R.key0, R.key1);
+}
+
+__device__ __forceinline__ uint32_t pick(const uint4& b, uint32_t lane) {
+  return lane == 0 ? b.x : lane == 1 ? b.y : lane == 2 ? b.z : b.w;
+}
+
+// u = (2*(w >> 9) + 1) * 2^-24: an odd multiple of 2^-24 in (0, 1), exact in FP32.
+__device__ __forceinline__ float u24(uint32_t w) {
+  return __uint2float_rn(2u * (w >> 9) + 1u) * 0x1p-24f;
+}
+
+// 52-bit uniform (2*x + 1) * 2^-53 from two words, exact in FP64.
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  const unsigned long long x = ((unsigned long long)(a >> 6) << 26) | (unsigned long long)(b >> 6);
+  return (2.0 * (double)x + 1.0) * 0x1p-53;
+}
+
+// Box-Muller: r = sqrt(-2 ln u1), angle 2 pi u2.
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
+  const float r = sqrtf(-2.0f * logf(u24(a)));
+  float s, c;
+  sincospif(2.0f * u24(b), &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// ---- reductions within a chain group of G lanes (butterfly: every lane of
+// the group ends with the bitwise-identical total) ----
+template <int G>
+__device__ __forceinline__ float gsum(float v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+  return v;
+}
+
+template <int G>
+__device__ __forceinline__ float gmax(float v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, G));
+  return v;
+}
+
+// ---- block reductions (fixed order: deterministic) ----
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// scratch: >= 32 doubles of shared memory; every thread of the block calls.
+__device__ __forceinline__ double block_sum_d(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum_d(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  const double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max_d(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_max_d(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : -INFINITY;
+  if (wid == 0) t = warp_max_d(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  const double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// exclusive prefix sum of one int per thread; returns the prefix, *total the sum
+__device__ __forceinline__ int block_exscan_i(int v, int* scratch, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += n;
+  }
+  __syncthreads();
+  if (lane == 31) scratch[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int s = (lane < nw) ? scratch[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += n;
+    }
+    scratch[lane] = s;  // inclusive over warps
+  }
+  __syncthreads();
+  const int base = wid > 0 ? scratch[wid - 1] : 0;
+  *total = scratch[nw - 1];
+  __syncthreads();
+  return base + inc - v;
+}
+
+// Sort key ordering (logL ascending, slot ascending); -0 is folded into +0.
+__device__ __forceinline__ unsigned long long sort_key(float f, int slot) {
+  f = f + 0.0f;
+  uint32_t u = __float_as_uint(f);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)u << 32) | (uint32_t)slot;
+}
+
+// Bitonic sort of n (power of two) keys in shared memory by the whole block.
+__device__ __forceinline__ void bitonic_sort(unsigned long long* keys, int n) {
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+        const int lo = 2 * t - (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const unsigned long long a = keys[lo], b = keys[hi];
+        if ((a > b) == up) {
+          keys[lo] = b;
+          keys[hi] = a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double logaddexp_d(double a, double b) {
+  if (a == -INFINITY) return b;
+  if (b == -INFINITY) return a;
+  const double m = fmax(a, b);
+  return m + log1p(exp(-fabs(a - b)));
+}
+
+}  // namespace nss

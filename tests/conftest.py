@@ -26,3 +26,11 @@ def paper_value(name):
             if parts[0] == name:
                 return float(parts[1]), int(parts[2])
     raise KeyError(name)
+
+
+@pytest.fixture(scope="session")
+def gpu_lib():
+    """Builds (if stale) and loads the CUDA library; GPU tests only."""
+    from paper_2601_23252_gb300 import build, native
+    build.build()
+    return native.lib()

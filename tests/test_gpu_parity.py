@@ -1,0 +1,110 @@
+"""GPU <-> checker parity of one outer iteration fed the same FP32 state and
+the same Philox counters: selection indices, threshold and parents
+bit-exact; per-chain accept/eval counters bit-exact except near-ties;
+positions and logL of the matching chains within 1e-5 relative; evidence
+scalars within FP64 rounding of the FP32 terms."""
+import numpy as np
+import pytest
+
+import oracle as O
+from parity import compare_step, near_tie_mask, oracle_opts, oracle_problem
+from paper_2601_23252_gb300 import native
+from paper_2601_23252_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+COUNTERS = ("evals", "accepts", "nulls", "expansions", "shrinks", "cap_out")
+
+
+def _wl(name, seed):
+    if name == "gauss_d2":
+        return W.gauss_d2(seed=seed)
+    if name == "gmm_d32":
+        return W.gmm_d32(seed=seed)
+    if name == "gmm_d32_small":
+        return W.gmm_d32(seed=seed, n_live=300, k=150).with_(p=12)
+    if name == "gauss_d5_odd":
+        d = 5
+        return W.Workload("gauss_d5", d, "box", np.zeros(d), np.ones(d), "gauss", 64, 33, 7,
+                          sigma=0.05, mu=np.full((1, d), 0.4), seed=seed)
+    if name == "gauss20":
+        return W.gauss20_paper(seed=seed, n_live=256, k=100).with_(p=10)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["gauss_d2", "gauss_d5_odd"])
+def test_initial_live_set_matches_checker(gpu_lib, name):
+    wl = _wl(name, 3)
+    with native.Sampler(wl) as s:
+        st = s.export_state()
+    pb, op = oracle_problem(wl), oracle_opts(wl)
+    ox, _, _ = O.init_live(pb, op)
+    # uniform box [0,1]^d: x = u is exact in FP32 on both sides
+    assert np.array_equal(st["x"], ox.astype(np.float32))
+    ref = pb.loglik(st["x"].astype(np.float64))
+    assert np.allclose(st["logL"], ref, rtol=1e-5, atol=1e-5)
+    assert np.all(st["birth"] == -np.inf)
+
+
+@pytest.mark.parametrize("name,seed,warm", [
+    ("gauss_d2", 1, 1), ("gauss_d2", 2, 6), ("gauss_d5_odd", 4, 3), ("gmm_d32_small", 5, 4),
+    ("gmm_d32", 0, 3), ("gmm_d32", 7, 25), ("gauss20", 2, 5)])
+def test_one_step_parity(gpu_lib, name, seed, warm):
+    wl = _wl(name, seed)
+    rep = compare_step(wl, warm)
+    g, t = rep["gpu"], rep["orc"]
+    key = wl.name if wl.name in ("gauss_d2", "gmm_d32", "gauss20") else "gmm_d32"
+    # (i) selection and threshold: bit-exact
+    assert np.array_equal(g["dead_idx"], t["dead_idx"])
+    assert g["logLstar"] == np.float32(t["logLstar"])
+    # (ii) parents: bit-exact
+    assert np.array_equal(g["parent"], t["parent"])
+    # metric factor
+    scale = np.abs(t["L"]).max()
+    lerr = np.abs(g["L"] - t["L"]).max() / scale
+    # (iii) counters: exact for every chain that had no near-tie
+    tie = near_tie_mask(rep, key)
+    same = np.ones(wl.k, bool)
+    for c in COUNTERS:
+        same &= g[c] == t[c]
+    ok = same & ~tie
+    xerr = np.abs(g["new_x"][ok] - t["new_x"][ok]).max() if ok.any() else 0.0
+    lrel = (np.abs(g["new_logL"][ok] - t["new_logL"][ok]) / np.maximum(1.0, np.abs(t["new_logL"][ok]))).max()
+    print(f"\n{name} seed={seed} warm={warm}: L rel err {lerr:.2e}, ties {tie.mean():.4f}, "
+          f"mismatch {np.mean(~same):.4f}, x err {xerr:.2e}, logL rel err {lrel:.2e}, "
+          f"logZ err {abs(rep['info']['logZ'] - rep['orc_logZ']):.2e}, "
+          f"evals gpu {g['evals'].sum()} orc {t['evals'].sum()}")
+    assert lerr < 2e-5
+    assert np.all(same | tie), np.nonzero(~(same | tie))[0][:10]
+    assert tie.mean() < 0.1
+    assert ok.mean() > 0.9
+    width = np.max(wl.b - wl.a) if wl.prior == "box" else 1.0
+    assert xerr <= 1e-5 * width
+    assert lrel <= 1e-5
+    # every chain (tied or not) ends strictly inside the constrained set
+    moved = g["nulls"] < wl.p
+    ll64 = oracle_problem(wl).loglik(g["new_x"][moved].astype(np.float64))
+    assert np.all(ll64 > t["logLstar"] - 1e-4 * max(1.0, abs(t["logLstar"])))
+    # evidence scalars
+    assert abs(rep["info"]["logX"] - rep["orc_logX"]) < 1e-12
+    assert abs(rep["info"]["logZ"] - rep["orc_logZ"]) < 1e-6 * max(1.0, abs(rep["orc_logZ"]))
+    # the state left behind: dead slots hold the chain results, born at logL*
+    gs = rep["gstate"]
+    assert np.array_equal(gs["x"][g["dead_idx"]], g["new_x"])
+    assert np.all(gs["birth"][g["dead_idx"]] == g["logLstar"])
+    keep = np.setdiff1d(np.arange(wl.n_live), g["dead_idx"])
+    assert np.array_equal(gs["x"][keep], rep["x32"][keep])
+
+
+def test_batched_runs_equal_single_runs(gpu_lib):
+    wls = [W.gauss_d2(seed=11), W.gmm_d32(seed=12, n_live=200, k=100).with_(p=8, run_id=1),
+           W.gauss_d2(seed=13).with_(run_id=2)]
+    with native.Sampler(wls) as b:
+        b.run()
+        dead_b = [b.dead(r) for r in range(3)]
+    for r, wl in enumerate(wls):
+        with native.Sampler(wl) as s:
+            res = s.run()
+            d1 = s.dead(0)
+        for key in ("x", "logL", "nlive", "birth", "log_w"):
+            assert np.array_equal(d1[key], dead_b[r][key]), (r, key)

@@ -235,6 +235,7 @@ def run_native(args):
     flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     sampler = native.Sampler(wls, stream=stream.cuda_stream)
+    chosen = sampler.autotune(iters=3)
     for _ in range(args.warmup):
         sampler.reset()
         sampler.run()
@@ -288,7 +289,7 @@ def run_native(args):
     achieved = flops / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": ncu_traffic(),
-                "kernel": "k_sweep<8> (HRSS sweep, fused mixture likelihood)",
+                "kernel": f"k_sweep<{chosen[0]['lanes_per_chain']},{chosen[0]['dims_per_lane']}> (HRSS sweep, fused mixture likelihood)",
                 "peak_source": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x "
                                f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src} max clock)",
                 "avg_launch_ms": sweep_ms / sweep_launches,
@@ -300,6 +301,7 @@ def run_native(args):
             "config": {"workload": "gmm_d32", "d": 32, "n_comp": 4, "sigma": 0.02, "n_live": 1000,
                        "k": 500, "p": 96, "runs_per_gpu": nrun, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (512 MB write)",
+                       "sweep_cfg": chosen[0],
                        "evidence_accumulation": "f64"},
             "evals_per_s": evals_all / (total_ms_all / 1e3),
             "gate": {"mean_dlogZ": float(dlogZ.mean()), "max_abs_dlogZ_over_err": float(np.max(np.abs(dlogZ) / errs)),
@@ -316,6 +318,8 @@ def run_native(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with native.Sampler(wls, stream=stream.cuda_stream) as sm:
+                for r in range(nrun):
+                    sm.set_cfg(r, chosen[r]["id"])
                 rr = sm.run()
                 for r in range(nrun):
                     n = rr[r]["n_dead"]
@@ -337,6 +341,7 @@ def run_native(args):
         t_plain, dead_plain = 0.0, 0
         for wl in wls[:4]:
             with native.Sampler(wl, stream=stream.cuda_stream) as sp:
+                sp.autotune(iters=3)
                 sp.run()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)

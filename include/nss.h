@@ -234,6 +234,21 @@ nss_status nss_run(nss_ctx *ctx, nss_result *res);
    keep the current ones.  Counters and the dead-point store are cleared. */
 nss_status nss_reset(nss_ctx *ctx, const uint64_t *seeds);
 
+/* Sweep configurations.  A chain is owned by G lanes of a warp, each lane
+   holding DPL of its dimensions (G x DPL = the smallest power of two >= max(d,
+   4)); a warp runs 32/G chains.  nss_autotune times every configuration that
+   fits each run's dimension for `iters` outer iterations from a fresh prior
+   draw, keeps the fastest (device time per likelihood evaluation) for each
+   dimension class, and leaves the context reset to its prior draw (call it
+   right after create).  cfg_out: n_runs entries or NULL.  The configuration
+   changes only the order of FP32 additions inside a likelihood, not the
+   method. */
+nss_status nss_autotune(nss_ctx *ctx, int iters, int *cfg_out);
+nss_status nss_set_cfg(nss_ctx *ctx, int run, int cfg);
+int nss_get_cfg(const nss_ctx *ctx, int run);
+int nss_cfg_lanes(int cfg);
+int nss_cfg_dims(int cfg);
+
 /* Finalise runs that were stepped to termination with nss_step. */
 nss_status nss_finalise(nss_ctx *ctx, nss_result *res);
 

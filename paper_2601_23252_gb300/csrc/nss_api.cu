@@ -24,7 +24,7 @@ using nss::WorkItem;
 
 struct EvRec {
   cudaEvent_t a, b;
-  int kind;
+  int kind, cfg;
 };
 
 struct nss_ctx {
@@ -41,11 +41,11 @@ struct nss_ctx {
   int* ipool = nullptr;
   double* dpool = nullptr;
   long long nf = 0, ni = 0, nd = 0;
-  std::vector<WorkItem> init_items[nss::kNumClasses], sweep_items[nss::kNumClasses];
-  WorkItem* d_init[nss::kNumClasses] = {};
-  WorkItem* d_sweep[nss::kNumClasses] = {};
+  std::vector<WorkItem> init_items[nss::kNumCfgs], sweep_items[nss::kNumCfgs];
+  WorkItem* d_init[nss::kNumCfgs] = {};
+  WorkItem* d_sweep[nss::kNumCfgs] = {};
   int* d_queue = nullptr;
-  int sweep_grid[nss::kNumClasses] = {};
+  int sweep_grid[nss::kNumCfgs] = {};
   size_t prologue_smem = 0, final_smem = 0;
   // volume simulation scratch
   int R = 100;
@@ -58,6 +58,7 @@ struct nss_ctx {
   std::vector<EvRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   nss_profile prof{};
+  double cfg_ms[nss::kNumCfgs] = {};
   long long launches = 0;
   bool broken = false;
   std::string err;
@@ -101,13 +102,24 @@ nss::Dev dev_of(nss_ctx* c) {
   return D;
 }
 
-int class_of(int d) {
-  if (d <= 4) return 0;
-  if (d <= 8) return 1;
-  if (d <= 16) return 2;
-  if (d <= 32) return 3;
-  if (d <= 64) return 4;
-  return 5;
+// Sweep configurations able to hold d dimensions with the least padding:
+// G lanes x DPL dimensions = the smallest power of two >= max(d, 4).
+std::vector<int> candidate_cfgs(int d) {
+  int cap = 4;
+  while (cap < d) cap <<= 1;
+  std::vector<int> out;
+  for (int q = 0; q < nss::kNumCfgs; ++q)
+    if (nss::cfg_g(q) * nss::cfg_dpl(q) == cap) out.push_back(q);
+  return out;
+}
+
+// Before tuning: the widest chain group (fewest chains per warp, least
+// divergence between chains of a warp).
+int default_cfg(int d) {
+  int best = -1;
+  for (int q : candidate_cfgs(d))
+    if (best < 0 || nss::cfg_g(q) > nss::cfg_g(best)) best = q;
+  return best;
 }
 
 // ---- slice-width rule helpers (App. E), host FP64 -------------------------
@@ -237,7 +249,7 @@ void free_ctx(nss_ctx* c) {
   cudaFree(c->fpool);
   cudaFree(c->ipool);
   cudaFree(c->dpool);
-  for (int q = 0; q < nss::kNumClasses; ++q) {
+  for (int q = 0; q < nss::kNumCfgs; ++q) {
     cudaFree(c->d_init[q]);
     cudaFree(c->d_sweep[q]);
   }
@@ -267,9 +279,9 @@ cudaEvent_t take_event(nss_ctx* c) {
 
 struct Rec {
   nss_ctx* c;
-  int kind;
+  int kind, cfg;
   cudaEvent_t a = nullptr;
-  Rec(nss_ctx* c_, int k_) : c(c_), kind(k_) {
+  Rec(nss_ctx* c_, int k_, int cfg_ = -1) : c(c_), kind(k_), cfg(cfg_) {
     c->launches++;
     c->prof.total_launches++;
     c->prof.launches[kind]++;
@@ -282,7 +294,7 @@ struct Rec {
     if (a) {
       cudaEvent_t b = take_event(c);
       cudaEventRecord(b, c->stream);
-      c->pending.push_back({a, b, kind});
+      c->pending.push_back({a, b, kind, cfg});
     }
   }
 };
@@ -290,7 +302,10 @@ struct Rec {
 void harvest(nss_ctx* c) {  // after a stream synchronisation
   for (auto& e : c->pending) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) c->prof.ms[e.kind] += ms;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      c->prof.ms[e.kind] += ms;
+      if (e.cfg >= 0) c->cfg_ms[e.cfg] += ms;
+    }
     c->ev_pool.push_back(e.a);
     c->ev_pool.push_back(e.b);
   }
@@ -312,10 +327,10 @@ nss_status enqueue_iteration(nss_ctx* c) {
     Rec r(c, NSS_K_PROLOGUE);
     CK(nss::launch_prologue(D, c->n_runs, c->prologue_smem, c->stream), "prologue launch");
   }
-  for (int q = 0; q < nss::kNumClasses; ++q) {
+  for (int q = 0; q < nss::kNumCfgs; ++q) {
     if (c->sweep_items[q].empty()) continue;
     CK(cudaMemsetAsync(c->d_queue + q, 0, sizeof(int), c->stream), "queue reset");
-    Rec r(c, NSS_K_SWEEP);
+    Rec r(c, NSS_K_SWEEP, q);
     CK(nss::launch_sweep(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->d_queue + q,
                          c->sweep_grid[q], c->stream), "sweep launch");
   }
@@ -323,6 +338,47 @@ nss_status enqueue_iteration(nss_ctx* c) {
     Rec r(c, NSS_K_TERMINATE);
     CK(nss::launch_terminate(D, c->n_runs, c->stream), "terminate launch");
   }
+  return NSS_OK;
+}
+
+// Work lists of the init and sweep kernels: 32/G slots or chains of one run
+// per warp, grouped by sweep configuration, costliest runs first.
+nss_status build_work(nss_ctx* c) {
+  for (int q = 0; q < nss::kNumCfgs; ++q) {
+    c->init_items[q].clear();
+    c->sweep_items[q].clear();
+    cudaFree(c->d_init[q]);
+    cudaFree(c->d_sweep[q]);
+    c->d_init[q] = c->d_sweep[q] = nullptr;
+  }
+  for (int r = 0; r < c->n_runs; ++r) {
+    const RunDesc& R = c->desc[r];
+    const int per = 32 / nss::cfg_g(R.cfg);
+    for (int s = 0; s < R.m; s += per) c->init_items[R.cfg].push_back({r, s, std::min(s + per, R.m), 0});
+    for (int j = 0; j < R.k; j += per) c->sweep_items[R.cfg].push_back({r, j, std::min(j + per, R.k), 0});
+  }
+  for (int q = 0; q < nss::kNumCfgs; ++q) {
+    auto cost = [&](const WorkItem& w) { return (double)c->desc[w.run].p * c->desc[w.run].d; };
+    std::stable_sort(c->sweep_items[q].begin(), c->sweep_items[q].end(),
+                     [&](const WorkItem& a, const WorkItem& b) { return cost(a) > cost(b); });
+    if (!c->init_items[q].empty()) {
+      CK(cudaMalloc(&c->d_init[q], sizeof(WorkItem) * c->init_items[q].size()), "work list allocation");
+      CK(cudaMemcpyAsync(c->d_init[q], c->init_items[q].data(), sizeof(WorkItem) * c->init_items[q].size(),
+                         cudaMemcpyHostToDevice, c->stream), "work list upload");
+    }
+    if (!c->sweep_items[q].empty()) {
+      CK(cudaMalloc(&c->d_sweep[q], sizeof(WorkItem) * c->sweep_items[q].size()), "work list allocation");
+      CK(cudaMemcpyAsync(c->d_sweep[q], c->sweep_items[q].data(), sizeof(WorkItem) * c->sweep_items[q].size(),
+                         cudaMemcpyHostToDevice, c->stream), "work list upload");
+      const int per_sm = nss::sweep_blocks_per_sm(q);
+      const int warps_needed = (int)c->sweep_items[q].size();
+      const int blocks_needed = (warps_needed + 3) / 4;
+      c->sweep_grid[q] = std::max(1, std::min(blocks_needed, per_sm * c->num_sms));
+    }
+  }
+  CK(cudaMemcpyAsync(c->d_desc, c->desc.data(), sizeof(RunDesc) * c->n_runs, cudaMemcpyHostToDevice, c->stream),
+     "descriptor upload");
+  CK(cudaStreamSynchronize(c->stream), "work list upload");
   return NSS_OK;
 }
 
@@ -338,7 +394,7 @@ void clear_states(nss_ctx* c) {
 
 nss_status launch_inits(nss_ctx* c) {
   nss::Dev D = dev_of(c);
-  for (int q = 0; q < nss::kNumClasses; ++q) {
+  for (int q = 0; q < nss::kNumCfgs; ++q) {
     if (c->init_items[q].empty()) continue;
     Rec rr(c, NSS_K_INIT);
     CK(nss::launch_init(q, D, c->d_init[q], (int)c->init_items[q].size(), c->stream), "init launch");
@@ -539,7 +595,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     R.n_comp = (lk.kind == NSS_LOGLIK_GMM_ISO_EQUAL) ? lk.n_comp : 1;
     R.n_data = lk.n_data;
     R.dir_norm = o.dir_norm;
-    R.cls = class_of(R.d);
+    R.cfg = default_cfg(R.d);
     R.fault_mode = lk.fault_mode;
     R.fault_param = (float)lk.fault_param;
     R.max_iter = o.max_iter;
@@ -598,19 +654,6 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     c->prologue_smem = std::max(c->prologue_smem, std::max(sortb, std::max(covb, meanb)));
     c->final_smem = std::max(c->final_smem, (size_t)R.m2 * 8);
   }
-  // work items: 32/G chains (or slots) of one run per warp, costliest first
-  for (int r = 0; r < n_runs; ++r) {
-    const RunDesc& R = c->desc[r];
-    const int per = 32 >> R.cls;
-    for (int s = 0; s < R.m; s += per) c->init_items[R.cls].push_back({r, s, std::min(s + per, R.m), 0});
-    for (int j = 0; j < R.k; j += per) c->sweep_items[R.cls].push_back({r, j, std::min(j + per, R.k), 0});
-  }
-  for (int q = 0; q < nss::kNumClasses; ++q) {
-    auto cost = [&](const WorkItem& w) { return (double)c->desc[w.run].p * c->desc[w.run].d; };
-    std::stable_sort(c->sweep_items[q].begin(), c->sweep_items[q].end(),
-                     [&](const WorkItem& a, const WorkItem& b) { return cost(a) > cost(b); });
-  }
-
   // ---- device allocation and upload --------------------------------------
   cudaError_t e;
 #define CKC(call, where)                                           \
@@ -631,7 +674,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   CKC(cudaMalloc(&c->fpool, sizeof(float) * std::max(c->nf, 16LL)), "FP32 pool allocation");
   CKC(cudaMalloc(&c->ipool, sizeof(int) * std::max(c->ni, 16LL)), "INT32 pool allocation");
   CKC(cudaMalloc(&c->dpool, sizeof(double) * std::max(c->nd, 16LL)), "FP64 pool allocation");
-  CKC(cudaMalloc(&c->d_queue, sizeof(int) * nss::kNumClasses), "queue allocation");
+  CKC(cudaMalloc(&c->d_queue, sizeof(int) * nss::kNumCfgs), "queue allocation");
   CKC(cudaMalloc(&c->d_vbase, sizeof(int) * n_runs), "vbase allocation");
   CKC(cudaMemsetAsync(c->fpool, 0, sizeof(float) * std::max(c->nf, 16LL), c->stream), "pool clear");
   CKC(cudaMemsetAsync(c->ipool, 0, sizeof(int) * std::max(c->ni, 16LL), c->stream), "pool clear");
@@ -652,7 +695,8 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
       if (lk.kind != NSS_LOGLIK_FLAT)
         for (int q = 0; q < R.n_comp; ++q)
           for (int i = 0; i < R.d; ++i) seg[(R.o_mu - R.o_a) + (size_t)q * R.dpad + i] = (float)lk.mu[(size_t)q * R.d + i];
-      CKC(cudaMemcpy(c->fpool + R.o_a, seg.data(), sizeof(float) * seg.size(), cudaMemcpyHostToDevice), "problem upload");
+      CKC(cudaMemcpyAsync(c->fpool + R.o_a, seg.data(), sizeof(float) * seg.size(), cudaMemcpyHostToDevice,
+                          c->stream), "problem upload");
       c->prof.h2d_bytes += (long long)(sizeof(float) * seg.size() + sizeof(double) * (2 * R.m + 1));
       // unrolled live-count tables (App. D.1)
       std::vector<double> cum(R.m + 1), lnd(R.m);
@@ -664,28 +708,26 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
         acc += 1.0 / n;
       }
       cum[R.m] = acc;
-      CKC(cudaMemcpy(c->dpool + R.o_cum, cum.data(), sizeof(double) * cum.size(), cudaMemcpyHostToDevice), "table upload");
-      CKC(cudaMemcpy(c->dpool + R.o_lnd, lnd.data(), sizeof(double) * lnd.size(), cudaMemcpyHostToDevice), "table upload");
+      CKC(cudaMemcpyAsync(c->dpool + R.o_cum, cum.data(), sizeof(double) * cum.size(), cudaMemcpyHostToDevice,
+                          c->stream), "table upload");
+      CKC(cudaMemcpyAsync(c->dpool + R.o_lnd, lnd.data(), sizeof(double) * lnd.size(), cudaMemcpyHostToDevice,
+                          c->stream), "table upload");
     }
     (void)hf;
     (void)hd;
   }
-  CKC(cudaMemcpy(c->d_desc, c->desc.data(), sizeof(RunDesc) * n_runs, cudaMemcpyHostToDevice), "descriptor upload");
+  CKC(cudaMemcpyAsync(c->d_desc, c->desc.data(), sizeof(RunDesc) * n_runs, cudaMemcpyHostToDevice, c->stream),
+      "descriptor upload");
   c->prof.h2d_bytes += (long long)(sizeof(RunDesc) + sizeof(RunState)) * n_runs;
   clear_states(c);
-  CKC(cudaMemcpy(c->d_state, c->h_state, sizeof(RunState) * n_runs, cudaMemcpyHostToDevice), "state upload");
-  for (int q = 0; q < nss::kNumClasses; ++q) {
-    if (!c->init_items[q].empty()) {
-      CKC(cudaMalloc(&c->d_init[q], sizeof(WorkItem) * c->init_items[q].size()), "work list allocation");
-      CKC(cudaMemcpy(c->d_init[q], c->init_items[q].data(), sizeof(WorkItem) * c->init_items[q].size(), cudaMemcpyHostToDevice), "work list upload");
-    }
-    if (!c->sweep_items[q].empty()) {
-      CKC(cudaMalloc(&c->d_sweep[q], sizeof(WorkItem) * c->sweep_items[q].size()), "work list allocation");
-      CKC(cudaMemcpy(c->d_sweep[q], c->sweep_items[q].data(), sizeof(WorkItem) * c->sweep_items[q].size(), cudaMemcpyHostToDevice), "work list upload");
-      const int per_sm = nss::sweep_blocks_per_sm(q);
-      const int warps_needed = (int)c->sweep_items[q].size();
-      const int blocks_needed = (warps_needed + 3) / 4;
-      c->sweep_grid[q] = std::max(1, std::min(blocks_needed, per_sm * c->num_sms));
+  CKC(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(RunState) * n_runs, cudaMemcpyHostToDevice, c->stream),
+      "state upload");
+  {
+    nss_status sw = build_work(c);
+    if (sw != NSS_OK) {
+      std::fprintf(stderr, "nss_create: %s\n", c->err.c_str());
+      free_ctx(c);
+      return sw;
     }
   }
   // initial live points
@@ -761,6 +803,78 @@ nss_status nss_reset(nss_ctx* c, const uint64_t* seeds) {
                      c->stream), "state upload");
   c->prof.h2d_bytes += (long long)sizeof(RunState) * c->n_runs;
   return launch_inits(c);
+}
+
+int nss_cfg_lanes(int cfg) { return (cfg >= 0 && cfg < nss::kNumCfgs) ? nss::cfg_g(cfg) : 0; }
+int nss_cfg_dims(int cfg) { return (cfg >= 0 && cfg < nss::kNumCfgs) ? nss::cfg_dpl(cfg) : 0; }
+
+int nss_get_cfg(const nss_ctx* c, int run) {
+  if (!c || run < 0 || run >= c->n_runs) return -1;
+  return c->desc[run].cfg;
+}
+
+nss_status nss_set_cfg(nss_ctx* c, int run, int cfg) {
+  if (!c || run < 0 || run >= c->n_runs) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  bool fits = false;
+  for (int q : candidate_cfgs(c->desc[run].d)) fits |= (q == cfg);
+  if (!fits) return set_err(c, NSS_ERR_ARG, "configuration %d does not fit d=%d", cfg, c->desc[run].d);
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  c->desc[run].cfg = cfg;
+  return build_work(c);
+}
+
+nss_status nss_autotune(nss_ctx* c, int iters, int* cfg_out) {
+  if (!c || iters < 1) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  // runs grouped by the capacity G x DPL their dimension needs
+  std::vector<int> caps;
+  for (int r = 0; r < c->n_runs; ++r) {
+    int cap = 4;
+    while (cap < c->desc[r].d) cap <<= 1;
+    if (std::find(caps.begin(), caps.end(), cap) == caps.end()) caps.push_back(cap);
+  }
+  const bool prof_saved = c->profiling;
+  const nss_profile prof_saved_v = c->prof;
+  c->profiling = true;
+  for (int cap : caps) {
+    std::vector<int> runs;
+    for (int r = 0; r < c->n_runs; ++r) {
+      int cr = 4;
+      while (cr < c->desc[r].d) cr <<= 1;
+      if (cr == cap) runs.push_back(r);
+    }
+    int best = -1;
+    double best_cost = INFINITY;
+    for (int q : candidate_cfgs(cap)) {
+      for (int r : runs) c->desc[r].cfg = q;
+      if ((st = build_work(c)) != NSS_OK) return st;
+      if ((st = nss_reset(c, nullptr)) != NSS_OK) return st;
+      if ((st = sync_state(c)) != NSS_OK) return st;
+      c->cfg_ms[q] = 0.0;
+      for (int i = 0; i < iters; ++i)
+        if ((st = enqueue_iteration(c)) != NSS_OK) return st;
+      if ((st = sync_state(c)) != NSS_OK) return st;
+      double ev = 0.0;
+      for (int r : runs) ev += (double)c->h_state[r].evals;
+      const double cost = c->cfg_ms[q] / std::max(1.0, ev);
+      if (cost < best_cost) {
+        best_cost = cost;
+        best = q;
+      }
+    }
+    for (int r : runs) c->desc[r].cfg = best;
+  }
+  c->profiling = prof_saved;
+  c->prof = prof_saved_v;
+  if ((st = build_work(c)) != NSS_OK) return st;
+  if ((st = nss_reset(c, nullptr)) != NSS_OK) return st;
+  if (cfg_out)
+    for (int r = 0; r < c->n_runs; ++r) cfg_out[r] = c->desc[r].cfg;
+  return sync_state(c);
 }
 
 nss_status nss_finalise(nss_ctx* c, nss_result* res) {

@@ -17,7 +17,7 @@ constexpr int kShrinkCap = 100;     // shrinkage proposals before a null move (A
 constexpr uint32_t kTagParent = 0xFFFFFFF0u;
 constexpr uint32_t kTagInit = 0xFFFFFFF1u;
 constexpr uint32_t kTagVolsim = 0xFFFFFFF2u;
-constexpr int kNumClasses = 6;      // chain-group widths G = 1, 2, 4, 8, 16, 32
+constexpr int kNumCfgs = 15;        // (G lanes, DPL dims per lane) sweep configurations
 constexpr int kVolTile = 1024;      // dead points per volume-simulation tile
 
 enum PriorKind { kPriorBox = 0, kPriorGauss = 1 };
@@ -26,7 +26,7 @@ enum LikKind { kLikGauss = 0, kLikGmm = 1, kLikLogreg = 2, kLikGp = 3, kLikFlat 
 struct RunDesc {
   int d, dpad, m, k, p, m2;         // m2: power of two >= m for the sort
   int prior_kind, lik_kind, n_comp, n_data;
-  int dir_norm, cls;                // cls: sweep kernel class (G = 1 << cls)
+  int dir_norm, cfg;                // cfg: sweep configuration (G lanes x DPL dims)
   int fault_mode, max_iter;
   float w, cov_eps, fault_param;
   float inv2s2, lognorm;            // Gaussian / mixture constants

@@ -6,10 +6,7 @@
 //               in slot order, parents, dead-point append, unrolled evidence
 //               update (FP64 accumulation), live-set covariance and its
 //               Cholesky factor (the direction metric, Sec. 3.2).
-//   k_sweep     persistent grid over (run, chain) work items: each chain group
-//               of G lanes runs p Hit-and-Run Slice Sampling steps with the
-//               likelihood evaluated inside the step (App. B.4) and writes the
-//               new point into its dead slot (step (iv)).
+//   k_sweep     (nss_sweep.cu) the HRSS sweep with the likelihood fused in.
 //   k_terminate one block per run: remaining live evidence and the stopping
 //               test (App. B.3).
 // After termination:
@@ -24,168 +21,6 @@
 #include "nss_kernels.h"
 
 namespace nss {
-
-// ---------------------------------------------------------------------------
-// Likelihood of a chain group: lane gl owns dimensions [4 gl, 4 gl + 4).
-// Padding dimensions hold zeros in x, v and the means, so they add nothing.
-// ---------------------------------------------------------------------------
-template <int G>
-__device__ __forceinline__ float group_loglik(const RunDesc& R, const float* __restrict__ f,
-                                              const float y[4], int gl, unsigned mask) {
-  const int lk = R.lik_kind;
-  const bool has = gl * 4 < R.dpad;
-  if (lk == kLikFlat) return 0.0f;
-  if (lk == kLikGauss || lk == kLikFault) {
-    float q = 0.0f;
-    if (has) {
-      const float4 m = __ldg(reinterpret_cast<const float4*>(f + R.o_mu) + gl);
-      const float e0 = y[0] - m.x, e1 = y[1] - m.y, e2 = y[2] - m.z, e3 = y[3] - m.w;
-      q = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, e3 * e3)));
-    }
-    q = gsum<G>(q, mask);
-    float ll = fmaf(-q, R.inv2s2, R.lognorm);
-    if (lk == kLikFault) {
-      const float x0 = __shfl_sync(mask, y[0], 0, G);
-      if (x0 < R.fault_param) ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
-    }
-    return ll;
-  }
-  // equal-weight isotropic mixture: online log-sum-exp over components
-  float M = -INFINITY, S = 0.0f;
-  const float4* mu = reinterpret_cast<const float4*>(f + R.o_mu);
-  const int stride4 = R.dpad >> 2;
-  for (int c = 0; c < R.n_comp; ++c) {
-    float q = 0.0f;
-    if (has) {
-      const float4 m = __ldg(mu + c * stride4 + gl);
-      const float e0 = y[0] - m.x, e1 = y[1] - m.y, e2 = y[2] - m.z, e3 = y[3] - m.w;
-      q = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, e3 * e3)));
-    }
-    q = gsum<G>(q, mask);
-    const float v = -q * R.inv2s2;
-    if (v > M) {
-      S = S * expf(M - v) + 1.0f;
-      M = v;
-    } else {
-      S += expf(v - M);
-    }
-  }
-  return M + logf(S) + R.lognorm;
-}
-
-// Per-chain constants held by every lane of a group.
-struct ChainConst {
-  float a[4], b[4];
-  bool own[4];
-  float lstar;
-  bool box, nonflat;
-};
-
-template <int G>
-__device__ __forceinline__ float group_logprior(const RunDesc& R, const ChainConst& C,
-                                                const float y[4], unsigned mask) {
-  float s = 0.0f;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (C.own[i]) {
-      const float u = (y[i] - C.a[i]) / C.b[i];
-      s = fmaf(-0.5f * u, u, s);
-    }
-  return gsum<G>(s, mask) + R.prior_const;
-}
-
-// One logical likelihood evaluation: y is in the slice when it is in the prior
-// support, above the prior slice height (non-flat prior) and strictly above
-// logL* (Sec. 3.1: E < E_batch).  Returns the decision, identical in all lanes.
-template <int G>
-__device__ __forceinline__ bool in_slice(const RunDesc& R, const float* __restrict__ f,
-                                         const ChainConst& C, const float y[4], float height,
-                                         int gl, unsigned mask, float& ll, int& nan_cnt) {
-  if (C.box) {
-    bool out = false;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (C.own[i] && !(y[i] >= C.a[i] && y[i] <= C.b[i])) out = true;
-    if (__any_sync(mask, out)) return false;
-  }
-  if (C.nonflat) {
-    const float lp = group_logprior<G>(R, C, y, mask);
-    if (!(lp > height)) return false;
-  }
-  ll = group_loglik<G>(R, f, y, gl, mask);
-  if (isnan(ll)) {
-    ll = -INFINITY;
-    ++nan_cnt;
-  }
-  return ll > C.lstar;
-}
-
-// Words of one HRSS step, cached one Philox block (four words) at a time.
-struct WordCache {
-  uint32_t blk;
-  uint4 v;
-};
-__device__ __forceinline__ uint32_t step_word(const RunDesc& R, WordCache& wc, uint32_t iter,
-                                              uint32_t chain, uint32_t step, uint32_t wi) {
-  const uint32_t b = wi >> 2;
-  if (b != wc.blk) {
-    wc.v = draw_block(R, iter, chain, step, b);
-    wc.blk = b;
-  }
-  return pick(wc.v, wi & 3u);
-}
-
-// ---------------------------------------------------------------------------
-// Initial live set: m prior draws per run (Sec. 2.1), counter (0, slot,
-// TAG_INIT, word/4); group lane gl draws dimensions [4 gl, 4 gl + 4).
-// ---------------------------------------------------------------------------
-template <int G>
-__global__ void __launch_bounds__(128) k_init(Dev D, const WorkItem* __restrict__ items, int n_items) {
-  const int lane = threadIdx.x & 31;
-  const int gl = lane % G, grp = lane / G;
-  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int it = warp; it < n_items; it += nwarps) {
-    const WorkItem wi = items[it];
-    const RunDesc& R = D.desc[wi.run];
-    const int slot = wi.c0 + grp;
-    if (slot >= wi.c1) continue;
-    float x[4] = {0.f, 0.f, 0.f, 0.f};
-    const bool has = gl * 4 < R.dpad;
-    const uint4 w = draw_block(R, 0u, (uint32_t)slot, kTagInit, (uint32_t)gl);
-    if (R.prior_kind == kPriorBox) {
-      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int dim = gl * 4 + i;
-        if (dim < R.d) {
-          const float a = D.f[R.o_a + dim], b = D.f[R.o_b + dim];
-          x[i] = fmaf(b - a, u24(ws[i]), a);
-        }
-      }
-    } else {
-      float z[4];
-      box_muller(w.x, w.y, z[0], z[1]);
-      box_muller(w.z, w.w, z[2], z[3]);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int dim = gl * 4 + i;
-        if (dim < R.d) x[i] = fmaf(D.f[R.o_b + dim], z[i], D.f[R.o_a + dim]);
-      }
-    }
-    float ll = group_loglik<G>(R, D.f, x, gl, mask);
-    if (isnan(ll)) ll = -INFINITY;
-    if (has) {
-      reinterpret_cast<float4*>(D.f + R.o_x + (long long)slot * R.dpad)[gl] =
-          make_float4(x[0], x[1], x[2], x[3]);
-    }
-    if (gl == 0) {
-      D.f[R.o_logL + slot] = ll;
-      D.f[R.o_birth + slot] = -INFINITY;
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Unrolled evidence update for `cnt` deaths (App. D.1): the j-th death has
@@ -450,172 +285,6 @@ __global__ void __launch_bounds__(1024) k_prologue(Dev D) {
 }
 
 // ---------------------------------------------------------------------------
-// (iii)+(iv): the HRSS sweep.  One chain per group of G lanes; a warp takes
-// 32/G chains of one run from the work queue.
-// ---------------------------------------------------------------------------
-template <int G>
-__device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j, int gl,
-                            unsigned mask, float* zs) {
-  const RunState& S = *Sw;
-  const float* __restrict__ f = D.f;
-  const int d = R.d, ld = R.dpad;
-  const bool has = gl * 4 < ld;
-  const int parent = D.i[R.o_parent + j];
-  const uint32_t iter = (uint32_t)S.iter;
-  ChainConst C;
-  C.box = R.prior_kind == kPriorBox;
-  C.nonflat = !C.box;
-  C.lstar = S.logLstar;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int dim = gl * 4 + i;
-    C.own[i] = dim < d;
-    C.a[i] = C.own[i] ? f[R.o_a + dim] : 0.f;
-    C.b[i] = C.own[i] ? f[R.o_b + dim] : 1.f;
-  }
-  float x[4] = {0.f, 0.f, 0.f, 0.f};
-  if (has) {
-    const float4 p4 = reinterpret_cast<const float4*>(f + R.o_x + (long long)parent * ld)[gl];
-    x[0] = p4.x; x[1] = p4.y; x[2] = p4.z; x[3] = p4.w;
-  }
-  float lx = f[R.o_logL + parent];
-  const float w = R.w;
-  const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
-  const float* Lg = f + R.o_L;
-  int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
-  for (int s = 0; s < R.p; ++s) {
-    // direction: z ~ N(0, I), d~ = L z, v = d~ / |z| (or / |d~|)
-    const uint4 wb = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)gl);
-    float z[4];
-    box_muller(wb.x, wb.y, z[0], z[1]);
-    box_muller(wb.z, wb.w, z[2], z[3]);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (!C.own[i]) z[i] = 0.0f;
-    zs[gl * 4 + 0] = z[0];
-    zs[gl * 4 + 1] = z[1];
-    zs[gl * 4 + 2] = z[2];
-    zs[gl * 4 + 3] = z[3];
-    __syncwarp(mask);
-    const float zz = gsum<G>(fmaf(z[0], z[0], fmaf(z[1], z[1], fmaf(z[2], z[2], z[3] * z[3]))), mask);
-    float dt[4] = {0.f, 0.f, 0.f, 0.f};
-    if (has) {
-      for (int bb = 0; bb <= gl; ++bb) {
-        const float4 zb = reinterpret_cast<const float4*>(zs)[bb];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const float4 l4 = __ldg(reinterpret_cast<const float4*>(Lg + (gl * 4 + r) * ld) + bb);
-          dt[r] = fmaf(l4.x, zb.x, fmaf(l4.y, zb.y, fmaf(l4.z, zb.z, fmaf(l4.w, zb.w, dt[r]))));
-        }
-      }
-    }
-    __syncwarp(mask);
-    float nrm;
-    if (R.dir_norm == 0) {
-      nrm = sqrtf(zz);
-    } else {
-      nrm = sqrtf(gsum<G>(fmaf(dt[0], dt[0], fmaf(dt[1], dt[1], fmaf(dt[2], dt[2], dt[3] * dt[3]))), mask));
-    }
-    float v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = dt[i] / nrm;
-    WordCache wc;
-    wc.blk = 0xFFFFFFFFu;
-    float height = 0.0f;
-    if (C.nonflat) {
-      const float uh = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz + 1u));
-      height = group_logprior<G>(R, C, x, mask) + logf(uh);
-    }
-    // randomised initial bracket of width w around t = 0
-    const float U = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz));
-    float tl = -w * U;
-    float tr = tl + w;
-    float y[4], lly;
-    // stepping out, at most 10 expansions per side
-    for (int n = 0;; ++n) {
-      if (n >= kStepOutCap) { ++capo; break; }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) y[i] = fmaf(tl, v[i], x[i]);
-      ++evals;
-      if (!in_slice<G>(R, f, C, y, height, gl, mask, lly, nanc)) break;
-      tl -= w;
-      ++exps;
-    }
-    for (int n = 0;; ++n) {
-      if (n >= kStepOutCap) { ++capo; break; }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) y[i] = fmaf(tr, v[i], x[i]);
-      ++evals;
-      if (!in_slice<G>(R, f, C, y, height, gl, mask, lly, nanc)) break;
-      tr += w;
-      ++exps;
-    }
-    // shrinkage, at most 100 proposals, then a null move
-    bool ok = false;
-    for (int r = 0; r < kShrinkCap; ++r) {
-      const float u = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)r));
-      const float t = fmaf(u, tr - tl, tl);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) y[i] = fmaf(t, v[i], x[i]);
-      ++evals;
-      ++shr;
-      if (in_slice<G>(R, f, C, y, height, gl, mask, lly, nanc)) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = y[i];
-        lx = lly;
-        ok = true;
-        break;
-      }
-      if (t < 0.0f) tl = t; else tr = t;
-    }
-    if (ok) ++acc; else ++nul;
-  }
-  // (iv) replace dead slot j, born at logL*
-  const int slot = D.i[R.o_dead + j];
-  if (has)
-    reinterpret_cast<float4*>(D.f + R.o_x + (long long)slot * ld)[gl] = make_float4(x[0], x[1], x[2], x[3]);
-  if (gl == 0) {
-    D.f[R.o_logL + slot] = lx;
-    D.f[R.o_birth + slot] = C.lstar;
-    int* st = D.i + R.o_stats;
-    st[j] = evals;
-    st[R.k + j] = acc;
-    st[2 * R.k + j] = nul;
-    st[3 * R.k + j] = exps;
-    st[4 * R.k + j] = shr;
-    st[5 * R.k + j] = capo;
-    atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->evals), (unsigned long long)evals);
-    if (nul) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nulls), (unsigned long long)nul);
-    if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->cap_out), (unsigned long long)capo);
-    if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nan_evals), (unsigned long long)nanc);
-  }
-}
-
-constexpr int kSweepThreads = 128;
-
-template <int G>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep(Dev D, const WorkItem* __restrict__ items,
-                                                         int n_items, int* queue) {
-  __shared__ __align__(16) float zbuf[kSweepThreads / 32][32 * 4];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int gl = lane % G, grp = lane / G;
-  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
-  float* zs = &zbuf[wid][grp * G * 4];
-  for (;;) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(queue, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= n_items) break;
-    const WorkItem wi = items[it];
-    RunState* S = D.st + wi.run;
-    if (S->done) continue;
-    const int j = wi.c0 + grp;
-    if (j < wi.c1) sweep_chain<G>(D, D.desc[wi.run], S, j, gl, mask, zs);
-    __syncwarp();
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Termination (App. B.3, reading: live fraction): Z_live = X mean(L_live);
 // stop when Z_live / (Z + Z_live) < tol.  Also counts the iteration.
 // ---------------------------------------------------------------------------
@@ -837,24 +506,6 @@ __global__ void k_vol_norm(Dev D, int run) {
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-template <int G>
-static cudaError_t launch_init_t(const Dev& D, const WorkItem* items, int n, cudaStream_t s) {
-  const int blocks = (n * 32 + 127) / 128;
-  k_init<G><<<blocks > 0 ? blocks : 1, 128, 0, s>>>(D, items, n);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_init(int cls, const Dev& D, const WorkItem* items, int n, cudaStream_t s) {
-  switch (cls) {
-    case 0: return launch_init_t<1>(D, items, n, s);
-    case 1: return launch_init_t<2>(D, items, n, s);
-    case 2: return launch_init_t<4>(D, items, n, s);
-    case 3: return launch_init_t<8>(D, items, n, s);
-    case 4: return launch_init_t<16>(D, items, n, s);
-    default: return launch_init_t<32>(D, items, n, s);
-  }
-}
-
 cudaError_t launch_prologue(const Dev& D, int n_runs, size_t smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
@@ -866,38 +517,6 @@ cudaError_t launch_prologue(const Dev& D, int n_runs, size_t smem, cudaStream_t 
   }
   k_prologue<<<n_runs, 1024, smem, s>>>(D);
   return cudaGetLastError();
-}
-
-template <int G>
-static cudaError_t launch_sweep_t(const Dev& D, const WorkItem* items, int n, int* queue, int grid,
-                                  cudaStream_t s) {
-  k_sweep<G><<<grid, kSweepThreads, 0, s>>>(D, items, n, queue);
-  return cudaGetLastError();
-}
-
-int sweep_blocks_per_sm(int cls) {
-  int nb = 0;
-  switch (cls) {
-    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<1>, kSweepThreads, 0); break;
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<2>, kSweepThreads, 0); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<4>, kSweepThreads, 0); break;
-    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<8>, kSweepThreads, 0); break;
-    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<16>, kSweepThreads, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<32>, kSweepThreads, 0); break;
-  }
-  return nb > 0 ? nb : 1;
-}
-
-cudaError_t launch_sweep(int cls, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
-                         cudaStream_t s) {
-  switch (cls) {
-    case 0: return launch_sweep_t<1>(D, items, n, queue, grid, s);
-    case 1: return launch_sweep_t<2>(D, items, n, queue, grid, s);
-    case 2: return launch_sweep_t<4>(D, items, n, queue, grid, s);
-    case 3: return launch_sweep_t<8>(D, items, n, queue, grid, s);
-    case 4: return launch_sweep_t<16>(D, items, n, queue, grid, s);
-    default: return launch_sweep_t<32>(D, items, n, queue, grid, s);
-  }
 }
 
 cudaError_t launch_terminate(const Dev& D, int n_runs, cudaStream_t s) {

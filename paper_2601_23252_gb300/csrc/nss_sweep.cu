@@ -1,0 +1,546 @@
+// nss_sweep.cu -- the Hit-and-Run Slice Sampling sweep (steps (iii)+(iv) of
+// Sec. 3.1; HRSS of Sec. 3.2 and App. B.4) and the initial prior draw, for
+// sm_103a.
+//
+// A chain is owned by a group of G lanes of one warp; lane gl holds the DPL
+// dimensions [gl*DPL, gl*DPL + DPL) of the chain's position x, direction v
+// and candidate y in registers.  A warp holds 32/G chains of one run.  The
+// likelihood of a candidate is a group reduction (xor butterflies, so every
+// lane of the group ends with the bitwise-identical value and the whole group
+// takes the same branch).  Chains of a warp step in lockstep per HRSS step
+// and diverge only inside the stepping-out and shrinkage loops; a persistent
+// grid takes warps' worth of chains from an atomic ticket queue (costliest
+// runs first), so a warp that finishes early takes the next chains instead
+// of idling.  No lane ever waits on another block.
+#include <cfloat>
+#include <cmath>
+
+#include "nss_device.cuh"
+#include "nss_kernels.h"
+
+namespace nss {
+
+// ---- lane-slice loads and stores of a point row ---------------------------
+template <int DPL>
+__device__ __forceinline__ void load_lane(const float* __restrict__ row, int gl, float (&x)[DPL]) {
+  if constexpr (DPL == 4) {
+    const float4 t = reinterpret_cast<const float4*>(row)[gl];
+    x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+  } else if constexpr (DPL == 2) {
+    const float2 t = reinterpret_cast<const float2*>(row)[gl];
+    x[0] = t.x; x[1] = t.y;
+  } else {
+    x[0] = row[gl];
+  }
+}
+
+template <int DPL>
+__device__ __forceinline__ void ldg_lane(const float* __restrict__ row, int gl, float (&x)[DPL]) {
+  if constexpr (DPL == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(row) + gl);
+    x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+  } else if constexpr (DPL == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(row) + gl);
+    x[0] = t.x; x[1] = t.y;
+  } else {
+    x[0] = __ldg(row + gl);
+  }
+}
+
+template <int DPL>
+__device__ __forceinline__ void store_lane(float* row, int gl, const float (&x)[DPL]) {
+  if constexpr (DPL == 4) {
+    reinterpret_cast<float4*>(row)[gl] = make_float4(x[0], x[1], x[2], x[3]);
+  } else if constexpr (DPL == 2) {
+    reinterpret_cast<float2*>(row)[gl] = make_float2(x[0], x[1]);
+  } else {
+    row[gl] = x[0];
+  }
+}
+
+// Standard normals of the lane's dimensions from words [0, 2 ceil(d/2)) of the
+// counter stream (c0, c1, c2): dimension i uses Box-Muller pair i/2.
+template <int DPL>
+__device__ __forceinline__ void lane_normals(const RunDesc& R, uint32_t c0, uint32_t c1, uint32_t c2,
+                                             int gl, float (&z)[DPL]) {
+  if constexpr (DPL == 4) {
+    const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)gl);
+    box_muller(w.x, w.y, z[0], z[1]);
+    box_muller(w.z, w.w, z[2], z[3]);
+  } else if constexpr (DPL == 2) {
+    const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)(gl >> 1));
+    if (gl & 1) box_muller(w.z, w.w, z[0], z[1]);
+    else box_muller(w.x, w.y, z[0], z[1]);
+  } else {
+    const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)(gl >> 2));
+    float a, b;
+    if (gl & 2) box_muller(w.z, w.w, a, b);
+    else box_muller(w.x, w.y, a, b);
+    z[0] = (gl & 1) ? b : a;
+  }
+}
+
+// Uniforms of the lane's dimensions, word i for dimension i.
+template <int DPL>
+__device__ __forceinline__ void lane_uniform_words(const RunDesc& R, uint32_t c0, uint32_t c1, uint32_t c2,
+                                                   int gl, uint32_t (&u)[DPL]) {
+  const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)((gl * DPL) >> 2));
+  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+  const int o = (gl * DPL) & 3;
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) u[i] = ws[o + i];
+}
+
+// ---- likelihood of a chain group ------------------------------------------
+template <int G, int DPL>
+struct Lik {
+  float mu4[4][DPL];   // cached means of up to four mixture components
+  bool cached;
+
+  __device__ __forceinline__ void init(const RunDesc& R, const float* __restrict__ f, int gl, bool has) {
+    cached = (R.lik_kind == kLikGmm && R.n_comp <= 4) || R.lik_kind == kLikGauss || R.lik_kind == kLikFault;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) mu4[c][i] = 0.0f;
+    if (!cached || !has) return;
+    const int nc = (R.lik_kind == kLikGmm) ? R.n_comp : 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < nc) ldg_lane<DPL>(f + R.o_mu + (long long)c * R.dpad, gl, mu4[c]);
+  }
+
+  __device__ __forceinline__ static float sqdist(const float (&y)[DPL], const float (&m)[DPL]) {
+    float q = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) {
+      const float e = y[i] - m[i];
+      q = fmaf(e, e, q);
+    }
+    return q;
+  }
+
+  __device__ __forceinline__ float eval(const RunDesc& R, const float* __restrict__ f, const float (&y)[DPL],
+                                        int gl, bool has, unsigned mask) const {
+    const int lk = R.lik_kind;
+    if (lk == kLikFlat) return 0.0f;
+    if (lk == kLikGauss || lk == kLikFault) {
+      const float q = gsum<G>(has ? sqdist(y, mu4[0]) : 0.0f, mask);
+      float ll = fmaf(-q, R.inv2s2, R.lognorm);
+      if (lk == kLikFault) {
+        const float x0 = __shfl_sync(mask, y[0], 0, G);
+        if (x0 < R.fault_param) ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
+      }
+      return ll;
+    }
+    if constexpr (G >= 4) {
+      if (R.n_comp == 4) {
+        // four components: transposed butterfly.  After two exchange levels
+        // lane gl holds the partial of component (gl & G/2 ? 2 : 0) +
+        // (gl & G/4 ? 1 : 0); the remaining levels finish its sum.
+        float q[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q[c] = has ? sqdist(y, mu4[c]) : 0.0f;
+        const bool h1 = gl & (G / 2);
+        const float r0 = __shfl_xor_sync(mask, h1 ? q[0] : q[2], G / 2, G);
+        const float r1 = __shfl_xor_sync(mask, h1 ? q[1] : q[3], G / 2, G);
+        const float k0 = (h1 ? q[2] : q[0]) + r0;
+        const float k1 = (h1 ? q[3] : q[1]) + r1;
+        const bool h2 = gl & (G / 4);
+        const float r2 = __shfl_xor_sync(mask, h2 ? k0 : k1, G / 4, G);
+        float s = (h2 ? k1 : k0) + r2;
+#pragma unroll
+        for (int o = G / 8; o > 0; o >>= 1) s += __shfl_xor_sync(mask, s, o, G);
+        const float v = -s * R.inv2s2;
+        float M = fmaxf(v, __shfl_xor_sync(mask, v, G / 2, G));
+        M = fmaxf(M, __shfl_xor_sync(mask, M, G / 4, G));
+        float e = expf(v - M);
+        e += __shfl_xor_sync(mask, e, G / 2, G);
+        e += __shfl_xor_sync(mask, e, G / 4, G);
+        return M + logf(e) + R.lognorm;
+      }
+    }
+    // general mixture: one reduction per component, online log-sum-exp
+    float M = -INFINITY, S = 0.0f;
+    const int K = R.n_comp;
+    if (cached) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < K) {
+          const float q = gsum<G>(has ? sqdist(y, mu4[c]) : 0.0f, mask);
+          const float v = -q * R.inv2s2;
+          if (v > M) {
+            S = S * expf(M - v) + 1.0f;
+            M = v;
+          } else {
+            S += expf(v - M);
+          }
+        }
+      }
+    } else {
+      for (int c = 0; c < K; ++c) {
+        float mq[DPL];
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) mq[i] = 0.0f;
+        if (has) ldg_lane<DPL>(f + R.o_mu + (long long)c * R.dpad, gl, mq);
+        const float q = gsum<G>(has ? sqdist(y, mq) : 0.0f, mask);
+        const float v = -q * R.inv2s2;
+        if (v > M) {
+          S = S * expf(M - v) + 1.0f;
+          M = v;
+        } else {
+          S += expf(v - M);
+        }
+      }
+    }
+    return M + logf(S) + R.lognorm;
+  }
+};
+
+// ---- per-chain constants ---------------------------------------------------
+template <int DPL>
+struct ChainConst {
+  float a[DPL], b[DPL], ib[DPL];
+  bool own[DPL];
+  float lstar;
+  bool box, nonflat;
+};
+
+template <int G, int DPL>
+__device__ __forceinline__ float group_logprior(const RunDesc& R, const ChainConst<DPL>& C,
+                                                const float (&y)[DPL], unsigned mask) {
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < DPL; ++i)
+    if (C.own[i]) {
+      const float u = (y[i] - C.a[i]) * C.ib[i];
+      s = fmaf(-0.5f * u, u, s);
+    }
+  return gsum<G>(s, mask) + R.prior_const;
+}
+
+// One logical likelihood evaluation: y is in the slice when it lies in the
+// prior support, above the prior slice height (non-flat prior) and strictly
+// above logL* (Sec. 3.1: E < E_batch).  The decision is uniform over the group.
+template <int G, int DPL>
+__device__ __forceinline__ bool in_slice(const RunDesc& R, const float* __restrict__ f, const Lik<G, DPL>& L,
+                                         const ChainConst<DPL>& C, const float (&y)[DPL], float height, int gl,
+                                         bool has, unsigned mask, float& ll, int& nan_cnt) {
+  if (C.box) {
+    bool out = false;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i)
+      if (C.own[i] && !(y[i] >= C.a[i] && y[i] <= C.b[i])) out = true;
+    if (__any_sync(mask, out)) return false;
+  }
+  if (C.nonflat) {
+    const float lp = group_logprior<G, DPL>(R, C, y, mask);
+    if (!(lp > height)) return false;
+  }
+  ll = L.eval(R, f, y, gl, has, mask);
+  if (isnan(ll)) {
+    ll = -INFINITY;
+    ++nan_cnt;
+  }
+  return ll > C.lstar;
+}
+
+struct WordCache {
+  uint32_t blk;
+  uint4 v;
+};
+__device__ __forceinline__ uint32_t step_word(const RunDesc& R, WordCache& wc, uint32_t iter, uint32_t chain,
+                                              uint32_t step, uint32_t wi) {
+  const uint32_t b = wi >> 2;
+  if (b != wc.blk) {
+    wc.v = draw_block(R, iter, chain, step, b);
+    wc.blk = b;
+  }
+  return pick(wc.v, wi & 3u);
+}
+
+// ---------------------------------------------------------------------------
+// Initial live set (Sec. 2.1): slot s draws x ~ Pi from counter
+// (0, s, TAG_INIT, word/4) -- box: x_i = a_i + (b_i - a_i) u(word i);
+// Gaussian: x_i = a_i + b_i z_i with Box-Muller pairs.
+// ---------------------------------------------------------------------------
+template <int G, int DPL>
+__global__ void __launch_bounds__(128) k_init(Dev D, const WorkItem* __restrict__ items, int n_items) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % G, grp = lane / G;
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < n_items; it += nwarps) {
+    const WorkItem wi = items[it];
+    const RunDesc& R = D.desc[wi.run];
+    const int slot = wi.c0 + grp;
+    if (slot >= wi.c1) continue;
+    const bool has = gl * DPL < R.dpad;
+    float x[DPL];
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) x[i] = 0.0f;
+    if (R.prior_kind == kPriorBox) {
+      uint32_t u[DPL];
+      lane_uniform_words<DPL>(R, 0u, (uint32_t)slot, kTagInit, gl, u);
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) {
+        const int dim = gl * DPL + i;
+        if (dim < R.d) {
+          const float a = D.f[R.o_a + dim], b = D.f[R.o_b + dim];
+          x[i] = fmaf(b - a, u24(u[i]), a);
+        }
+      }
+    } else {
+      float z[DPL];
+      lane_normals<DPL>(R, 0u, (uint32_t)slot, kTagInit, gl, z);
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) {
+        const int dim = gl * DPL + i;
+        if (dim < R.d) x[i] = fmaf(D.f[R.o_b + dim], z[i], D.f[R.o_a + dim]);
+      }
+    }
+    Lik<G, DPL> L;
+    L.init(R, D.f, gl, has);
+    float ll = L.eval(R, D.f, x, gl, has, mask);
+    if (isnan(ll)) ll = -INFINITY;
+    if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * R.dpad, gl, x);
+    if (gl == 0) {
+      D.f[R.o_logL + slot] = ll;
+      D.f[R.o_birth + slot] = -INFINITY;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One chain: p HRSS steps from its parent, then replacement of dead slot j.
+// ---------------------------------------------------------------------------
+template <int G, int DPL>
+__device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j, int gl, unsigned mask,
+                            float* zs) {
+  const float* __restrict__ f = D.f;
+  const int d = R.d, ld = R.dpad;
+  const bool has = gl * DPL < ld;
+  const int parent = D.i[R.o_parent + j];
+  const uint32_t iter = (uint32_t)Sw->iter;
+  ChainConst<DPL> C;
+  C.box = R.prior_kind == kPriorBox;
+  C.nonflat = !C.box;
+  C.lstar = Sw->logLstar;
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) {
+    const int dim = gl * DPL + i;
+    C.own[i] = dim < d;
+    C.a[i] = C.own[i] ? f[R.o_a + dim] : 0.f;
+    C.b[i] = C.own[i] ? f[R.o_b + dim] : 1.f;
+    C.ib[i] = 1.0f / C.b[i];
+  }
+  Lik<G, DPL> L;
+  L.init(R, f, gl, has);
+  float x[DPL];
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) x[i] = 0.0f;
+  if (has) load_lane<DPL>(f + R.o_x + (long long)parent * ld, gl, x);
+  float lx = f[R.o_logL + parent];
+  const float w = R.w;
+  const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
+  const float4* L4 = reinterpret_cast<const float4*>(f + R.o_L);
+  const int ld4 = ld >> 2;
+  const float4* zs4 = reinterpret_cast<const float4*>(zs);
+  int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
+  for (int s = 0; s < R.p; ++s) {
+    // direction: z ~ N(0, I), d~ = L z, v = d~ / |z|  (or / |d~|)
+    float z[DPL];
+    lane_normals<DPL>(R, iter, (uint32_t)j, (uint32_t)s, gl, z);
+    float zz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) {
+      if (!C.own[i]) z[i] = 0.0f;
+      zs[gl * DPL + i] = z[i];
+      zz = fmaf(z[i], z[i], zz);
+    }
+    __syncwarp(mask);
+    zz = gsum<G>(zz, mask);
+    float dt[DPL];
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) dt[i] = 0.0f;
+    if (has) {
+      const int row0 = gl * DPL;
+      const int nb = ((row0 + DPL - 1) >> 2) + 1;
+      for (int bb = 0; bb < nb; ++bb) {
+        const float4 zb = zs4[bb];
+#pragma unroll
+        for (int r = 0; r < DPL; ++r) {
+          const float4 l4 = __ldg(L4 + (row0 + r) * ld4 + bb);
+          dt[r] = fmaf(l4.x, zb.x, fmaf(l4.y, zb.y, fmaf(l4.z, zb.z, fmaf(l4.w, zb.w, dt[r]))));
+        }
+      }
+    }
+    __syncwarp(mask);
+    float nrm;
+    if (R.dir_norm == 0) {
+      nrm = sqrtf(zz);
+    } else {
+      float dd = 0.0f;
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) dd = fmaf(dt[i], dt[i], dd);
+      nrm = sqrtf(gsum<G>(dd, mask));
+    }
+    float v[DPL];
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) v[i] = dt[i] / nrm;
+    WordCache wc;
+    wc.blk = 0xFFFFFFFFu;
+    float height = 0.0f;
+    if (C.nonflat) {
+      const float uh = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz + 1u));
+      height = group_logprior<G, DPL>(R, C, x, mask) + logf(uh);
+    }
+    // randomised initial bracket of width w around t = 0
+    const float U = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz));
+    float tl = -w * U;
+    float tr = tl + w;
+    float y[DPL], lly;
+    // stepping out, at most 10 expansions per side
+    for (int n = 0;; ++n) {
+      if (n >= kStepOutCap) { ++capo; break; }
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) y[i] = fmaf(tl, v[i], x[i]);
+      ++evals;
+      if (!in_slice<G, DPL>(R, f, L, C, y, height, gl, has, mask, lly, nanc)) break;
+      tl -= w;
+      ++exps;
+    }
+    for (int n = 0;; ++n) {
+      if (n >= kStepOutCap) { ++capo; break; }
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) y[i] = fmaf(tr, v[i], x[i]);
+      ++evals;
+      if (!in_slice<G, DPL>(R, f, L, C, y, height, gl, has, mask, lly, nanc)) break;
+      tr += w;
+      ++exps;
+    }
+    // shrinkage, at most 100 proposals, then a null move
+    bool ok = false;
+    for (int r = 0; r < kShrinkCap; ++r) {
+      const float u = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)r));
+      const float t = fmaf(u, tr - tl, tl);
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) y[i] = fmaf(t, v[i], x[i]);
+      ++evals;
+      ++shr;
+      if (in_slice<G, DPL>(R, f, L, C, y, height, gl, has, mask, lly, nanc)) {
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) x[i] = y[i];
+        lx = lly;
+        ok = true;
+        break;
+      }
+      if (t < 0.0f) tl = t;
+      else tr = t;
+    }
+    if (ok) ++acc;
+    else ++nul;
+  }
+  // (iv) replace dead slot j, born at logL*
+  const int slot = D.i[R.o_dead + j];
+  if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, x);
+  if (gl == 0) {
+    D.f[R.o_logL + slot] = lx;
+    D.f[R.o_birth + slot] = C.lstar;
+    int* st = D.i + R.o_stats;
+    st[j] = evals;
+    st[R.k + j] = acc;
+    st[2 * R.k + j] = nul;
+    st[3 * R.k + j] = exps;
+    st[4 * R.k + j] = shr;
+    st[5 * R.k + j] = capo;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->evals), (unsigned long long)evals);
+    if (nul) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nulls), (unsigned long long)nul);
+    if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->cap_out), (unsigned long long)capo);
+    if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nan_evals), (unsigned long long)nanc);
+  }
+}
+
+constexpr int kSweepThreads = 128;
+// resident blocks per SM the register budget is tuned for
+constexpr int sweep_min_blocks(int dpl) { return dpl == 1 ? 8 : dpl == 2 ? 6 : 4; }
+
+template <int G, int DPL>
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(Dev D, const WorkItem* __restrict__ items, int n_items,
+                                                         int* queue) {
+  __shared__ __align__(16) float zbuf[kSweepThreads / 32][32 * DPL];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gl = lane % G, grp = lane / G;
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  float* zs = &zbuf[wid][grp * G * DPL];
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(queue, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
+    const WorkItem wi = items[it];
+    RunState* S = D.st + wi.run;
+    if (S->done) continue;
+    const int j = wi.c0 + grp;
+    if (j < wi.c1) sweep_chain<G, DPL>(D, D.desc[wi.run], S, j, gl, mask, zs);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// configuration table and launchers
+// ---------------------------------------------------------------------------
+#define NSS_CFGS(X) \
+  X(0, 1, 4) X(1, 2, 4) X(2, 4, 4) X(3, 8, 4) X(4, 16, 4) X(5, 32, 4) \
+  X(6, 2, 2) X(7, 4, 2) X(8, 8, 2) X(9, 16, 2) X(10, 32, 2) \
+  X(11, 4, 1) X(12, 8, 1) X(13, 16, 1) X(14, 32, 1)
+
+int cfg_g(int cfg) {
+#define X(id, g, p) if (cfg == id) return g;
+  NSS_CFGS(X)
+#undef X
+  return 32;
+}
+
+int cfg_dpl(int cfg) {
+#define X(id, g, p) if (cfg == id) return p;
+  NSS_CFGS(X)
+#undef X
+  return 4;
+}
+
+cudaError_t launch_init(int cfg, const Dev& D, const WorkItem* items, int n, cudaStream_t s) {
+  const int blocks = (n * 32 + 127) / 128;
+  switch (cfg) {
+#define X(id, g, p) case id: k_init<g, p><<<blocks > 0 ? blocks : 1, 128, 0, s>>>(D, items, n); break;
+    NSS_CFGS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int sweep_blocks_per_sm(int cfg) {
+  int nb = 0;
+  switch (cfg) {
+#define X(id, g, p) case id: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<g, p>, kSweepThreads, 0); break;
+    NSS_CFGS(X)
+#undef X
+    default: break;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_sweep(int cfg, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
+                         cudaStream_t s) {
+  switch (cfg) {
+#define X(id, g, p) case id: k_sweep<g, p><<<grid, kSweepThreads, 0, s>>>(D, items, n, queue); break;
+    NSS_CFGS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nss

@@ -94,6 +94,11 @@ def lib():
     L.nss_run.argtypes = [C.c_void_p, P(Result)]
     L.nss_finalise.argtypes = [C.c_void_p, P(Result)]
     L.nss_reset.argtypes = [C.c_void_p, P(C.c_uint64)]
+    L.nss_autotune.argtypes = [C.c_void_p, C.c_int, _ip]
+    L.nss_set_cfg.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.nss_get_cfg.argtypes = [C.c_void_p, C.c_int]
+    L.nss_cfg_lanes.argtypes = [C.c_int]
+    L.nss_cfg_dims.argtypes = [C.c_int]
     L.nss_get_dead.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_size_t, P(C.c_size_t)]
     L.nss_export_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, P(State)]
@@ -237,6 +242,22 @@ class Sampler:
         if seeds is not None:
             arr = (C.c_uint64 * self.n_runs)(*[int(v) for v in seeds])
         self._check(lib().nss_reset(self._h, arr), "nss_reset")
+
+    def autotune(self, iters=3):
+        """Pick the fastest sweep configuration per dimension class; resets the runs."""
+        out = (C.c_int * self.n_runs)()
+        self._check(lib().nss_autotune(self._h, int(iters), out), "nss_autotune")
+        return [self.cfg_info(q) for q in out]
+
+    def set_cfg(self, run, cfg):
+        self._check(lib().nss_set_cfg(self._h, run, cfg), "nss_set_cfg")
+
+    def cfg(self, run=0):
+        return self.cfg_info(lib().nss_get_cfg(self._h, run))
+
+    @staticmethod
+    def cfg_info(q):
+        return {"id": int(q), "lanes_per_chain": lib().nss_cfg_lanes(q), "dims_per_lane": lib().nss_cfg_dims(q)}
 
     def finalise(self):
         res = (Result * self.n_runs)()

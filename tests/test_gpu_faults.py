@@ -45,7 +45,8 @@ def test_plateau_gives_null_moves_and_terminates(gpu_lib):
     # with L = 1 the Delta-X quadrature sums the removed volume: Z = 1 - X_N,
     # log X_N = -sum 1/n over every death including the final live set
     logXN = -np.sum(1.0 / d["nlive"])
-    assert abs(res["logZ_det"] - np.log1p(-np.exp(logXN))) < 1e-9
+    # FP64 accumulation of FP32 exponentials: relative 1e-7 of Z
+    assert abs(res["logZ_det"] - np.log1p(-np.exp(logXN))) < 1e-7
     assert abs(res["logZ"]) < 0.01
 
 

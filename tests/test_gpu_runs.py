@@ -58,8 +58,9 @@ def test_gmm_d32_twenty_seeds_against_checker(gpu_lib):
     diff = lz - lo
     print(f"\ngmm_d32: gpu mean dev from closed form {np.mean(lz - truth):+.4f}, checker {np.mean(lo - truth):+.4f}; "
           f"paired gpu-checker mean {diff.mean():+.4f} sd {diff.std(ddof=1):.4f}, max |d|/err {np.max(np.abs(diff) / err):.2f}")
-    # each GPU run within 3 of its own reported error of the checker's run of the same seed
-    assert np.all(np.abs(diff) < 3.0 * err)
+    # each GPU run within 3 combined reported errors of the checker's run of
+    # the same seed (the two runs decorrelate after their first near-tie)
+    assert np.all(np.abs(diff) < 3.0 * np.sqrt(err**2 + eo**2))
     # 20-seed means agree within three standard errors of the paired difference
     assert abs(diff.mean()) < 3.0 * diff.std(ddof=1) / np.sqrt(20) + 1e-3
     # same mean bias relative to the closed form on both sides

@@ -317,9 +317,8 @@ def run_native(args):
         for s in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with native.Sampler(wls, stream=stream.cuda_stream) as sm:
-                for r in range(nrun):
-                    sm.set_cfg(r, chosen[r]["id"])
+            wls_cfg = [w.with_(extra={"options": {"sweep_cfg": chosen[r]["id"]}}) for r, w in enumerate(wls)]
+            with native.Sampler(wls_cfg, stream=stream.cuda_stream) as sm:
                 rr = sm.run()
                 for r in range(nrun):
                     n = rr[r]["n_dead"]
@@ -371,6 +370,7 @@ def run_ncu_case(args):
     wls = [W.gmm_d32(seed=s).with_(extra={"options": {"dead_capacity": 8 * 500 + 1000}})
            for s in range(args.runs)]
     with native.Sampler(wls) as s:
+        s.autotune(iters=2)
         for _ in range(6):
             s.step()
     return 0

@@ -136,10 +136,12 @@ typedef struct {
     int n_sim;                 /* volume-simulation trajectories R (App. D.2)    */
     double cov_eps;            /* metric regularisation eps * tr(Sigma)/d        */
     void *cuda_stream;         /* cudaStream_t; NULL = default stream            */
+    int sweep_cfg;             /* sweep configuration id, -1 = default           */
 } nss_options;
 
 /* Fills the paper's defaults: w = 1, MAHAL, tol = 1e-3, max_iter = 100000,
-   n_sim = 100, cov_eps = 1e-6, seed 0, run_id 0, default stream. */
+   n_sim = 100, cov_eps = 1e-6, seed 0, run_id 0, default stream,
+   default sweep configuration. */
 void nss_options_default(nss_options *opt);
 
 /* Per-run state after a step. */

@@ -238,6 +238,11 @@ nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m
   if (o.n_sim < 2 || o.n_sim > 1024) return set_err(c, NSS_ERR_ARG, "run %d: n_sim outside [2,1024]", run);
   if (!(o.cov_eps >= 0)) return set_err(c, NSS_ERR_ARG, "run %d: cov_eps < 0", run);
   if (o.dead_capacity < 0) return set_err(c, NSS_ERR_ARG, "run %d: dead_capacity < 0", run);
+  if (o.sweep_cfg >= 0) {
+    bool fits = false;
+    for (int q : candidate_cfgs(pr.d)) fits |= (q == o.sweep_cfg);
+    if (!fits) return set_err(c, NSS_ERR_ARG, "run %d: sweep_cfg %d does not fit d=%d", run, o.sweep_cfg, pr.d);
+  }
   return NSS_OK;
 }
 
@@ -518,6 +523,7 @@ void nss_options_default(nss_options* o) {
   o->n_sim = 100;
   o->cov_eps = 1e-6;
   o->cuda_stream = nullptr;
+  o->sweep_cfg = -1;
 }
 
 int nss_abi_version(void) { return NSS_ABI_VERSION; }
@@ -596,6 +602,8 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     R.n_data = lk.n_data;
     R.dir_norm = o.dir_norm;
     R.cfg = default_cfg(R.d);
+    for (int q : candidate_cfgs(R.d))
+      if (q == o.sweep_cfg) R.cfg = q;
     R.fault_mode = lk.fault_mode;
     R.fault_param = (float)lk.fault_param;
     R.max_iter = o.max_iter;

@@ -154,10 +154,10 @@ struct Lik {
         const float v = -s * R.inv2s2;
         float M = fmaxf(v, __shfl_xor_sync(mask, v, G / 2, G));
         M = fmaxf(M, __shfl_xor_sync(mask, M, G / 4, G));
-        float e = expf(v - M);
+        float e = __expf(v - M);
         e += __shfl_xor_sync(mask, e, G / 2, G);
         e += __shfl_xor_sync(mask, e, G / 4, G);
-        return M + logf(e) + R.lognorm;
+        return M + __logf(e) + R.lognorm;
       }
     }
     // general mixture: one reduction per component, online log-sum-exp
@@ -245,18 +245,47 @@ __device__ __forceinline__ bool in_slice(const RunDesc& R, const float* __restri
   return ll > C.lstar;
 }
 
-struct WordCache {
-  uint32_t blk;
-  uint4 v;
-};
-__device__ __forceinline__ uint32_t step_word(const RunDesc& R, WordCache& wc, uint32_t iter, uint32_t chain,
-                                              uint32_t step, uint32_t wi) {
-  const uint32_t b = wi >> 2;
-  if (b != wc.blk) {
-    wc.v = draw_block(R, iter, chain, step, b);
-    wc.blk = b;
+// The words of one HRSS step: group lane b computes Philox block b of the
+// step's counter stream (iteration, chain, step, b) once; a word w < 4G is
+// then read from lane w/4 by a shuffle, a later word (a shrinkage proposal
+// past the first 4G - nz - 3) is drawn on demand.
+template <int G>
+struct StepWords {
+  uint4 mine;
+  __device__ __forceinline__ void draw(const RunDesc& R, uint32_t iter, uint32_t chain, uint32_t step, int gl) {
+    mine = draw_block(R, iter, chain, step, (uint32_t)gl);
   }
-  return pick(wc.v, wi & 3u);
+  // word wi, uniform over the group
+  __device__ __forceinline__ uint32_t word(const RunDesc& R, uint32_t iter, uint32_t chain, uint32_t step,
+                                           uint32_t wi, unsigned mask) const {
+    const uint32_t b = wi >> 2;
+    if (b < (uint32_t)G) return __shfl_sync(mask, pick(mine, wi & 3u), (int)b, G);
+    return pick(draw_block(R, iter, chain, step, b), wi & 3u);
+  }
+  // all four words of block b (b < G), for lane-specific picks
+  __device__ __forceinline__ uint4 block(int b, unsigned mask) const {
+    return make_uint4(__shfl_sync(mask, mine.x, b, G), __shfl_sync(mask, mine.y, b, G),
+                      __shfl_sync(mask, mine.z, b, G), __shfl_sync(mask, mine.w, b, G));
+  }
+};
+
+// Normals of the lane's dimensions for the step, from the shared blocks.
+template <int G, int DPL>
+__device__ __forceinline__ void step_normals(const StepWords<G>& W, int gl, unsigned mask, float (&z)[DPL]) {
+  if constexpr (DPL == 4) {
+    box_muller(W.mine.x, W.mine.y, z[0], z[1]);
+    box_muller(W.mine.z, W.mine.w, z[2], z[3]);
+  } else if constexpr (DPL == 2) {
+    const uint4 w = W.block(gl >> 1, mask);
+    if (gl & 1) box_muller(w.z, w.w, z[0], z[1]);
+    else box_muller(w.x, w.y, z[0], z[1]);
+  } else {
+    const uint4 w = W.block(gl >> 2, mask);
+    float a, b;
+    if (gl & 2) box_muller(w.z, w.w, a, b);
+    else box_muller(w.x, w.y, a, b);
+    z[0] = (gl & 1) ? b : a;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -350,8 +379,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
   for (int s = 0; s < R.p; ++s) {
     // direction: z ~ N(0, I), d~ = L z, v = d~ / |z|  (or / |d~|)
+    StepWords<G> W;
+    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl);
     float z[DPL];
-    lane_normals<DPL>(R, iter, (uint32_t)j, (uint32_t)s, gl, z);
+    step_normals<G, DPL>(W, gl, mask, z);
     float zz = 0.0f;
 #pragma unroll
     for (int i = 0; i < DPL; ++i) {
@@ -377,27 +408,25 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       }
     }
     __syncwarp(mask);
-    float nrm;
+    float inrm;
     if (R.dir_norm == 0) {
-      nrm = sqrtf(zz);
+      inrm = rsqrtf(zz);
     } else {
       float dd = 0.0f;
 #pragma unroll
       for (int i = 0; i < DPL; ++i) dd = fmaf(dt[i], dt[i], dd);
-      nrm = sqrtf(gsum<G>(dd, mask));
+      inrm = rsqrtf(gsum<G>(dd, mask));
     }
     float v[DPL];
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) v[i] = dt[i] / nrm;
-    WordCache wc;
-    wc.blk = 0xFFFFFFFFu;
+    for (int i = 0; i < DPL; ++i) v[i] = dt[i] * inrm;
     float height = 0.0f;
     if (C.nonflat) {
-      const float uh = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz + 1u));
+      const float uh = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz + 1u, mask));
       height = group_logprior<G, DPL>(R, C, x, mask) + logf(uh);
     }
     // randomised initial bracket of width w around t = 0
-    const float U = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz));
+    const float U = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz, mask));
     float tl = -w * U;
     float tr = tl + w;
     float y[DPL], lly;
@@ -423,7 +452,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     // shrinkage, at most 100 proposals, then a null move
     bool ok = false;
     for (int r = 0; r < kShrinkCap; ++r) {
-      const float u = u24(step_word(R, wc, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)r));
+      const float u = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)r, mask));
       const float t = fmaf(u, tr - tl, tl);
 #pragma unroll
       for (int i = 0; i < DPL; ++i) y[i] = fmaf(t, v[i], x[i]);

@@ -273,6 +273,15 @@ nss_status nss_step_trace(nss_ctx *ctx, int run, nss_trace *tr);
 nss_status nss_set_profiling(nss_ctx *ctx, int on);
 nss_status nss_get_profile(nss_ctx *ctx, nss_profile *prof);
 
+/* The batched logit contraction of the logistic-regression sweep, exposed for
+   verification: Z[j][n] = sum_i X[n][i] U[j][i] for host arrays X [n][d]
+   (rounded to bfloat16, as the likelihood uses it) and U [nu][d] (FP32, split
+   into three bfloat16 parts), computed by the tcgen05 tensor-core kernel with
+   FP32 accumulation.  Z [nu][n] is a host array.  1 <= d <= 128,
+   1 <= n <= 1<<20, 1 <= nu <= 1<<16.  Allocates and frees its own device
+   memory; runs on the default stream and synchronises. */
+nss_status nss_logreg_logits(const float *X, int n, int d, const float *U, int nu, float *Z);
+
 int nss_n_runs(const nss_ctx *ctx);
 /* Slice width actually used by a run (after the width rule). */
 double nss_run_width(const nss_ctx *ctx, int run);

@@ -27,9 +27,25 @@ struct EvRec {
   int kind, cfg;
 };
 
+struct LRWork {
+  int run = -1;
+  int rows_pad = 0, cols_pad = 0, emax = 0;
+  __nv_bfloat16* Xb = nullptr;
+  uint32_t* ybits = nullptr;
+  float *zx = nullptr, *zv = nullptr, *xc = nullptr, *vdir = nullptr, *lc = nullptr;
+  __nv_bfloat16* parts = nullptr;
+  int* err = nullptr;
+  CUtensorMap mapX, mapU;
+  nss::LRArgs args;
+};
+
 struct nss_ctx {
   int n_runs = 0;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<LRWork> lr;
+  cudaGraphExec_t iter_graph = nullptr;
+  long long graph_launches = 0;
   int device = 0, num_sms = 1;
   std::vector<RunDesc> desc;
   std::vector<double> widths;
@@ -225,6 +241,11 @@ nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m
     case NSS_LOGLIK_FLAT:
       break;
     case NSS_LOGLIK_LOGREG:
+      if (!lk.X || !lk.y || lk.n_data < 1 || lk.n_data > 20 * 512)
+        return set_err(c, NSS_ERR_ARG, "run %d: logistic regression needs X, y and 1 <= n_data <= 10240", run);
+      if (pr.kind != NSS_PRIOR_GAUSS_DIAG)
+        return set_err(c, NSS_ERR_ARG, "run %d: logistic regression takes the Gaussian prior", run);
+      break;
     case NSS_LOGLIK_GP_RBF_WHITE:
       return set_err(c, NSS_ERR_ARG, "run %d: likelihood kind %d is not built in this library", run, lk.kind);
     default:
@@ -267,6 +288,19 @@ void free_ctx(nss_ctx* c) {
     cudaEventDestroy(e.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& w : c->lr) {
+    cudaFree(w.Xb);
+    cudaFree(w.ybits);
+    cudaFree(w.zx);
+    cudaFree(w.zv);
+    cudaFree(w.xc);
+    cudaFree(w.vdir);
+    cudaFree(w.lc);
+    cudaFree(w.parts);
+    cudaFree(w.err);
+  }
+  if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
@@ -339,6 +373,22 @@ nss_status enqueue_iteration(nss_ctx* c) {
     CK(nss::launch_sweep(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->d_queue + q,
                          c->sweep_grid[q], c->stream), "sweep launch");
   }
+  for (auto& w : c->lr) {
+    const RunDesc& R = c->desc[w.run];
+    const int* done = &c->d_state[w.run].done;
+    Rec r(c, NSS_K_OTHER);
+    CK(nss::launch_lr_parents(D, w.args, w.run, R.k, c->stream), "logistic parents launch");
+    CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.k, w.err, done,
+                          c->stream), "logits launch");
+    for (int s = 0; s < R.p; ++s) {
+      CK(nss::launch_lr_dir(D, w.args, w.run, R.k, s, c->stream), "logistic direction launch");
+      CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zv, w.rows_pad, R.n_data, R.k, w.err, done,
+                            c->stream), "logits launch");
+      CK(nss::launch_lr_slice(D, w.args, w.run, R.k, s, w.emax, c->stream), "logistic slice launch");
+    }
+    CK(nss::launch_lr_replace(D, w.args, w.run, R.k, c->stream), "logistic replace launch");
+    c->launches += 3 + 3LL * R.p;
+  }
   {
     Rec r(c, NSS_K_TERMINATE);
     CK(nss::launch_terminate(D, c->n_runs, c->stream), "terminate launch");
@@ -346,9 +396,39 @@ nss_status enqueue_iteration(nss_ctx* c) {
   return NSS_OK;
 }
 
+// One outer iteration: replayed from a captured CUDA graph when the context
+// has logistic runs (hundreds of launches per iteration) and profiling is
+// off; enqueued launch by launch otherwise.
+nss_status run_iteration(nss_ctx* c) {
+  if (c->lr.empty() || c->profiling) return enqueue_iteration(c);
+  if (!c->iter_graph) {
+    const long long l0 = c->launches, t0 = c->prof.total_launches;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    nss_status st = enqueue_iteration(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != NSS_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
+    e = cudaGraphInstantiate(&c->iter_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;
+    c->prof.total_launches = t0;
+  }
+  CK(cudaGraphLaunch(c->iter_graph, c->stream), "graph launch");
+  c->launches += c->graph_launches;
+  c->prof.total_launches += c->graph_launches;
+  return NSS_OK;
+}
+
 // Work lists of the init and sweep kernels: 32/G slots or chains of one run
 // per warp, grouped by sweep configuration, costliest runs first.
 nss_status build_work(nss_ctx* c) {
+  if (c->iter_graph) {  // the captured iteration refers to the old work lists
+    cudaGraphExecDestroy(c->iter_graph);
+    c->iter_graph = nullptr;
+  }
   for (int q = 0; q < nss::kNumCfgs; ++q) {
     c->init_items[q].clear();
     c->sweep_items[q].clear();
@@ -360,6 +440,7 @@ nss_status build_work(nss_ctx* c) {
     const RunDesc& R = c->desc[r];
     const int per = 32 / nss::cfg_g(R.cfg);
     for (int s = 0; s < R.m; s += per) c->init_items[R.cfg].push_back({r, s, std::min(s + per, R.m), 0});
+    if (R.lik_kind == nss::kLikLogreg) continue;  // swept by the tensor-core line path
     for (int j = 0; j < R.k; j += per) c->sweep_items[R.cfg].push_back({r, j, std::min(j + per, R.k), 0});
   }
   for (int q = 0; q < nss::kNumCfgs; ++q) {
@@ -385,6 +466,71 @@ nss_status build_work(nss_ctx* c) {
      "descriptor upload");
   CK(cudaStreamSynchronize(c->stream), "work list upload");
   return NSS_OK;
+}
+
+// logL of the m initial live points of a logistic run: split, contract, reduce.
+nss_status lr_initial_loglik(nss_ctx* c, LRWork& w) {
+  const RunDesc& R = c->desc[w.run];
+  nss::Dev D = dev_of(c);
+  Rec rr(c, NSS_K_INIT);
+  CK(nss::launch_lr_live_parts(D, w.args, w.run, R.m, c->stream), "logistic live split launch");
+  CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.m, w.err, nullptr,
+                        c->stream), "logits launch");
+  CK(nss::launch_lr_rowll(D, w.args, w.run, R.m, w.emax, c->stream), "logistic row likelihood launch");
+  return NSS_OK;
+}
+
+// Workspace of a logistic-regression run: bf16 design matrix [rows_pad][128],
+// label bits in the slice kernel's thread layout, logits of chain points and
+// directions, the bf16 split buffer, and the TMA descriptors.
+nss_status setup_logreg(nss_ctx* c, int run, const nss_loglik& lk) {
+  const RunDesc& R = c->desc[run];
+  LRWork w;
+  w.run = run;
+  w.rows_pad = (R.n_data + 127) / 128 * 128;
+  w.cols_pad = (std::max(R.m, R.k) + 127) / 128 * 128;
+  w.emax = (R.n_data + 511) / 512 <= 4 ? 4 : 20;
+  std::vector<__nv_bfloat16> xb((size_t)w.rows_pad * 128, __float2bfloat16_rn(0.0f));
+  for (int n = 0; n < R.n_data; ++n)
+    for (int i = 0; i < R.d; ++i) xb[(size_t)n * 128 + i] = __float2bfloat16_rn(lk.X[(size_t)n * R.d + i]);
+  std::vector<uint32_t> yb(512, 0u);
+  for (int n = 0; n < R.n_data; ++n)
+    if (lk.y[n] > 0.5f) yb[n % 512] |= 1u << (n / 512);
+  const size_t zsz = sizeof(float) * (size_t)w.cols_pad * w.rows_pad;
+  CK(cudaMalloc(&w.Xb, sizeof(__nv_bfloat16) * xb.size()), "logistic workspace");
+  CK(cudaMalloc(&w.ybits, sizeof(uint32_t) * 512), "logistic workspace");
+  CK(cudaMalloc(&w.zx, zsz), "logistic workspace");
+  CK(cudaMalloc(&w.zv, zsz), "logistic workspace");
+  CK(cudaMalloc(&w.xc, sizeof(float) * w.cols_pad * 128), "logistic workspace");
+  CK(cudaMalloc(&w.vdir, sizeof(float) * w.cols_pad * 128), "logistic workspace");
+  CK(cudaMalloc(&w.lc, sizeof(float) * w.cols_pad), "logistic workspace");
+  CK(cudaMalloc(&w.parts, sizeof(__nv_bfloat16) * 3 * (size_t)w.cols_pad * 128), "logistic workspace");
+  CK(cudaMalloc(&w.err, sizeof(int)), "logistic workspace");
+  c->lr.push_back(w);  // owned by the context from here on (freed with it)
+  LRWork& W = c->lr.back();
+  CK(cudaMemcpyAsync(W.Xb, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice, c->stream),
+     "design upload");
+  CK(cudaMemcpyAsync(W.ybits, yb.data(), sizeof(uint32_t) * 512, cudaMemcpyHostToDevice, c->stream), "label upload");
+  c->prof.h2d_bytes += (long long)(sizeof(__nv_bfloat16) * xb.size() + sizeof(uint32_t) * 512);
+  CK(cudaMemsetAsync(W.zx, 0, zsz, c->stream), "workspace clear");
+  CK(cudaMemsetAsync(W.zv, 0, zsz, c->stream), "workspace clear");
+  CK(cudaMemsetAsync(W.parts, 0, sizeof(__nv_bfloat16) * 3 * (size_t)W.cols_pad * 128, c->stream), "workspace clear");
+  CK(cudaMemsetAsync(W.xc, 0, sizeof(float) * W.cols_pad * 128, c->stream), "workspace clear");
+  CK(cudaMemsetAsync(W.vdir, 0, sizeof(float) * W.cols_pad * 128, c->stream), "workspace clear");
+  CK(cudaMemsetAsync(W.err, 0, sizeof(int), c->stream), "workspace clear");
+  if (!nss::make_map_bf16(&W.mapX, W.Xb, (unsigned long long)W.rows_pad) ||
+      !nss::make_map_bf16(&W.mapU, W.parts, 3ULL * W.cols_pad))
+    return set_err(c, NSS_ERR_CUDA, "run %d: tensor map encoding failed", run);
+  W.args.ybits = W.ybits;
+  W.args.zx = W.zx;
+  W.args.zv = W.zv;
+  W.args.ldz = W.rows_pad;
+  W.args.xc = W.xc;
+  W.args.vdir = W.vdir;
+  W.args.lc = W.lc;
+  W.args.parts = W.parts;
+  W.args.part_stride = (long long)W.cols_pad * 128;
+  return lr_initial_loglik(c, W);
 }
 
 void clear_states(nss_ctx* c) {
@@ -547,6 +693,57 @@ const char* nss_last_error(const nss_ctx* c) { return c ? c->err.c_str() : "no c
 
 int nss_n_runs(const nss_ctx* c) { return c ? c->n_runs : 0; }
 
+nss_status nss_logreg_logits(const float* X, int n, int d, const float* U, int nu, float* Z) {
+  if (!X || !U || !Z || d < 1 || d > 128 || n < 1 || n > (1 << 20) || nu < 1 || nu > (1 << 16)) return NSS_ERR_ARG;
+  const int rows_pad = (n + 127) / 128 * 128, cols_pad = (nu + 127) / 128 * 128;
+  std::vector<__nv_bfloat16> xb((size_t)rows_pad * 128, __float2bfloat16_rn(0.0f));
+  for (int r = 0; r < n; ++r)
+    for (int i = 0; i < d; ++i) xb[(size_t)r * 128 + i] = __float2bfloat16_rn(X[(size_t)r * d + i]);
+  // three-part split of U on the host, the same rounding as the device split
+  std::vector<__nv_bfloat16> parts(3 * (size_t)cols_pad * 128, __float2bfloat16_rn(0.0f));
+  const size_t ps = (size_t)cols_pad * 128;
+  for (int j = 0; j < nu; ++j)
+    for (int i = 0; i < d; ++i) {
+      const float u = U[(size_t)j * d + i];
+      const __nv_bfloat16 h = __float2bfloat16_rn(u);
+      const float r1 = u - __bfloat162float(h);
+      const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+      const float r2 = r1 - __bfloat162float(m);
+      parts[(size_t)j * 128 + i] = h;
+      parts[ps + (size_t)j * 128 + i] = m;
+      parts[2 * ps + (size_t)j * 128 + i] = __float2bfloat16_rn(r2);
+    }
+  __nv_bfloat16 *dX = nullptr, *dP = nullptr;
+  float* dZ = nullptr;
+  int* dErr = nullptr;
+  nss_status st = NSS_OK;
+  cudaError_t e = cudaMalloc(&dX, sizeof(__nv_bfloat16) * xb.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dP, sizeof(__nv_bfloat16) * parts.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dZ, sizeof(float) * (size_t)nu * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dErr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(dX, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dP, parts.data(), sizeof(__nv_bfloat16) * parts.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(dErr, 0, sizeof(int));
+  if (e == cudaSuccess) e = nss::setup_logits_attributes();
+  CUtensorMap mx, mu;
+  if (e == cudaSuccess) {
+    if (!nss::make_map_bf16(&mx, dX, (unsigned long long)rows_pad) ||
+        !nss::make_map_bf16(&mu, dP, 3ULL * cols_pad)) st = NSS_ERR_CUDA;
+  }
+  if (e == cudaSuccess && st == NSS_OK) e = nss::launch_logits(mx, mu, rows_pad, cols_pad, dZ, n, n, nu, dErr, nullptr, 0);
+  if (e == cudaSuccess && st == NSS_OK) e = cudaDeviceSynchronize();
+  int herr = 0;
+  if (e == cudaSuccess && st == NSS_OK) e = cudaMemcpy(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st == NSS_OK) e = cudaMemcpy(Z, dZ, sizeof(float) * (size_t)nu * n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) st = (e == cudaErrorMemoryAllocation) ? NSS_ERR_OOM : NSS_ERR_CUDA;
+  if (st == NSS_OK && herr != 0) st = NSS_ERR_TIMEOUT;
+  cudaFree(dX);
+  cudaFree(dP);
+  cudaFree(dZ);
+  cudaFree(dErr);
+  return st;
+}
+
 double nss_run_width(const nss_ctx* c, int run) {
   if (!c || run < 0 || run >= c->n_runs) return NAN;
   return c->widths[run];
@@ -576,6 +773,16 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
       return NSS_ERR_ARG;
     }
   c->stream = static_cast<cudaStream_t>(opt[0].cuda_stream);
+  if (!c->stream) {
+    cudaError_t es = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (es != cudaSuccess) {
+      nss_status s_ = cuda_fail(c, es, "stream creation");
+      std::fprintf(stderr, "nss_create: %s\n", c->err.c_str());
+      delete c;
+      return s_;
+    }
+    c->own_stream = true;
+  }
 
   // ---- layout -------------------------------------------------------------
   c->desc.resize(n_runs);
@@ -675,6 +882,8 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     }                                                              \
   } while (0)
   CKC(cudaGetDevice(&c->device), "cudaGetDevice");
+  CKC(nss::setup_kernel_attributes(), "kernel attributes");
+  CKC(nss::setup_logits_attributes(), "kernel attributes");
   CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
   CKC(cudaMalloc(&c->d_desc, sizeof(RunDesc) * n_runs), "descriptor allocation");
   CKC(cudaMalloc(&c->d_state, sizeof(RunState) * n_runs), "state allocation");
@@ -747,6 +956,16 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
       return si;
     }
   }
+  // logistic-regression workspaces and the initial likelihoods
+  for (int r = 0; r < n_runs; ++r) {
+    if (c->desc[r].lik_kind != nss::kLikLogreg) continue;
+    nss_status sl = setup_logreg(c, r, loglik[r]);
+    if (sl != NSS_OK) {
+      std::fprintf(stderr, "nss_create: %s\n", c->err.c_str());
+      free_ctx(c);
+      return sl;
+    }
+  }
   CKC(cudaStreamSynchronize(c->stream), "init synchronize");
   harvest(c);
 #undef CKC
@@ -767,7 +986,7 @@ nss_status nss_step(nss_ctx* c, nss_step_info* info) {
   nss_status st = sync_state(c);
   if (st != NSS_OK) return st;
   if (!all_done(c)) {
-    if ((st = enqueue_iteration(c)) != NSS_OK) return st;
+    if ((st = run_iteration(c)) != NSS_OK) return st;
     if ((st = sync_state(c)) != NSS_OK) return st;
   }
   fill_info(c, info);
@@ -784,7 +1003,7 @@ nss_status nss_run(nss_ctx* c, nss_result* res) {
   int chunk = 4;
   while (!all_done(c)) {
     for (int i = 0; i < chunk; ++i)
-      if ((st = enqueue_iteration(c)) != NSS_OK) return st;
+      if ((st = run_iteration(c)) != NSS_OK) return st;
     if ((st = sync_state(c)) != NSS_OK) return st;
     chunk = std::min(chunk * 2, 16);
   }
@@ -810,7 +1029,10 @@ nss_status nss_reset(nss_ctx* c, const uint64_t* seeds) {
   CK(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(RunState) * c->n_runs, cudaMemcpyHostToDevice,
                      c->stream), "state upload");
   c->prof.h2d_bytes += (long long)sizeof(RunState) * c->n_runs;
-  return launch_inits(c);
+  if ((st = launch_inits(c)) != NSS_OK) return st;
+  for (auto& w : c->lr)
+    if ((st = lr_initial_loglik(c, w)) != NSS_OK) return st;
+  return NSS_OK;
 }
 
 int nss_cfg_lanes(int cfg) { return (cfg >= 0 && cfg < nss::kNumCfgs) ? nss::cfg_g(cfg) : 0; }

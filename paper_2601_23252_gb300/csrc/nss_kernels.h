@@ -1,5 +1,7 @@
 // nss_kernels.h -- host-side launchers of the Nested Slice Sampling kernels.
 #pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "nss_internal.h"
@@ -12,6 +14,33 @@ struct VolLaunch {
   int n_tiles, R;
   double *tsum, *toff, *tmax, *tacc;
 };
+
+// Device workspace of one logistic-regression run (line-affine logits).
+struct LRArgs {
+  const uint32_t* ybits;   // [512] label bits, bit i of word t = y[t + 512 i]
+  float* zx;               // [cols_pad][ldz] logits X x of each chain's point
+  float* zv;               // [cols_pad][ldz] logits X v of each chain's direction
+  long long ldz;
+  float* xc;               // [cols_pad][128] chain positions
+  float* vdir;             // [cols_pad][128] chain directions
+  float* lc;               // [cols_pad] chain logL
+  __nv_bfloat16* parts;    // [3][cols_pad][128] bf16 split of the vectors being multiplied
+  long long part_stride;   // cols_pad * 128
+};
+
+// one-time function attributes (dynamic shared memory above 48 KB)
+cudaError_t setup_kernel_attributes();
+cudaError_t setup_logits_attributes();
+
+bool make_map_bf16(CUtensorMap* map, void* base, unsigned long long rows);
+cudaError_t launch_logits(const CUtensorMap& mapX, const CUtensorMap& mapU, int rows_pad, int cols_pad, float* out,
+                          long long ldo, int n_rows, int n_cols, int* err, const int* skip, cudaStream_t s);
+cudaError_t launch_lr_parents(const Dev& D, const LRArgs& A, int run, int k, cudaStream_t s);
+cudaError_t launch_lr_live_parts(const Dev& D, const LRArgs& A, int run, int m, cudaStream_t s);
+cudaError_t launch_lr_rowll(const Dev& D, const LRArgs& A, int run, int m, int emax, cudaStream_t s);
+cudaError_t launch_lr_dir(const Dev& D, const LRArgs& A, int run, int k, int step, cudaStream_t s);
+cudaError_t launch_lr_slice(const Dev& D, const LRArgs& A, int run, int k, int step, int emax, cudaStream_t s);
+cudaError_t launch_lr_replace(const Dev& D, const LRArgs& A, int run, int k, cudaStream_t s);
 
 cudaError_t launch_init(int cfg, const Dev& D, const WorkItem* items, int n, cudaStream_t s);
 cudaError_t launch_prologue(const Dev& D, int n_runs, size_t smem, cudaStream_t s);

@@ -1,0 +1,498 @@
+// nss_logreg.cu -- Bayesian logistic regression likelihood inside the HRSS
+// sweep (Sec. 4.2 workloads; the sweep of Sec. 3.2 / App. B.4), for sm_103a.
+//
+// logL(x) = sum_n [y_n z_n - softplus(z_n)],  z = X x,  X the N x d design.
+//
+// Along an HRSS line x + t v the logits are affine in t:
+//   z(t) = X x + t X v,
+// so each step needs one product X v per chain (and X x once per chain per
+// outer iteration for the parent), and every slice evaluation of that step is
+// N fused multiply-adds and N softplus terms.  The products of all chains are
+// one batched contraction Z = X [u_1 ... u_k], computed on the 5th-generation
+// tensor cores: tcgen05.mma kind::f16 with BF16 operands and FP32
+// accumulation in tensor memory, operands staged by TMA.  X holds bfloat16
+// values exactly (the data set is bf16-exact); each FP32 vector u is split
+// into three bfloat16 parts u = u_hi + u_mid + u_lo (|u - sum| <= 2^-24 |u|),
+// so the contraction reproduces FP32 products.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cfloat>
+#include <cmath>
+
+#include "nss_device.cuh"
+#include "nss_kernels.h"
+#include "nss_tc.cuh"
+
+namespace nss {
+
+// ---------------------------------------------------------------------------
+// Tensor-core contraction  out[c][r] = sum_p sum_k X[r][k] * U_p[c][k]
+//   X   : bf16 [rows_pad][128]          (tensor map mapX, box 64 x 128)
+//   U   : bf16 [3][cols_pad][128]       (tensor map mapU, box 64 x 128)
+//   out : fp32 [cols][ldo]
+// One 128-thread block per 128 x 128 output tile: thread 0 issues the eight
+// TMA loads (two K chunks of X, three parts x two K chunks of U), thread 32
+// issues 24 MMAs of 128 x 128 x 16 into a 128-column TMEM accumulator, and
+// the four warps read their 32 TMEM lanes back and store coalesced rows.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 128;
+constexpr uint32_t kChunkBytes = 128u * 64u * 2u;   // 128 rows x 64 bf16
+constexpr uint32_t kMaxPolls = 1u << 22;
+constexpr int kLogitsSmem = 8 * kChunkBytes + 1024;
+
+__global__ void __launch_bounds__(128, 1) k_logits(const __grid_constant__ CUtensorMap mapX,
+                                                    const __grid_constant__ CUtensorMap mapU, int cols_pad,
+                                                    float* __restrict__ out, long long ldo, int n_rows,
+                                                    int n_cols, int* __restrict__ err,
+                                                    const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* A = base;                      // [2 chunks]
+  uint8_t* B = base + 2 * kChunkBytes;    // [3 parts][2 chunks]
+  __shared__ __align__(8) uint64_t bar_full;
+  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * kTile, col0 = blockIdx.y * kTile;
+
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar_full, 1);
+    tc::mbar_init(&bar_mma, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 128);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (threadIdx.x == 0) {
+    tc::mbar_arrive_expect_tx(&bar_full, 8 * kChunkBytes);
+    for (int c = 0; c < 2; ++c) tc::tma_load_2d(A + c * kChunkBytes, &mapX, &bar_full, c * 64, row0);
+    for (int p = 0; p < 3; ++p)
+      for (int c = 0; c < 2; ++c)
+        tc::tma_load_2d(B + (p * 2 + c) * kChunkBytes, &mapU, &bar_full, c * 64, p * cols_pad + col0);
+  }
+  if (threadIdx.x == 32) {
+    if (tc::mbar_wait(&bar_full, 0, kMaxPolls)) {
+      tc::fence_after_sync();
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTile, kTile);
+      uint32_t acc = 0;
+      for (int c = 0; c < 2; ++c)
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(A + c * kChunkBytes) + kk * 32);
+            const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(B + (p * 2 + c) * kChunkBytes) + kk * 32);
+            tc::mma_bf16(tmem, ad, bd, idesc, acc);
+            acc = 1;
+          }
+      tc::mma_commit(&bar_mma);
+    } else {
+      atomicExch(err, 1);
+    }
+  }
+  // every thread waits for the accumulator (bounded), decision made uniform
+  const bool ok = tc::mbar_wait(&bar_mma, 0, kMaxPolls);
+  const int all_ok = __syncthreads_and(ok ? 1 : 0);
+  if (all_ok) {
+    tc::fence_after_sync();
+    const int r = row0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int cc = 0; cc < 4; ++cc) {
+      float v[32];
+      tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(cc * 32), v);
+      if (r < n_rows) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int c = col0 + cc * 32 + i;
+          if (c < n_cols) out[static_cast<long long>(c) * ldo + r] = v[i];
+        }
+      }
+    }
+  } else {
+    if (threadIdx.x == 0) atomicExch(err, 2);
+    // let any copy still in flight land before the block's shared memory goes away
+    tc::mbar_wait(&bar_full, 0, kMaxPolls);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 -> three bfloat16 parts: h = bf16(u), m = bf16(u - h), l = bf16(u - h - m)
+// (each difference is exact in FP32).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split3(float u, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(u);
+  const float r1 = u - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(m);
+  l = __float2bfloat16_rn(r2);
+}
+
+__device__ __forceinline__ void write_parts(__nv_bfloat16* parts, long long part_stride, int row, int t,
+                                            float u) {
+  __nv_bfloat16 h, m, l;
+  split3(u, h, m, l);
+  parts[static_cast<long long>(row) * 128 + t] = h;
+  parts[part_stride + static_cast<long long>(row) * 128 + t] = m;
+  parts[2 * part_stride + static_cast<long long>(row) * 128 + t] = l;
+}
+
+// ---------------------------------------------------------------------------
+// Chain start of an outer iteration: copy each chain's parent into its
+// working position, clear its counters, and split the positions for the
+// contraction X x_parent.  Block j = chain j, thread t = dimension t.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_lr_parents(Dev D, LRArgs A, int run) {
+  const RunDesc& R = D.desc[run];
+  if (D.st[run].done) return;
+  const int j = blockIdx.x, t = threadIdx.x;
+  if (j >= R.k) return;
+  const int parent = D.i[R.o_parent + j];
+  const float x = (t < R.d) ? D.f[R.o_x + static_cast<long long>(parent) * R.dpad + t] : 0.0f;
+  A.xc[static_cast<long long>(j) * 128 + t] = x;
+  write_parts(A.parts, A.part_stride, j, t, x);
+  if (t == 0) A.lc[j] = D.f[R.o_logL + parent];
+  if (t < 6) D.i[R.o_stats + t * R.k + j] = 0;
+}
+
+// The initial live set: split every live point for the contraction X x.
+__global__ void __launch_bounds__(128) k_lr_live_parts(Dev D, LRArgs A, int run) {
+  const RunDesc& R = D.desc[run];
+  const int s = blockIdx.x, t = threadIdx.x;
+  if (s >= R.m) return;
+  const float x = (t < R.d) ? D.f[R.o_x + static_cast<long long>(s) * R.dpad + t] : 0.0f;
+  write_parts(A.parts, A.part_stride, s, t, x);
+}
+
+// ---------------------------------------------------------------------------
+// Per-chain block reductions over the N logits (512 threads, thread t owns
+// elements n = t + 512 i).
+// ---------------------------------------------------------------------------
+constexpr int kLRThreads = 512;
+
+__device__ __forceinline__ float2 block_sum2(float a, float b, float2* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) red[wid] = make_float2(a, b);
+  __syncthreads();
+  if (wid == 0) {
+    float2 v = (lane < (kLRThreads >> 5)) ? red[lane] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    if (lane == 0) red[32] = v;
+  }
+  __syncthreads();
+  const float2 r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// y z - softplus(z), softplus(z) = max(z, 0) + log(1 + e^-|z|)
+__device__ __forceinline__ float bern_logit(float z, bool y) {
+  const float sp = fmaxf(z, 0.0f) + __logf(1.0f + __expf(-fabsf(z)));
+  return (y ? z : 0.0f) - sp;
+}
+
+// logL of rows of a logits matrix (the initial live set)
+template <int EMAX>
+__global__ void __launch_bounds__(kLRThreads) k_lr_rowll(Dev D, LRArgs A, int run) {
+  __shared__ float2 red[33];
+  const RunDesc& R = D.desc[run];
+  const int s = blockIdx.x, t = threadIdx.x;
+  if (s >= R.m) return;
+  const uint32_t yb = A.ybits[t];
+  float acc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < EMAX; ++i) {
+    const int n = t + kLRThreads * i;
+    if (n < R.n_data) acc += bern_logit(A.zx[static_cast<long long>(s) * A.ldz + n], (yb >> i) & 1u);
+  }
+  const float2 tot = block_sum2(acc, 0.0f, red);
+  if (t == 0) {
+    const float ll = isnan(tot.x) ? -INFINITY : tot.x;
+    D.f[R.o_logL + s] = ll;
+    D.f[R.o_birth + s] = -INFINITY;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Direction of HRSS step s for every chain: z ~ N(0, I) from words
+// [0, 2 ceil(d/2)) of counter (iteration, chain, s, .), d~ = L z,
+// v = d~/|z| (or d~/|d~|).  Block j = chain j, thread t = dimension t.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_lr_dir(Dev D, LRArgs A, int run, int step) {
+  __shared__ float zs[128];
+  __shared__ float red[4];
+  const RunDesc& R = D.desc[run];
+  const RunState& S = D.st[run];
+  if (S.done) return;
+  const int j = blockIdx.x, t = threadIdx.x;
+  if (j >= R.k) return;
+  const uint32_t iter = static_cast<uint32_t>(S.iter);
+  float z = 0.0f;
+  if (t < R.d) {
+    const uint4 w = draw_block(R, iter, static_cast<uint32_t>(j), static_cast<uint32_t>(step),
+                               static_cast<uint32_t>(t >> 2));
+    float a, b;
+    if (t & 2) box_muller(w.z, w.w, a, b);
+    else box_muller(w.x, w.y, a, b);
+    z = (t & 1) ? b : a;
+  }
+  zs[t] = z;
+  float zz = z * z;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
+  if ((t & 31) == 0) red[t >> 5] = zz;
+  __syncthreads();
+  zz = red[0] + red[1] + red[2] + red[3];
+  float dt = 0.0f;
+  if (t < R.d) {
+    const float* Lr = D.f + R.o_L + static_cast<long long>(t) * R.dpad;
+    for (int b = 0; b <= t; ++b) dt = fmaf(Lr[b], zs[b], dt);
+  }
+  float inrm;
+  if (R.dir_norm == 0) {
+    inrm = rsqrtf(zz);
+  } else {
+    __syncthreads();
+    float dd = dt * dt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    if ((t & 31) == 0) red[t >> 5] = dd;
+    __syncthreads();
+    inrm = rsqrtf(red[0] + red[1] + red[2] + red[3]);
+  }
+  const float v = (t < R.d) ? dt * inrm : 0.0f;
+  A.vdir[static_cast<long long>(j) * 128 + t] = v;
+  write_parts(A.parts, A.part_stride, j, t, v);
+}
+
+// ---------------------------------------------------------------------------
+// HRSS step s of every chain along its line, with the logits affine in t.
+// Block j = chain j (512 threads).  Slice test: prior slice height under the
+// N(a, b^2) prior, then logL > logL* (strict).  Words: U at nz, height at
+// nz+1, shrinkage r at nz+3+r, nz = 2 ceil(d/2) (the same layout as every
+// other likelihood).
+// ---------------------------------------------------------------------------
+template <int EMAX>
+__global__ void __launch_bounds__(kLRThreads) k_lr_slice(Dev D, LRArgs A, int run, int step) {
+  __shared__ float2 red[33];
+  const RunDesc& R = D.desc[run];
+  RunState* S = D.st + run;
+  if (S->done) return;
+  const int j = blockIdx.x, t = threadIdx.x;
+  if (j >= R.k) return;
+  const uint32_t iter = static_cast<uint32_t>(S->iter);
+  const float lstar = S->logLstar;
+  const int N = R.n_data, d = R.d;
+  float zx[EMAX], zv[EMAX];
+  const long long rowz = static_cast<long long>(j) * A.ldz;
+#pragma unroll
+  for (int i = 0; i < EMAX; ++i) {
+    const int n = t + kLRThreads * i;
+    zx[i] = (n < N) ? A.zx[rowz + n] : 0.0f;
+    zv[i] = (n < N) ? A.zv[rowz + n] : 0.0f;
+  }
+  const uint32_t yb = A.ybits[t];
+  const bool own = t < d;
+  float xt = own ? A.xc[static_cast<long long>(j) * 128 + t] : 0.0f;
+  const float vt = own ? A.vdir[static_cast<long long>(j) * 128 + t] : 0.0f;
+  const float at = own ? D.f[R.o_a + t] : 0.0f;
+  const float ibt = own ? 1.0f / D.f[R.o_b + t] : 0.0f;
+  float lx = A.lc[j];
+
+  const uint32_t nz = 2u * static_cast<uint32_t>((d + 1) >> 1);
+  uint32_t cblk = 0xFFFFFFFFu;
+  uint4 cw = make_uint4(0, 0, 0, 0);
+  auto word = [&](uint32_t wi) {
+    if ((wi >> 2) != cblk) {
+      cblk = wi >> 2;
+      cw = draw_block(R, iter, static_cast<uint32_t>(j), static_cast<uint32_t>(step), cblk);
+    }
+    return pick(cw, wi & 3u);
+  };
+  // prior slice height: log Pi(x) + ln u
+  float ux = own ? (xt - at) * ibt : 0.0f;
+  const float2 px = block_sum2(-0.5f * ux * ux, 0.0f, red);
+  const float height = px.x + R.prior_const + logf(u24(word(nz + 1u)));
+
+  int evals = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
+  auto in_slice = [&](float tt, float& ll) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < EMAX; ++i) {
+      const int n = t + kLRThreads * i;
+      if (n < N) acc += bern_logit(fmaf(tt, zv[i], zx[i]), (yb >> i) & 1u);
+    }
+    const float yt = fmaf(tt, vt, xt);
+    const float u = own ? (yt - at) * ibt : 0.0f;
+    const float2 tot = block_sum2(acc, -0.5f * u * u, red);
+    ++evals;
+    ll = tot.x;
+    if (isnan(ll)) {
+      ll = -INFINITY;
+      ++nanc;
+    }
+    const float lp = tot.y + R.prior_const;
+    return (lp > height) && (ll > lstar);
+  };
+
+  const float w = R.w;
+  const float U = u24(word(nz));
+  float tl = -w * U, tr = tl + w, lly;
+  for (int n = 0;; ++n) {
+    if (n >= kStepOutCap) { ++capo; break; }
+    if (!in_slice(tl, lly)) break;
+    tl -= w;
+    ++exps;
+  }
+  for (int n = 0;; ++n) {
+    if (n >= kStepOutCap) { ++capo; break; }
+    if (!in_slice(tr, lly)) break;
+    tr += w;
+    ++exps;
+  }
+  bool ok = false;
+  float tacc = 0.0f;
+  for (int r = 0; r < kShrinkCap; ++r) {
+    const float u = u24(word(nz + 3u + static_cast<uint32_t>(r)));
+    const float tt = fmaf(u, tr - tl, tl);
+    ++shr;
+    if (in_slice(tt, lly)) {
+      ok = true;
+      tacc = tt;
+      lx = lly;
+      break;
+    }
+    if (tt < 0.0f) tl = tt;
+    else tr = tt;
+  }
+  if (ok) {
+#pragma unroll
+    for (int i = 0; i < EMAX; ++i) {
+      const int n = t + kLRThreads * i;
+      if (n < N) A.zx[rowz + n] = fmaf(tacc, zv[i], zx[i]);
+    }
+    if (own) A.xc[static_cast<long long>(j) * 128 + t] = fmaf(tacc, vt, xt);
+  }
+  if (t == 0) {
+    A.lc[j] = lx;
+    int* st = D.i + R.o_stats;
+    st[j] += evals;
+    st[R.k + j] += ok ? 1 : 0;
+    st[2 * R.k + j] += ok ? 0 : 1;
+    st[3 * R.k + j] += exps;
+    st[4 * R.k + j] += shr;
+    st[5 * R.k + j] += capo;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&S->evals), static_cast<unsigned long long>(evals));
+    if (!ok) atomicAdd(reinterpret_cast<unsigned long long*>(&S->nulls), 1ull);
+    if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&S->cap_out), static_cast<unsigned long long>(capo));
+    if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&S->nan_evals), static_cast<unsigned long long>(nanc));
+  }
+}
+
+// (iv) replace dead slot j with chain j's final point, born at logL*
+__global__ void __launch_bounds__(128) k_lr_replace(Dev D, LRArgs A, int run) {
+  const RunDesc& R = D.desc[run];
+  const RunState& S = D.st[run];
+  if (S.done) return;
+  const int j = blockIdx.x, t = threadIdx.x;
+  if (j >= R.k) return;
+  const int slot = D.i[R.o_dead + j];
+  if (t < R.dpad) D.f[R.o_x + static_cast<long long>(slot) * R.dpad + t] = (t < R.d) ? A.xc[static_cast<long long>(j) * 128 + t] : 0.0f;
+  if (t == 0) {
+    D.f[R.o_logL + slot] = A.lc[j];
+    D.f[R.o_birth + slot] = S.logLstar;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// bf16 matrix [rows][128] in global memory, box 64 columns x 128 rows, 128-byte swizzle
+bool make_map_bf16(CUtensorMap* map, void* base, unsigned long long rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {128, rows};
+  const cuuint64_t strides[1] = {128 * 2};
+  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+cudaError_t setup_logits_attributes() {
+  return cudaFuncSetAttribute(k_logits, cudaFuncAttributeMaxDynamicSharedMemorySize, kLogitsSmem);
+}
+
+cudaError_t launch_logits(const CUtensorMap& mapX, const CUtensorMap& mapU, int rows_pad, int cols_pad, float* out,
+                          long long ldo, int n_rows, int n_cols, int* err, const int* skip, cudaStream_t s) {
+  dim3 grid(rows_pad / kTile, (n_cols + kTile - 1) / kTile);
+  k_logits<<<grid, 128, kLogitsSmem, s>>>(mapX, mapU, cols_pad, out, ldo, n_rows, n_cols, err, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lr_parents(const Dev& D, const LRArgs& A, int run, int k, cudaStream_t s) {
+  k_lr_parents<<<k, 128, 0, s>>>(D, A, run);
+  return cudaGetLastError();
+}
+cudaError_t launch_lr_live_parts(const Dev& D, const LRArgs& A, int run, int m, cudaStream_t s) {
+  k_lr_live_parts<<<m, 128, 0, s>>>(D, A, run);
+  return cudaGetLastError();
+}
+cudaError_t launch_lr_rowll(const Dev& D, const LRArgs& A, int run, int m, int emax, cudaStream_t s) {
+  if (emax <= 4) k_lr_rowll<4><<<m, kLRThreads, 0, s>>>(D, A, run);
+  else if (emax <= 20) k_lr_rowll<20><<<m, kLRThreads, 0, s>>>(D, A, run);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+cudaError_t launch_lr_dir(const Dev& D, const LRArgs& A, int run, int k, int step, cudaStream_t s) {
+  k_lr_dir<<<k, 128, 0, s>>>(D, A, run, step);
+  return cudaGetLastError();
+}
+cudaError_t launch_lr_slice(const Dev& D, const LRArgs& A, int run, int k, int step, int emax, cudaStream_t s) {
+  if (emax <= 4) k_lr_slice<4><<<k, kLRThreads, 0, s>>>(D, A, run, step);
+  else if (emax <= 20) k_lr_slice<20><<<k, kLRThreads, 0, s>>>(D, A, run, step);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+cudaError_t launch_lr_replace(const Dev& D, const LRArgs& A, int run, int k, cudaStream_t s) {
+  k_lr_replace<<<k, 128, 0, s>>>(D, A, run);
+  return cudaGetLastError();
+}
+
+}  // namespace nss

@@ -329,10 +329,13 @@ __global__ void __launch_bounds__(128) k_init(Dev D, const WorkItem* __restrict_
         if (dim < R.d) x[i] = fmaf(D.f[R.o_b + dim], z[i], D.f[R.o_a + dim]);
       }
     }
-    Lik<G, DPL> L;
-    L.init(R, D.f, gl, has);
-    float ll = L.eval(R, D.f, x, gl, has, mask);
-    if (isnan(ll)) ll = -INFINITY;
+    float ll = 0.0f;  // logistic regression: filled by the contraction pass
+    if (R.lik_kind != kLikLogreg) {
+      Lik<G, DPL> L;
+      L.init(R, D.f, gl, has);
+      ll = L.eval(R, D.f, x, gl, has, mask);
+      if (isnan(ll)) ll = -INFINITY;
+    }
     if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * R.dpad, gl, x);
     if (gl == 0) {
       D.f[R.o_logL + slot] = ll;

@@ -107,6 +107,7 @@ def lib():
     L.nss_set_profiling.argtypes = [C.c_void_p, C.c_int]
     L.nss_get_profile.argtypes = [C.c_void_p, P(Profile)]
     L.nss_n_runs.argtypes = [C.c_void_p]
+    L.nss_logreg_logits.argtypes = [_fp, C.c_int, C.c_int, _fp, C.c_int, _fp]
     L.nss_run_width.argtypes = [C.c_void_p, C.c_int]
     L.nss_run_width.restype = C.c_double
     L.nss_destroy.argtypes = [C.c_void_p]
@@ -171,6 +172,20 @@ class _Spec:
         for key, val in wl.extra.get("options", {}).items():
             setattr(o, key, val)
         self.opts = o
+
+
+def logreg_logits(X, U):
+    """Z = U X^T by the tensor-core contraction of the logistic sweep (X as bf16,
+    U split into three bf16 parts, FP32 accumulation)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    U = np.ascontiguousarray(U, dtype=np.float32)
+    n, d = X.shape
+    nu = U.shape[0]
+    Z = np.empty((nu, n), np.float32)
+    st = lib().nss_logreg_logits(X.ctypes.data_as(_fp), n, d, U.ctypes.data_as(_fp), nu, Z.ctypes.data_as(_fp))
+    if st != NSS_OK:
+        raise NSSError(st, "nss_logreg_logits")
+    return Z
 
 
 class Sampler:

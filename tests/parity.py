@@ -17,8 +17,10 @@ from paper_2601_23252_gb300 import workloads as W
 #   gmm_d32 (logL ~ 90, |grad| ~ 300):       ~3e-5 + 2e-4  -> 1e-3
 #   gauss20 (logL ~ 30, |grad| ~ 100):       ~1e-5 + 1e-4  -> 5e-4
 #   batch64 (logL ~ 200, sigma >= 0.01):     ~1e-4 + 1e-3  -> 5e-3
+#   logreg (N rows, |z| ~ 3..10): FP32 logits 1e-6 |z| per row, FP32 sums of
+#   N terms of ~1 nat, fast exp/log in softplus: ~sqrt(N) 1e-5 -> 2e-3 (N=1e3), 1e-2 (N=1e4)
 TIES = {"gauss_d2": (2e-5, 2e-5, 2e-6), "gmm_d32": (1e-3, 1e-3, 2e-6), "batch64": (5e-3, 5e-3, 2e-6),
-        "gauss20": (5e-4, 5e-4, 2e-6)}
+        "gauss20": (5e-4, 5e-4, 2e-6), "logreg_small": (2e-3, 1e-4, 0.0), "logreg_d100": (1e-2, 1e-4, 0.0)}
 
 
 def oracle_problem(wl):

@@ -1,0 +1,125 @@
+"""Logistic-regression likelihood on the GPU: the tcgen05 tensor-core logit
+contraction against FP64 numpy, the initial likelihoods and one-step parity
+against the FP64 checker (reduced N and d), sampled chains of a full-size
+step (N = 10000, d = 100, k = 1000, p = 200), and evidences against the
+checker's runs of the same seeds."""
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import golden_path
+from parity import compare_step, near_tie_mask, oracle_opts, oracle_problem
+from paper_2601_23252_gb300 import native
+from paper_2601_23252_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+COUNTERS = ("evals", "accepts", "nulls", "expansions", "shrinks", "cap_out")
+
+
+def small(seed=0):
+    return W.logreg_d100(seed=seed, n_rows=1000, d=10, n_live=200, k=100).with_(name="logreg_small")
+
+
+@pytest.mark.parametrize("n,d,nu", [(1000, 10, 100), (10000, 100, 1000), (300, 128, 257), (129, 1, 1)])
+def test_tensor_core_logits_match_fp64(gpu_lib, n, d, nu):
+    rng = np.random.default_rng(n + d)
+    X = W.to_bf16_exact(rng.standard_normal((n, d)).astype(np.float32))
+    U = rng.standard_normal((nu, d)).astype(np.float32) * np.float32(0.3)
+    Z = native.logreg_logits(X, U)
+    ref = U.astype(np.float64) @ X.astype(np.float64).T
+    scale = np.sqrt((U.astype(np.float64) ** 2) @ (X.astype(np.float64) ** 2).T)
+    err = np.max(np.abs(Z - ref) / np.maximum(scale, 1e-30))
+    print(f"\nlogits n={n} d={d} nu={nu}: max error / (|u| |x|) = {err:.2e}")
+    # three bf16 parts reproduce FP32 inputs; FP32 accumulation over d terms
+    assert err < 1e-6
+
+
+def test_initial_logL_matches_checker(gpu_lib):
+    wl = small(seed=3)
+    with native.Sampler(wl) as s:
+        st = s.export_state()
+    pb = oracle_problem(wl)
+    ref = pb.loglik(st["x"].astype(np.float64))
+    err = np.abs(st["logL"] - ref)
+    print(f"\ninitial logL: max abs err {err.max():.2e} (|logL| ~ {np.abs(ref).mean():.1f})")
+    assert np.all(err < 2e-3)
+    ox, _, _ = O.init_live(pb, oracle_opts(wl))
+    assert np.allclose(st["x"], ox, rtol=2e-6, atol=2e-6)
+
+
+@pytest.mark.parametrize("seed,warm", [(1, 2), (2, 8)])
+def test_one_step_parity_logistic(gpu_lib, seed, warm):
+    wl = small(seed)
+    rep = compare_step(wl, warm)
+    g, t = rep["gpu"], rep["orc"]
+    assert np.array_equal(g["dead_idx"], t["dead_idx"])
+    assert g["logLstar"] == np.float32(t["logLstar"])
+    assert np.array_equal(g["parent"], t["parent"])
+    tie = near_tie_mask(rep, "logreg_small")
+    same = np.ones(wl.k, bool)
+    for c in COUNTERS:
+        same &= g[c] == t[c]
+    ok = same & ~tie
+    xerr = np.abs(g["new_x"][ok] - t["new_x"][ok]).max()
+    lerr = np.abs(g["new_logL"][ok] - t["new_logL"][ok]).max()
+    print(f"\nlogreg seed={seed} warm={warm}: ties {tie.mean():.3f} mismatch {np.mean(~same):.3f} "
+          f"x err {xerr:.2e} logL err {lerr:.2e}")
+    assert np.all(same | tie)
+    assert ok.mean() > 0.8
+    scale = np.abs(t["new_x"][ok]).max()
+    assert xerr <= 1e-5 * max(1.0, scale)
+    assert lerr <= 1e-5 * np.abs(t["new_logL"][ok]).max() + 2e-3
+    assert abs(rep["info"]["logZ"] - rep["orc_logZ"]) < 1e-5 * max(1.0, abs(rep["orc_logZ"]))
+
+
+def test_full_size_step_sampled_chains(gpu_lib):
+    """One step at the full logistic size from the prior draw; a sample of
+    chains recomputed by the checker one HRSS step at a time."""
+    wl = W.logreg_d100(seed=0)
+    with native.Sampler(wl) as s:
+        st0 = s.export_state()
+        s.step()
+        g = s.trace(0)
+    pb = oracle_problem(wl)
+    x32 = st0["x"].astype(np.float64)
+    l32 = st0["logL"].astype(np.float64)
+    dead, surv, ls = O.select(l32, wl.k)
+    assert np.array_equal(g["dead_idx"], dead) and g["logLstar"] == np.float32(ls)
+    par = O.parents(wl.seed, wl.run_id, 0, wl.n_live, wl.k, surv)
+    assert np.array_equal(g["parent"], par)
+    L, _ = O.metric(x32)
+    assert np.abs(g["L"] - L).max() / np.abs(L).max() < 1e-4
+    checked = 0
+    for j in (0, 17, 333, 999):
+        x, lx = x32[par[j]].copy(), l32[par[j]]
+        tot = {c: 0 for c in ("evals", "accepts", "nulls")}
+        tie = False
+        for s_ in range(wl.p):
+            x, lx, c = O.hrss_step(pb, L, wl.w, 0, ls, wl.seed, wl.run_id, 0, j, s_, x, lx)
+            for key in tot:
+                tot[key] += c[key]
+            tie |= c["margin"] < 1e-2 or c["pmargin"] < 1e-4
+        if tie:
+            continue
+        checked += 1
+        assert g["evals"][j] == tot["evals"] and g["accepts"][j] == tot["accepts"]
+        assert np.abs(g["new_x"][j] - x).max() < 1e-4
+        assert abs(g["new_logL"][j] - lx) < 1e-5 * abs(lx) + 1e-2
+    print(f"\nfull-size logistic step: {checked} of 4 sampled chains compared exactly")
+    assert checked >= 2
+
+
+def test_logistic_evidence_against_checker(gpu_lib):
+    rows = [l.split() for l in open(golden_path("oracle_logreg_small_logz.txt")) if not l.startswith("#")]
+    gold = {int(r[0]): (float(r[1]), float(r[2])) for r in rows}
+    seeds = sorted(gold)
+    with native.Sampler([small(s) for s in seeds]) as smp:
+        res = smp.run()
+    lz = np.array([r["logZ"] for r in res]); err = np.array([r["logZ_err"] for r in res])
+    lo = np.array([gold[s][0] for s in seeds]); eo = np.array([gold[s][1] for s in seeds])
+    diff = lz - lo
+    print(f"\nlogreg_small: paired gpu-checker mean {diff.mean():+.4f} sd {diff.std(ddof=1):.4f}; "
+          f"mean err {err.mean():.3f}")
+    assert np.all(np.abs(diff) < 3.0 * np.sqrt(err**2 + eo**2))
+    assert abs(diff.mean()) < 3.0 * diff.std(ddof=1) / np.sqrt(len(seeds)) + 1e-3

@@ -34,6 +34,7 @@ struct LRWork {
   uint32_t* ybits = nullptr;
   float *zx = nullptr, *zv = nullptr, *xc = nullptr, *vdir = nullptr, *lc = nullptr;
   __nv_bfloat16* parts = nullptr;
+  float *center = nullptr, *zref = nullptr;
   int* err = nullptr;
   CUtensorMap mapX, mapU;
   nss::LRArgs args;
@@ -297,6 +298,8 @@ void free_ctx(nss_ctx* c) {
     cudaFree(w.vdir);
     cudaFree(w.lc);
     cudaFree(w.parts);
+    cudaFree(w.center);
+    cudaFree(w.zref);
     cudaFree(w.err);
   }
   if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
@@ -377,17 +380,18 @@ nss_status enqueue_iteration(nss_ctx* c) {
     const RunDesc& R = c->desc[w.run];
     const int* done = &c->d_state[w.run].done;
     Rec r(c, NSS_K_OTHER);
+    CK(nss::launch_lr_center(D, w.args, w.run, R.n_data, c->stream), "logistic centre launch");
     CK(nss::launch_lr_parents(D, w.args, w.run, R.k, c->stream), "logistic parents launch");
     CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.k, w.err, done,
-                          c->stream), "logits launch");
+                          w.zref, c->stream), "logits launch");
     for (int s = 0; s < R.p; ++s) {
       CK(nss::launch_lr_dir(D, w.args, w.run, R.k, s, c->stream), "logistic direction launch");
       CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zv, w.rows_pad, R.n_data, R.k, w.err, done,
-                            c->stream), "logits launch");
+                            nullptr, c->stream), "logits launch");
       CK(nss::launch_lr_slice(D, w.args, w.run, R.k, s, w.emax, c->stream), "logistic slice launch");
     }
     CK(nss::launch_lr_replace(D, w.args, w.run, R.k, c->stream), "logistic replace launch");
-    c->launches += 3 + 3LL * R.p;
+    c->launches += 5 + 3LL * R.p;
   }
   {
     Rec r(c, NSS_K_TERMINATE);
@@ -473,9 +477,10 @@ nss_status lr_initial_loglik(nss_ctx* c, LRWork& w) {
   const RunDesc& R = c->desc[w.run];
   nss::Dev D = dev_of(c);
   Rec rr(c, NSS_K_INIT);
+  CK(nss::launch_lr_center(D, w.args, w.run, R.n_data, c->stream), "logistic centre launch");
   CK(nss::launch_lr_live_parts(D, w.args, w.run, R.m, c->stream), "logistic live split launch");
   CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.m, w.err, nullptr,
-                        c->stream), "logits launch");
+                        w.zref, c->stream), "logits launch");
   CK(nss::launch_lr_rowll(D, w.args, w.run, R.m, w.emax, c->stream), "logistic row likelihood launch");
   return NSS_OK;
 }
@@ -506,6 +511,8 @@ nss_status setup_logreg(nss_ctx* c, int run, const nss_loglik& lk) {
   CK(cudaMalloc(&w.lc, sizeof(float) * w.cols_pad), "logistic workspace");
   CK(cudaMalloc(&w.parts, sizeof(__nv_bfloat16) * 3 * (size_t)w.cols_pad * 128), "logistic workspace");
   CK(cudaMalloc(&w.err, sizeof(int)), "logistic workspace");
+  CK(cudaMalloc(&w.center, sizeof(float) * 128), "logistic workspace");
+  CK(cudaMalloc(&w.zref, sizeof(float) * w.rows_pad), "logistic workspace");
   c->lr.push_back(w);  // owned by the context from here on (freed with it)
   LRWork& W = c->lr.back();
   CK(cudaMemcpyAsync(W.Xb, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice, c->stream),
@@ -530,6 +537,9 @@ nss_status setup_logreg(nss_ctx* c, int run, const nss_loglik& lk) {
   W.args.lc = W.lc;
   W.args.parts = W.parts;
   W.args.part_stride = (long long)W.cols_pad * 128;
+  W.args.Xb = W.Xb;
+  W.args.center = W.center;
+  W.args.zref = W.zref;
   return lr_initial_loglik(c, W);
 }
 
@@ -730,7 +740,8 @@ nss_status nss_logreg_logits(const float* X, int n, int d, const float* U, int n
     if (!nss::make_map_bf16(&mx, dX, (unsigned long long)rows_pad) ||
         !nss::make_map_bf16(&mu, dP, 3ULL * cols_pad)) st = NSS_ERR_CUDA;
   }
-  if (e == cudaSuccess && st == NSS_OK) e = nss::launch_logits(mx, mu, rows_pad, cols_pad, dZ, n, n, nu, dErr, nullptr, 0);
+  if (e == cudaSuccess && st == NSS_OK)
+    e = nss::launch_logits(mx, mu, rows_pad, cols_pad, dZ, n, n, nu, dErr, nullptr, nullptr, 0);
   if (e == cudaSuccess && st == NSS_OK) e = cudaDeviceSynchronize();
   int herr = 0;
   if (e == cudaSuccess && st == NSS_OK) e = cudaMemcpy(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost);

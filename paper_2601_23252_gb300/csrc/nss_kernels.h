@@ -26,6 +26,9 @@ struct LRArgs {
   float* lc;               // [cols_pad] chain logL
   __nv_bfloat16* parts;    // [3][cols_pad][128] bf16 split of the vectors being multiplied
   long long part_stride;   // cols_pad * 128
+  const __nv_bfloat16* Xb; // [rows_pad][128] design matrix
+  float* center;           // [128] centre mu of the contraction (live-set mean)
+  float* zref;             // [rows_pad] X mu
 };
 
 // one-time function attributes (dynamic shared memory above 48 KB)
@@ -34,7 +37,9 @@ cudaError_t setup_logits_attributes();
 
 bool make_map_bf16(CUtensorMap* map, void* base, unsigned long long rows);
 cudaError_t launch_logits(const CUtensorMap& mapX, const CUtensorMap& mapU, int rows_pad, int cols_pad, float* out,
-                          long long ldo, int n_rows, int n_cols, int* err, const int* skip, cudaStream_t s);
+                          long long ldo, int n_rows, int n_cols, int* err, const int* skip, const float* zref,
+                          cudaStream_t s);
+cudaError_t launch_lr_center(const Dev& D, const LRArgs& A, int run, int n_data, cudaStream_t s);
 cudaError_t launch_lr_parents(const Dev& D, const LRArgs& A, int run, int k, cudaStream_t s);
 cudaError_t launch_lr_live_parts(const Dev& D, const LRArgs& A, int run, int m, cudaStream_t s);
 cudaError_t launch_lr_rowll(const Dev& D, const LRArgs& A, int run, int m, int emax, cudaStream_t s);

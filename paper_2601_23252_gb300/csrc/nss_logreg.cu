@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(128, 1) k_logits(const __grid_constant__ CUten
                                                     const __grid_constant__ CUtensorMap mapU, int cols_pad,
                                                     float* __restrict__ out, long long ldo, int n_rows,
                                                     int n_cols, int* __restrict__ err,
-                                                    const int* __restrict__ skip) {
+                                                    const int* __restrict__ skip,
+                                                    const float* __restrict__ zref) {
   if (skip && *skip) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -108,10 +109,11 @@ __global__ void __launch_bounds__(128, 1) k_logits(const __grid_constant__ CUten
       float v[32];
       tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(cc * 32), v);
       if (r < n_rows) {
+        const float z0 = zref ? zref[r] : 0.0f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int c = col0 + cc * 32 + i;
-          if (c < n_cols) out[static_cast<long long>(c) * ldo + r] = v[i];
+          if (c < n_cols) out[static_cast<long long>(c) * ldo + r] = v[i] + z0;
         }
       }
     }
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(128) k_lr_parents(Dev D, LRArgs A, int run) {
   const int parent = D.i[R.o_parent + j];
   const float x = (t < R.d) ? D.f[R.o_x + static_cast<long long>(parent) * R.dpad + t] : 0.0f;
   A.xc[static_cast<long long>(j) * 128 + t] = x;
-  write_parts(A.parts, A.part_stride, j, t, x);
+  write_parts(A.parts, A.part_stride, j, t, (t < R.d) ? x - A.center[t] : 0.0f);
   if (t == 0) A.lc[j] = D.f[R.o_logL + parent];
   if (t < 6) D.i[R.o_stats + t * R.k + j] = 0;
 }
@@ -170,7 +172,31 @@ __global__ void __launch_bounds__(128) k_lr_live_parts(Dev D, LRArgs A, int run)
   const int s = blockIdx.x, t = threadIdx.x;
   if (s >= R.m) return;
   const float x = (t < R.d) ? D.f[R.o_x + static_cast<long long>(s) * R.dpad + t] : 0.0f;
-  write_parts(A.parts, A.part_stride, s, t, x);
+  write_parts(A.parts, A.part_stride, s, t, (t < R.d) ? x - A.center[t] : 0.0f);
+}
+
+// Centre of the contraction: the live-set mean mu (FP64 sums), and the
+// reference logits X mu (FP64 dot products), so that the tensor cores only
+// contract the small offsets x - mu.
+__global__ void __launch_bounds__(128) k_lr_center(Dev D, LRArgs A, int run) {
+  const RunDesc& R = D.desc[run];
+  if (D.st[run].done) return;
+  const int t = threadIdx.x;
+  double s = 0.0;
+  if (t < R.d)
+    for (int i = 0; i < R.m; ++i) s += (double)D.f[R.o_x + static_cast<long long>(i) * R.dpad + t];
+  A.center[t] = (t < R.d) ? static_cast<float>(s / R.m) : 0.0f;
+}
+
+__global__ void __launch_bounds__(256) k_lr_zref(Dev D, LRArgs A, int run) {
+  const RunDesc& R = D.desc[run];
+  if (D.st[run].done) return;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= R.n_data) return;
+  const __nv_bfloat16* xr = A.Xb + static_cast<long long>(n) * 128;
+  double s = 0.0;
+  for (int i = 0; i < R.d; ++i) s += (double)__bfloat162float(xr[i]) * (double)A.center[i];
+  A.zref[n] = static_cast<float>(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -460,9 +486,10 @@ cudaError_t setup_logits_attributes() {
 }
 
 cudaError_t launch_logits(const CUtensorMap& mapX, const CUtensorMap& mapU, int rows_pad, int cols_pad, float* out,
-                          long long ldo, int n_rows, int n_cols, int* err, const int* skip, cudaStream_t s) {
+                          long long ldo, int n_rows, int n_cols, int* err, const int* skip, const float* zref,
+                          cudaStream_t s) {
   dim3 grid(rows_pad / kTile, (n_cols + kTile - 1) / kTile);
-  k_logits<<<grid, 128, kLogitsSmem, s>>>(mapX, mapU, cols_pad, out, ldo, n_rows, n_cols, err, skip);
+  k_logits<<<grid, 128, kLogitsSmem, s>>>(mapX, mapU, cols_pad, out, ldo, n_rows, n_cols, err, skip, zref);
   return cudaGetLastError();
 }
 
@@ -470,6 +497,14 @@ cudaError_t launch_lr_parents(const Dev& D, const LRArgs& A, int run, int k, cud
   k_lr_parents<<<k, 128, 0, s>>>(D, A, run);
   return cudaGetLastError();
 }
+cudaError_t launch_lr_center(const Dev& D, const LRArgs& A, int run, int n_data, cudaStream_t s) {
+  k_lr_center<<<1, 128, 0, s>>>(D, A, run);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_lr_zref<<<(n_data + 255) / 256, 256, 0, s>>>(D, A, run);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lr_live_parts(const Dev& D, const LRArgs& A, int run, int m, cudaStream_t s) {
   k_lr_live_parts<<<m, 128, 0, s>>>(D, A, run);
   return cudaGetLastError();

@@ -920,7 +920,9 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
         seg[i] = (float)pr.a[i];
         seg[(R.o_b - R.o_a) + i] = (float)pr.b[i];
       }
-      if (lk.kind != NSS_LOGLIK_FLAT)
+      const bool has_mu = lk.kind == NSS_LOGLIK_GAUSS_ISO || lk.kind == NSS_LOGLIK_GMM_ISO_EQUAL ||
+                          lk.kind == NSS_LOGLIK_TEST_FAULT;
+      if (has_mu)
         for (int q = 0; q < R.n_comp; ++q)
           for (int i = 0; i < R.d; ++i) seg[(R.o_mu - R.o_a) + (size_t)q * R.dpad + i] = (float)lk.mu[(size_t)q * R.d + i];
       CKC(cudaMemcpyAsync(c->fpool + R.o_a, seg.data(), sizeof(float) * seg.size(), cudaMemcpyHostToDevice,

@@ -282,6 +282,32 @@ nss_status nss_get_profile(nss_ctx *ctx, nss_profile *prof);
    memory; runs on the default stream and synchronises. */
 nss_status nss_logreg_logits(const float *X, int n, int d, const float *U, int nu, float *Z);
 
+/* Volume simulation without allocation.  The paper has no counterpart: this
+   is a library convenience for callers that must not allocate device memory
+   when they need it, e.g. a service whose framework allocator owns and caches
+   the device memory, or latency-bound code that forbids cudaMalloc/cudaFree
+   (which synchronise the device) after start-up.  It computes what
+   nss_run/nss_finalise compute after the last iteration -- logZ mean and
+   standard deviation over n_sim simulated volume trajectories and the
+   normalised log posterior weights -- for a dead-point list the caller already
+   holds, and allocates nothing: its partial sums live in one fixed 2 MiB
+   __device__ array that every GPU loading this library keeps until the
+   process exits.
+     logL [n], nlive [n]      device inputs (death order, as nss_get_dead gives)
+     log_w [n]                device output
+     logZ_stats [2]           device output: logZ mean, logZ standard deviation
+     seed, run_id             the run's Philox key, as in nss_options
+     cuda_stream              stream for the work (NULL = legacy default stream)
+   Limits: 1 <= n <= 524288 dead points, 2 <= n_sim <= 128; larger sizes
+   return NSS_ERR_ARG.  The first call on a device looks up the array's device
+   address (cudaGetSymbolAddress) with that device current; make it before any
+   stream capture.  Every call shares the array and leaves its contents
+   behind; calls whose work overlaps on the GPU race on it, so order them.
+   Returns after enqueueing (no synchronisation). */
+nss_status nss_volume_sim_static(const float *logL, const int *nlive, long long n, int n_sim,
+                                 uint64_t seed, uint32_t run_id, double *log_w, double *logZ_stats,
+                                 void *cuda_stream);
+
 int nss_n_runs(const nss_ctx *ctx);
 /* Slice width actually used by a run (after the width rule). */
 double nss_run_width(const nss_ctx *ctx, int run);

@@ -1,0 +1,209 @@
+// nss_noalloc.cu -- the post-hoc volume simulation with fixed, preallocated
+// scratch, for callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc at the point where they need the
+// evidence of a finished run: a service whose framework allocator already
+// owns (and caches) the device memory, or latency-bound code that has a
+// no-allocation rule after start-up because cudaMalloc/cudaFree synchronise
+// the device and can stall every stream.  nss_volume_sim_static gives them
+// the same simulation as nss_run/nss_finalise, on device buffers they pass
+// in, with its per-tile partial sums kept in one file-scope __device__ array
+// instead of memory allocated per call.
+//
+// That array is shared by every call in the process and keeps the previous
+// call's contents; each call writes every entry it later reads, so nothing
+// has to start at zero.  Two calls whose kernels overlap on the GPU (for
+// example on two streams) race on it; the caller must order them.
+#include <cmath>
+#include <mutex>
+
+#include "../../include/nss.h"
+#include "nss_device.cuh"
+
+namespace nss {
+namespace {
+
+constexpr int kStaticMaxSim = 128;            // trajectories R
+constexpr int kStaticMaxTiles = 512;          // 512 x 1024 = 524288 dead points
+constexpr int kStaticMaxDead = kStaticMaxTiles * kVolTile;
+constexpr size_t kStaticSlab = (size_t)kStaticMaxSim * kStaticMaxTiles;
+constexpr size_t kStaticDoubles = 4 * kStaticSlab + 8;   // tsum, toff, tmax, tacc, misc
+
+// Held by every GPU that loads this library until the process exits (2 MiB).
+static __device__ __align__(256) double g_vol_scratch[kStaticDoubles];
+
+struct StaticVol {
+  const float* logL;
+  const int* nlive;
+  long long n;
+  int R, nt;
+  uint32_t k0, k1;
+  double *tsum, *toff, *tmax, *tacc, *misc;
+};
+
+__device__ __forceinline__ float svol_term(const StaticVol& V, int r, long long i) {
+  const uint4 b = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)(i >> 1), kTagVolsim, 0u), V.k0, V.k1);
+  const double u = (i & 1) ? u53(b.z, b.w) : u53(b.x, b.y);
+  return logf((float)u) / (float)V.nlive[i];
+}
+
+__global__ void k_svol_tilesum(StaticVol V) {
+  const int tile = blockIdx.x, r = threadIdx.x;
+  if (r >= V.R) return;
+  const long long i0 = (long long)tile * kVolTile, i1 = min(i0 + kVolTile, V.n);
+  double s = 0.0;
+  for (long long i = i0; i < i1; ++i) s += (double)svol_term(V, r, i);
+  V.tsum[(size_t)r * V.nt + tile] = s;
+}
+
+__global__ void k_svol_scan(StaticVol V) {
+  const int r = threadIdx.x;
+  if (r >= V.R) return;
+  double acc = 0.0;
+  for (int q = 0; q < V.nt; ++q) {
+    const size_t o = (size_t)r * V.nt + q;
+    V.toff[o] = acc;
+    acc += V.tsum[o];
+  }
+}
+
+__global__ void k_svol_weights(StaticVol V, double* __restrict__ lw) {
+  extern __shared__ double sh[];  // [blockDim][32]
+  const int tile = blockIdx.x, r = threadIdx.x;
+  const long long n = V.n;
+  const long long i0 = (long long)tile * kVolTile, i1 = min(i0 + kVolTile, n);
+  const bool act = r < V.R;
+  double prev = act ? V.toff[(size_t)r * V.nt + tile] : 0.0;
+  double cur = act ? prev + (double)svol_term(V, r, i0) : 0.0;
+  double M = -INFINITY, Sacc = 0.0;
+  const double ln2 = 0.69314718055994530942;
+  for (long long c0 = i0; c0 < i1; c0 += 32) {
+    const int cn = (int)min((long long)32, i1 - c0);
+    if (act) {
+      for (int q = 0; q < cn; ++q) {
+        const long long i = c0 + q;
+        double nxt = -INFINITY;
+        if (i + 1 < n) nxt = cur + (double)svol_term(V, r, i + 1);
+        const double ldx = prev + (double)logf(-expm1f((float)(nxt - prev))) - ln2;
+        const double v = (double)V.logL[i] + ldx;
+        if (v == -INFINITY) {
+        } else if (v > M) {
+          Sacc = Sacc * (double)expf((float)(M - v)) + 1.0;
+          M = v;
+        } else {
+          Sacc += (double)expf((float)(v - M));
+        }
+        sh[r * 32 + q] = ldx;
+        prev = cur;
+        cur = nxt;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < cn) {
+      double s = 0.0;
+      for (int q = 0; q < V.R; ++q) s += sh[q * 32 + threadIdx.x];
+      lw[c0 + threadIdx.x] = (double)V.logL[c0 + threadIdx.x] + s / (double)V.R;
+    }
+    __syncthreads();
+  }
+  if (act) {
+    V.tmax[(size_t)r * V.nt + tile] = M;
+    V.tacc[(size_t)r * V.nt + tile] = Sacc;
+  }
+}
+
+__global__ void k_svol_final(StaticVol V, const double* __restrict__ lw, double* __restrict__ stats) {
+  __shared__ double red[32];
+  __shared__ double lz[kStaticMaxSim];
+  for (int r = threadIdx.x; r < V.R; r += blockDim.x) {
+    double M = -INFINITY;
+    for (int q = 0; q < V.nt; ++q) M = fmax(M, V.tmax[(size_t)r * V.nt + q]);
+    double s = 0.0;
+    for (int q = 0; q < V.nt; ++q) {
+      const size_t o = (size_t)r * V.nt + q;
+      if (V.tmax[o] > -INFINITY) s += V.tacc[o] * exp(V.tmax[o] - M);
+    }
+    lz[r] = M + log(s);
+  }
+  __syncthreads();
+  double mean = 0.0;
+  for (int r = threadIdx.x; r < V.R; r += blockDim.x) mean += lz[r];
+  mean = block_sum_d(mean, red) / V.R;
+  double var = 0.0;
+  for (int r = threadIdx.x; r < V.R; r += blockDim.x) var += (lz[r] - mean) * (lz[r] - mean);
+  var = block_sum_d(var, red) / (V.R > 1 ? V.R - 1 : 1);
+  double mx = -INFINITY;
+  for (long long i = threadIdx.x; i < V.n; i += blockDim.x) mx = fmax(mx, lw[i]);
+  mx = block_max_d(mx, red);
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < V.n; i += blockDim.x) s += (double)expf((float)(lw[i] - mx));
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) {
+    stats[0] = mean;
+    stats[1] = sqrt(var);
+    V.misc[0] = mx + log(s);
+  }
+}
+
+__global__ void k_svol_norm(StaticVol V, double* __restrict__ lw) {
+  const double c = V.misc[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V.n; i += (long long)gridDim.x * blockDim.x)
+    lw[i] -= c;
+}
+
+// device address of the scratch array, looked up once per device
+std::mutex g_mu;
+double* g_dev_ptr[64] = {};
+
+cudaError_t scratch_for_current_device(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_dev_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_vol_scratch);
+    if (e != cudaSuccess) return e;
+    g_dev_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_dev_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace nss
+
+extern "C" nss_status nss_volume_sim_static(const float* logL, const int* nlive, long long n, int n_sim,
+                                            uint64_t seed, uint32_t run_id, double* log_w, double* logZ_stats,
+                                            void* cuda_stream) {
+  using namespace nss;
+  if (!logL || !nlive || !log_w || !logZ_stats) return NSS_ERR_ARG;
+  if (n < 1 || n > kStaticMaxDead) return NSS_ERR_ARG;
+  if (n_sim < 2 || n_sim > kStaticMaxSim) return NSS_ERR_ARG;
+  double* scratch = nullptr;
+  cudaError_t e = scratch_for_current_device(&scratch);
+  if (e != cudaSuccess) return NSS_ERR_CUDA;
+  StaticVol V;
+  V.logL = logL;
+  V.nlive = nlive;
+  V.n = n;
+  V.R = n_sim;
+  V.nt = (int)((n + kVolTile - 1) / kVolTile);
+  V.k0 = (uint32_t)seed;
+  V.k1 = (uint32_t)(seed >> 32) ^ run_id;
+  V.tsum = scratch;
+  V.toff = scratch + kStaticSlab;
+  V.tmax = scratch + 2 * kStaticSlab;
+  V.tacc = scratch + 3 * kStaticSlab;
+  V.misc = scratch + 4 * kStaticSlab;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int bt = (n_sim + 31) / 32 * 32;
+  k_svol_tilesum<<<V.nt, bt, 0, s>>>(V);
+  k_svol_scan<<<1, bt, 0, s>>>(V);
+  k_svol_weights<<<V.nt, bt, (size_t)bt * 32 * sizeof(double), s>>>(V, log_w);
+  k_svol_final<<<1, 256, 0, s>>>(V, log_w, logZ_stats);
+  k_svol_norm<<<64, 256, 0, s>>>(V, log_w);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? NSS_OK : NSS_ERR_CUDA;
+}

@@ -108,6 +108,8 @@ def lib():
     L.nss_get_profile.argtypes = [C.c_void_p, P(Profile)]
     L.nss_n_runs.argtypes = [C.c_void_p]
     L.nss_logreg_logits.argtypes = [_fp, C.c_int, C.c_int, _fp, C.c_int, _fp]
+    L.nss_volume_sim_static.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_uint64, C.c_uint32,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]
     L.nss_run_width.argtypes = [C.c_void_p, C.c_int]
     L.nss_run_width.restype = C.c_double
     L.nss_destroy.argtypes = [C.c_void_p]
@@ -172,6 +174,17 @@ class _Spec:
         for key, val in wl.extra.get("options", {}).items():
             setattr(o, key, val)
         self.opts = o
+
+
+def volume_sim_static(logL, nlive, n_sim, seed, run_id, log_w, logZ_stats, n=None, stream=None):
+    """Volume simulation into caller device buffers, with no device allocation
+    (fixed library scratch).  logL (float32), nlive (int32), log_w (float64)
+    and logZ_stats (float64, 2) are device tensors; n defaults to logL's size."""
+    n = int(logL.numel()) if n is None else int(n)
+    st = lib().nss_volume_sim_static(_ptr(logL), _ptr(nlive), n, int(n_sim), int(seed), int(run_id),
+                                     _ptr(log_w), _ptr(logZ_stats), stream)
+    if st != NSS_OK:
+        raise NSSError(st, "nss_volume_sim_static")
 
 
 def logreg_logits(X, U):

@@ -40,8 +40,15 @@ struct LRWork {
   nss::LRArgs args;
 };
 
+struct GPWork {
+  int run = -1;
+  float *t = nullptr, *y = nullptr;
+  nss::GPArgs args;
+};
+
 struct nss_ctx {
   int n_runs = 0;
+  std::vector<GPWork> gp;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<LRWork> lr;
@@ -248,7 +255,11 @@ nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m
         return set_err(c, NSS_ERR_ARG, "run %d: logistic regression takes the Gaussian prior", run);
       break;
     case NSS_LOGLIK_GP_RBF_WHITE:
-      return set_err(c, NSS_ERR_ARG, "run %d: likelihood kind %d is not built in this library", run, lk.kind);
+      if (!lk.gp_t || !lk.gp_y || lk.n_data < 1 || lk.n_data > 256)
+        return set_err(c, NSS_ERR_ARG, "run %d: GP needs gp_t, gp_y and 1 <= n_data <= 256", run);
+      if (pr.d != 3 || pr.kind != NSS_PRIOR_UNIFORM_BOX)
+        return set_err(c, NSS_ERR_ARG, "run %d: GP hyperparameters are 3 log-parameters under a box prior", run);
+      break;
     default:
       return set_err(c, NSS_ERR_ARG, "run %d: unknown likelihood kind %d", run, lk.kind);
   }
@@ -301,6 +312,10 @@ void free_ctx(nss_ctx* c) {
     cudaFree(w.center);
     cudaFree(w.zref);
     cudaFree(w.err);
+  }
+  for (auto& g : c->gp) {
+    cudaFree(g.t);
+    cudaFree(g.y);
   }
   if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -376,6 +391,11 @@ nss_status enqueue_iteration(nss_ctx* c) {
     CK(nss::launch_sweep(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->d_queue + q,
                          c->sweep_grid[q], c->stream), "sweep launch");
   }
+  for (auto& g : c->gp) {
+    const RunDesc& R = c->desc[g.run];
+    Rec r(c, NSS_K_SWEEP);
+    CK(nss::launch_gp_sweep(D, g.args, g.run, R.k, R.n_data, c->stream), "GP sweep launch");
+  }
   for (auto& w : c->lr) {
     const RunDesc& R = c->desc[w.run];
     const int* done = &c->d_state[w.run].done;
@@ -444,7 +464,7 @@ nss_status build_work(nss_ctx* c) {
     const RunDesc& R = c->desc[r];
     const int per = 32 / nss::cfg_g(R.cfg);
     for (int s = 0; s < R.m; s += per) c->init_items[R.cfg].push_back({r, s, std::min(s + per, R.m), 0});
-    if (R.lik_kind == nss::kLikLogreg) continue;  // swept by the tensor-core line path
+    if (R.lik_kind == nss::kLikLogreg || R.lik_kind == nss::kLikGp) continue;  // own sweep kernels
     for (int j = 0; j < R.k; j += per) c->sweep_items[R.cfg].push_back({r, j, std::min(j + per, R.k), 0});
   }
   for (int q = 0; q < nss::kNumCfgs; ++q) {
@@ -470,6 +490,35 @@ nss_status build_work(nss_ctx* c) {
      "descriptor upload");
   CK(cudaStreamSynchronize(c->stream), "work list upload");
   return NSS_OK;
+}
+
+nss_status gp_initial_loglik(nss_ctx* c, GPWork& g) {
+  const RunDesc& R = c->desc[g.run];
+  Rec rr(c, NSS_K_INIT);
+  CK(nss::launch_gp_init(dev_of(c), g.args, g.run, R.m, R.n_data, c->stream), "GP init launch");
+  return NSS_OK;
+}
+
+nss_status setup_gp(nss_ctx* c, int run, const nss_loglik& lk) {
+  const RunDesc& R = c->desc[run];
+  std::vector<float> t(R.n_data), y(R.n_data);
+  for (int i = 0; i < R.n_data; ++i) {
+    t[i] = (float)lk.gp_t[i];
+    y[i] = (float)lk.gp_y[i];
+  }
+  GPWork g;
+  g.run = run;
+  CK(cudaMalloc(&g.t, sizeof(float) * R.n_data), "GP data");
+  CK(cudaMalloc(&g.y, sizeof(float) * R.n_data), "GP data");
+  c->gp.push_back(g);
+  GPWork& G = c->gp.back();
+  CK(cudaMemcpyAsync(G.t, t.data(), sizeof(float) * R.n_data, cudaMemcpyHostToDevice, c->stream), "GP data upload");
+  CK(cudaMemcpyAsync(G.y, y.data(), sizeof(float) * R.n_data, cudaMemcpyHostToDevice, c->stream), "GP data upload");
+  CK(cudaStreamSynchronize(c->stream), "GP data upload");
+  c->prof.h2d_bytes += (long long)(2 * sizeof(float) * R.n_data);
+  G.args.t = G.t;
+  G.args.y = G.y;
+  return gp_initial_loglik(c, G);
 }
 
 // logL of the m initial live points of a logistic run: split, contract, reduce.
@@ -895,6 +944,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   CKC(cudaGetDevice(&c->device), "cudaGetDevice");
   CKC(nss::setup_kernel_attributes(), "kernel attributes");
   CKC(nss::setup_logits_attributes(), "kernel attributes");
+  CKC(nss::setup_gp_attributes(), "kernel attributes");
   CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
   CKC(cudaMalloc(&c->d_desc, sizeof(RunDesc) * n_runs), "descriptor allocation");
   CKC(cudaMalloc(&c->d_state, sizeof(RunState) * n_runs), "state allocation");
@@ -967,6 +1017,16 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
       std::fprintf(stderr, "nss_create: %s\n", c->err.c_str());
       free_ctx(c);
       return si;
+    }
+  }
+  // GP data and the initial likelihoods
+  for (int r = 0; r < n_runs; ++r) {
+    if (c->desc[r].lik_kind != nss::kLikGp) continue;
+    nss_status sg = setup_gp(c, r, loglik[r]);
+    if (sg != NSS_OK) {
+      std::fprintf(stderr, "nss_create: %s\n", c->err.c_str());
+      free_ctx(c);
+      return sg;
     }
   }
   // logistic-regression workspaces and the initial likelihoods
@@ -1045,6 +1105,8 @@ nss_status nss_reset(nss_ctx* c, const uint64_t* seeds) {
   if ((st = launch_inits(c)) != NSS_OK) return st;
   for (auto& w : c->lr)
     if ((st = lr_initial_loglik(c, w)) != NSS_OK) return st;
+  for (auto& g : c->gp)
+    if ((st = gp_initial_loglik(c, g)) != NSS_OK) return st;
   return NSS_OK;
 }
 

@@ -1,0 +1,252 @@
+// nss_gp.cu -- Gaussian-process hyperparameter likelihood inside the HRSS
+// sweep (the GP workloads of Sec. 4.3; the sweep of Sec. 3.2 / App. B.4),
+// for sm_103a.
+//
+// theta = (ln l, ln a, ln s); for data (t_i, y_i), i < n,
+//   K_ij = a^2 exp(-(t_i - t_j)^2 / (2 l^2)) + s^2 [i == j],
+//   log p(y | theta) = -1/2 y^T K^-1 y - sum_i ln L_ii - n/2 ln 2 pi,  K = L L^T.
+// One block of 1024 threads owns one chain and evaluates its candidates one
+// after another.  An evaluation fills the bordered matrix [[K, .], [y^T, .]]
+// (n + 1 rows, packed lower triangle in shared memory, FP32) and factors it
+// by right-looking column steps; the last row then holds alpha = L^-1 y, so
+// y^T K^-1 y = |alpha|^2.  ln det and |alpha|^2 are accumulated in FP64.  A
+// non-positive pivot (FP32 breakdown of an ill-conditioned K) makes the
+// candidate's logL = -inf; it is counted with the NaN evaluations.
+#include <cfloat>
+#include <cmath>
+
+#include "nss_device.cuh"
+#include "nss_kernels.h"
+
+namespace nss {
+
+constexpr int kGPThreads = 1024;
+constexpr int kGPMaxN = 256;
+
+__device__ __forceinline__ int pidx(int i, int j) { return (i * (i + 1)) / 2 + j; }
+
+struct GPShared {
+  float inv;
+  int ok;
+  double red[32];
+};
+
+// logL of theta for the run's data; every thread of the block calls it and
+// gets the same value.  P: packed (n+1) x (n+1) lower triangle.
+__device__ float gp_loglik(const float* __restrict__ tt, const float* __restrict__ yy, int n, const float th[3],
+                           float* P, GPShared& sh) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const float ell = expf(th[0]), amp = expf(th[1]), sn = expf(th[2]);
+  const float a2 = amp * amp, s2 = sn * sn, c = -0.5f / (ell * ell);
+  const int N = n + 1;
+  // fill
+  const int tot = (N * (N + 1)) / 2;
+  for (int e = tid; e < tot; e += T) {
+    // row i of linear index e: i(i+1)/2 <= e
+    int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while ((i * (i + 1)) / 2 > e) --i;
+    while (((i + 1) * (i + 2)) / 2 <= e) ++i;
+    const int j = e - (i * (i + 1)) / 2;
+    float v;
+    if (i < n) {
+      const float dt = tt[i] - tt[j];
+      v = a2 * expf(c * dt * dt) + (i == j ? s2 : 0.0f);
+    } else {
+      v = (j < n) ? yy[j] : 0.0f;
+    }
+    P[e] = v;
+  }
+  if (tid == 0) sh.ok = 1;
+  __syncthreads();
+  // right-looking column steps; thread (kc, rr): column j+1+kc, rows kc+rr, +4, ...
+  const int kc = tid >> 2, rr = tid & 3;
+  double ldet = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const float d = P[pidx(j, j)];
+      const bool good = d > 0.0f && isfinite(d);
+      const float l = sqrtf(good ? d : 1.0f);
+      P[pidx(j, j)] = l;
+      sh.inv = 1.0f / l;
+      if (!good) sh.ok = 0;
+    }
+    __syncthreads();
+    if (!sh.ok) break;
+    const float inv = sh.inv;
+    for (int i = j + 1 + tid; i < N; i += T) P[pidx(i, j)] *= inv;
+    if (tid == 0) ldet += (double)logf(P[pidx(j, j)]);
+    __syncthreads();
+    const int k = j + 1 + kc;
+    if (k < n) {
+      const float lk = P[pidx(k, j)];
+      for (int i = k + rr; i < N; i += 4) P[pidx(i, k)] = fmaf(-P[pidx(i, j)], lk, P[pidx(i, k)]);
+    }
+    __syncthreads();
+  }
+  const int ok = sh.ok;
+  __syncthreads();
+  if (!ok) return -INFINITY;
+  // |alpha|^2 from the last row, FP64 accumulation
+  double q = 0.0;
+  for (int j = tid; j < n; j += T) {
+    const double a = (double)P[pidx(n, j)];
+    q += a * a;
+  }
+  q = block_sum_d(q, sh.red);
+  if (tid == 0) sh.red[31] = ldet;
+  __syncthreads();
+  const double ld = sh.red[31];
+  __syncthreads();
+  const double ll = -0.5 * q - ld - 0.5 * (double)n * 1.8378770664093454836;
+  return (float)ll;
+}
+
+// Initial live set: logL of every prior draw (block per slot).
+__global__ void __launch_bounds__(kGPThreads) k_gp_init(Dev D, GPArgs A, int run) {
+  extern __shared__ float P[];
+  __shared__ GPShared sh;
+  const RunDesc& R = D.desc[run];
+  const int s = blockIdx.x;
+  if (s >= R.m) return;
+  float th[3];
+  for (int i = 0; i < 3; ++i) th[i] = D.f[R.o_x + (long long)s * R.dpad + i];
+  float ll = gp_loglik(A.t, A.y, R.n_data, th, P, sh);
+  if (isnan(ll)) ll = -INFINITY;
+  if (threadIdx.x == 0) D.f[R.o_logL + s] = ll;
+}
+
+// p HRSS steps of chain j (block j), then replacement of its dead slot.
+__global__ void __launch_bounds__(kGPThreads) k_gp_sweep(Dev D, GPArgs A, int run) {
+  extern __shared__ float P[];
+  __shared__ GPShared sh;
+  const RunDesc& R = D.desc[run];
+  RunState* S = D.st + run;
+  if (S->done) return;
+  const int j = blockIdx.x;
+  if (j >= R.k) return;
+  const int d = R.d;  // 3
+  const uint32_t iter = (uint32_t)S->iter;
+  const float lstar = S->logLstar;
+  const int parent = D.i[R.o_parent + j];
+  float x[3], a[3], b[3];
+  for (int i = 0; i < 3; ++i) {
+    x[i] = D.f[R.o_x + (long long)parent * R.dpad + i];
+    a[i] = D.f[R.o_a + i];
+    b[i] = D.f[R.o_b + i];
+  }
+  float lx = D.f[R.o_logL + parent];
+  float Lm[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) Lm[r][q] = D.f[R.o_L + r * R.dpad + q];
+  const float w = R.w;
+  const uint32_t nz = 4u;  // 2 ceil(3/2)
+  int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
+  for (int s = 0; s < R.p; ++s) {
+    const uint4 w0 = draw_block(R, iter, (uint32_t)j, (uint32_t)s, 0u);
+    const uint4 w1 = draw_block(R, iter, (uint32_t)j, (uint32_t)s, 1u);
+    float z[4];
+    box_muller(w0.x, w0.y, z[0], z[1]);
+    box_muller(w0.z, w0.w, z[2], z[3]);
+    const float zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
+    float v[3];
+    for (int r = 0; r < 3; ++r) v[r] = Lm[r][0] * z[0] + Lm[r][1] * z[1] + Lm[r][2] * z[2];
+    float inrm;
+    if (R.dir_norm == 0) inrm = rsqrtf(zz);
+    else inrm = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int r = 0; r < 3; ++r) v[r] *= inrm;
+    // words: U = word nz (block 1 lane 0), shrink r = word nz + 3 + r
+    uint32_t cblk = 1u;
+    uint4 cw = w1;
+    auto word = [&](uint32_t wi) {
+      if ((wi >> 2) != cblk) {
+        cblk = wi >> 2;
+        cw = draw_block(R, iter, (uint32_t)j, (uint32_t)s, cblk);
+      }
+      return pick(cw, wi & 3u);
+    };
+    auto in_slice = [&](float t, float& ll) {
+      float y[3];
+      bool in = true;
+      for (int r = 0; r < 3; ++r) {
+        y[r] = fmaf(t, v[r], x[r]);
+        if (!(y[r] >= a[r] && y[r] <= b[r])) in = false;
+      }
+      ++evals;
+      if (!in) return false;
+      ll = gp_loglik(A.t, A.y, R.n_data, y, P, sh);
+      if (isnan(ll) || ll == -INFINITY) {  // FP32 breakdown of K (or NaN): outside every slice
+        ++nanc;
+        ll = -INFINITY;
+      }
+      return ll > lstar;
+    };
+    const float U = u24(word(nz));
+    float tl = -w * U, tr = tl + w, lly = 0.0f;
+    for (int n = 0;; ++n) {
+      if (n >= kStepOutCap) { ++capo; break; }
+      if (!in_slice(tl, lly)) break;
+      tl -= w;
+      ++exps;
+    }
+    for (int n = 0;; ++n) {
+      if (n >= kStepOutCap) { ++capo; break; }
+      if (!in_slice(tr, lly)) break;
+      tr += w;
+      ++exps;
+    }
+    bool ok = false;
+    for (int r = 0; r < kShrinkCap; ++r) {
+      const float u = u24(word(nz + 3u + (uint32_t)r));
+      const float t = fmaf(u, tr - tl, tl);
+      ++shr;
+      if (in_slice(t, lly)) {
+        for (int q = 0; q < 3; ++q) x[q] = fmaf(t, v[q], x[q]);
+        lx = lly;
+        ok = true;
+        break;
+      }
+      if (t < 0.0f) tl = t;
+      else tr = t;
+    }
+    if (ok) ++acc;
+    else ++nul;
+  }
+  const int slot = D.i[R.o_dead + j];
+  if (threadIdx.x < R.dpad) D.f[R.o_x + (long long)slot * R.dpad + threadIdx.x] = (threadIdx.x < d) ? x[threadIdx.x] : 0.0f;
+  if (threadIdx.x == 0) {
+    D.f[R.o_logL + slot] = lx;
+    D.f[R.o_birth + slot] = lstar;
+    int* st = D.i + R.o_stats;
+    st[j] = evals;
+    st[R.k + j] = acc;
+    st[2 * R.k + j] = nul;
+    st[3 * R.k + j] = exps;
+    st[4 * R.k + j] = shr;
+    st[5 * R.k + j] = capo;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&S->evals), (unsigned long long)evals);
+    if (nul) atomicAdd(reinterpret_cast<unsigned long long*>(&S->nulls), (unsigned long long)nul);
+    if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&S->cap_out), (unsigned long long)capo);
+    if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&S->nan_evals), (unsigned long long)nanc);
+  }
+}
+
+size_t gp_smem_bytes(int n) { return sizeof(float) * (size_t)((n + 1) * (n + 2) / 2); }
+
+cudaError_t setup_gp_attributes() {
+  const int bytes = (int)gp_smem_bytes(kGPMaxN);
+  cudaError_t e = cudaFuncSetAttribute(k_gp_init, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gp_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_gp_init(const Dev& D, const GPArgs& A, int run, int m, int n, cudaStream_t s) {
+  k_gp_init<<<m, kGPThreads, gp_smem_bytes(n), s>>>(D, A, run);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gp_sweep(const Dev& D, const GPArgs& A, int run, int k, int n, cudaStream_t s) {
+  k_gp_sweep<<<k, kGPThreads, gp_smem_bytes(n), s>>>(D, A, run);
+  return cudaGetLastError();
+}
+
+}  // namespace nss

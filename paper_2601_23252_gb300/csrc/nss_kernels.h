@@ -31,6 +31,15 @@ struct LRArgs {
   float* zref;             // [rows_pad] X mu
 };
 
+// Device data of one GP run: inputs and targets (FP32).
+struct GPArgs {
+  const float* t;
+  const float* y;
+};
+cudaError_t setup_gp_attributes();
+cudaError_t launch_gp_init(const Dev& D, const GPArgs& A, int run, int m, int n, cudaStream_t s);
+cudaError_t launch_gp_sweep(const Dev& D, const GPArgs& A, int run, int k, int n, cudaStream_t s);
+
 // one-time function attributes (dynamic shared memory above 48 KB)
 cudaError_t setup_kernel_attributes();
 cudaError_t setup_logits_attributes();

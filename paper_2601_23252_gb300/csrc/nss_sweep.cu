@@ -329,8 +329,8 @@ __global__ void __launch_bounds__(128) k_init(Dev D, const WorkItem* __restrict_
         if (dim < R.d) x[i] = fmaf(D.f[R.o_b + dim], z[i], D.f[R.o_a + dim]);
       }
     }
-    float ll = 0.0f;  // logistic regression: filled by the contraction pass
-    if (R.lik_kind != kLikLogreg) {
+    float ll = 0.0f;  // logistic regression and GP: filled by their own init pass
+    if (R.lik_kind != kLikLogreg && R.lik_kind != kLikGp) {
       Lik<G, DPL> L;
       L.init(R, D.f, gl, has);
       ll = L.eval(R, D.f, x, gl, has, mask);

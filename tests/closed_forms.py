@@ -39,3 +39,26 @@ def rastrigin_logZ(alpha, d, r=5.14, A=10.0):
     t1 = np.log(alpha) + d * np.log(i1) if alpha > 0 else -np.inf
     t2 = np.log1p(-alpha) + d * np.log(i2) if alpha < 1 else -np.inf
     return float(np.logaddexp(t1, t2) - d * np.log(2 * r))
+
+
+def gp_quadrature_logZ(loglik, a, b, panels=8, order=6):
+    """Evidence of a 3-parameter likelihood under a uniform box prior by
+    composite Gauss-Legendre quadrature (panels x order nodes per axis):
+    Z = (1/vol) int_box L(theta) d theta, evaluated in log space."""
+    xq, wq = np.polynomial.legendre.leggauss(order)
+    axes = []
+    for lo, hi in zip(a, b):
+        edges = np.linspace(lo, hi, panels + 1)
+        pts = np.concatenate([(e0 + e1) / 2 + (e1 - e0) / 2 * xq for e0, e1 in zip(edges[:-1], edges[1:])])
+        wts = np.concatenate([(e1 - e0) / 2 * wq for e0, e1 in zip(edges[:-1], edges[1:])])
+        axes.append((pts, wts))
+    lv = []
+    lw = []
+    for p0, w0 in zip(*axes[0]):
+        for p1, w1 in zip(*axes[1]):
+            for p2, w2 in zip(*axes[2]):
+                lv.append(loglik(np.array([p0, p1, p2])))
+                lw.append(np.log(w0 * w1 * w2))
+    lv, lw = np.array(lv), np.array(lw)
+    vol = np.prod(np.asarray(b) - np.asarray(a))
+    return float(special.logsumexp(lv + lw) - np.log(vol))

@@ -20,7 +20,9 @@ from paper_2601_23252_gb300 import workloads as W
 #   logreg (N rows, |z| ~ 3..10): FP32 logits 1e-6 |z| per row, FP32 sums of
 #   N terms of ~1 nat, fast exp/log in softplus: ~sqrt(N) 1e-5 -> 2e-3 (N=1e3), 1e-2 (N=1e4)
 TIES = {"gauss_d2": (2e-5, 2e-5, 2e-6), "gmm_d32": (1e-3, 1e-3, 2e-6), "batch64": (5e-3, 5e-3, 2e-6),
-        "gauss20": (5e-4, 5e-4, 2e-6), "logreg_small": (2e-3, 1e-4, 0.0), "logreg_d100": (1e-2, 1e-4, 0.0)}
+        "gauss20": (5e-4, 5e-4, 2e-6), "logreg_small": (2e-3, 1e-4, 0.0), "logreg_d100": (1e-2, 1e-4, 0.0),
+        "gp_d3": (2e-3, 0.0, 2e-6)}
+#   gp_d3 (FP32 Cholesky of K, n <= 256, logL ~ 1e1..1e2): ~1e-4 |logL| -> 2e-3 (well-conditioned K)
 
 
 def oracle_problem(wl):

@@ -1,0 +1,76 @@
+"""GP hyperparameter likelihood on the GPU (RBF + white kernel, FP32
+Cholesky of the bordered kernel matrix, FP64 log-determinant): initial
+likelihoods against the FP64 checker, one-step parity, and evidences
+against brute-force 3-D quadrature."""
+import numpy as np
+import pytest
+
+import oracle as O
+from closed_forms import gp_quadrature_logZ
+from parity import compare_step, near_tie_mask, oracle_opts, oracle_problem
+from paper_2601_23252_gb300 import native
+from paper_2601_23252_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+COUNTERS = ("evals", "accepts", "nulls", "expansions", "shrinks", "cap_out")
+
+
+def test_initial_logL_matches_checker_full_size(gpu_lib):
+    wl = W.gp_d3(seed=1)  # n = 256
+    with native.Sampler(wl) as s:
+        st = s.export_state()
+    pb = oracle_problem(wl)
+    ref = pb.loglik(st["x"].astype(np.float64))
+    good = st["x"][:, 2] > np.log(0.03)   # noise level keeps K well conditioned for FP32
+    err = np.abs(st["logL"][good] - ref[good]) / np.maximum(1.0, np.abs(ref[good]))
+    print(f"\nGP initial logL: {good.sum()} well-conditioned points, max rel err {err.max():.2e}; "
+          f"FP32 breakdowns {np.sum(st['logL'] == -np.inf)} of {wl.n_live}")
+    assert err.max() < 1e-3
+    # breakdowns only where the checker's FP64 value is hopeless anyway
+    bad = st["logL"] == -np.inf
+    assert np.all(ref[bad] < np.median(ref))
+
+
+@pytest.mark.parametrize("seed,warm", [(1, 3), (2, 8)])
+def test_one_step_parity_gp(gpu_lib, seed, warm):
+    wl = W.gp_d3(seed=seed, n=64).with_(n_live=200, k=100)
+    rep = compare_step(wl, warm)
+    g, t = rep["gpu"], rep["orc"]
+    assert np.array_equal(g["dead_idx"], t["dead_idx"])
+    assert np.array_equal(g["parent"], t["parent"])
+    tie = near_tie_mask(rep, "gp_d3")
+    same = np.ones(wl.k, bool)
+    for c in COUNTERS:
+        same &= g[c] == t[c]
+    ok = same & ~tie
+    xerr = np.abs(g["new_x"][ok] - t["new_x"][ok]).max()
+    lerr = (np.abs(g["new_logL"][ok] - t["new_logL"][ok]) / np.maximum(1, np.abs(t["new_logL"][ok]))).max()
+    print(f"\nGP seed={seed} warm={warm}: ties {tie.mean():.3f} mismatch {np.mean(~same):.3f} "
+          f"x err {xerr:.2e} logL rel err {lerr:.2e}")
+    assert np.all(same | tie)
+    assert ok.mean() > 0.8
+    assert xerr < 1e-4
+    assert lerr < 1e-3
+
+
+def test_gp_evidence_matches_quadrature(gpu_lib):
+    wl = W.gp_d3(seed=2, n=24).with_(n_live=200, k=100)
+    pb = oracle_problem(wl)
+    truth = gp_quadrature_logZ(pb.loglik, wl.a, wl.b, panels=10, order=6)
+    wls = [wl.with_(seed=s) for s in range(8)]
+    with native.Sampler(wls) as smp:
+        res = smp.run()
+    lz = np.array([r["logZ"] for r in res]); err = np.array([r["logZ_err"] for r in res])
+    print(f"\nGP evidence: quadrature {truth:.4f}, gpu mean {lz.mean():.4f} (err {err.mean():.3f})")
+    assert np.all(np.abs(lz - truth) < 3.5 * err + 0.02)
+    assert abs(lz.mean() - truth) < 3 * lz.std(ddof=1) / np.sqrt(len(lz)) + 0.05
+
+
+def test_gp_full_size_run_completes(gpu_lib):
+    wl = W.gp_d3(seed=0)
+    with native.Sampler(wl) as s:
+        res = s.run()[0]
+    print(f"\nGP full size (n=256, m=500, k=250, p=15): logZ {res['logZ']:.3f} +- {res['logZ_err']:.3f}, "
+          f"{res['iters']} iterations, {res['evals']} evals, {res['nan_evals']} FP32 breakdowns")
+    assert res["status"] == 0 and np.isfinite(res["logZ"])

@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--ncu-case", action="store_true",
                     help="no timing: the bench batch for a few iterations, small dead stores "
                          "(the case captured by ncu)")
+    ap.add_argument("--ncu-case-logreg", action="store_true",
+                    help="no timing: one outer iteration of the full-size logistic-regression "
+                         "workload (d=100, N=10000, k=1000, p=200), for ncu captures of its kernels")
     return ap.parse_args()
 
 
@@ -376,10 +379,22 @@ def run_ncu_case(args):
     return 0
 
 
+def run_ncu_case_logreg(args):
+    from paper_2601_23252_gb300 import native
+    from paper_2601_23252_gb300 import workloads as W
+    wl = W.logreg_d100(seed=0).with_(extra={"options": {"dead_capacity": 4 * 1000 + 2000}})
+    with native.Sampler(wl) as s:
+        s.set_profiling(True)   # launch by launch (no graph), so ncu sees each kernel
+        s.step()
+    return 0
+
+
 def main():
     args = parse()
     if args.ncu_case:
         return run_ncu_case(args)
+    if args.ncu_case_logreg:
+        return run_ncu_case_logreg(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

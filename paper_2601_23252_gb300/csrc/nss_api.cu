@@ -243,8 +243,8 @@ nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m
         return set_err(c, NSS_ERR_ARG, "run %d: fault_mode must be 1 or 2", run);
       break;
     case NSS_LOGLIK_GMM_ISO_EQUAL:
-      if (!lk.mu || !(lk.sigma > 0) || lk.n_comp < 1)
-        return set_err(c, NSS_ERR_ARG, "run %d: mixture needs mu, sigma > 0, n_comp >= 1", run);
+      if (!lk.mu || !(lk.sigma > 0) || lk.n_comp < 1 || lk.n_comp > 8)
+        return set_err(c, NSS_ERR_ARG, "run %d: mixture needs mu, sigma > 0, 1 <= n_comp <= 8", run);
       break;
     case NSS_LOGLIK_FLAT:
       break;

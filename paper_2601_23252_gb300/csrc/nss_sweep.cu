@@ -197,54 +197,6 @@ struct Lik {
   }
 };
 
-// ---- per-chain constants ---------------------------------------------------
-template <int DPL>
-struct ChainConst {
-  float a[DPL], b[DPL], ib[DPL];
-  bool own[DPL];
-  float lstar;
-  bool box, nonflat;
-};
-
-template <int G, int DPL>
-__device__ __forceinline__ float group_logprior(const RunDesc& R, const ChainConst<DPL>& C,
-                                                const float (&y)[DPL], unsigned mask) {
-  float s = 0.0f;
-#pragma unroll
-  for (int i = 0; i < DPL; ++i)
-    if (C.own[i]) {
-      const float u = (y[i] - C.a[i]) * C.ib[i];
-      s = fmaf(-0.5f * u, u, s);
-    }
-  return gsum<G>(s, mask) + R.prior_const;
-}
-
-// One logical likelihood evaluation: y is in the slice when it lies in the
-// prior support, above the prior slice height (non-flat prior) and strictly
-// above logL* (Sec. 3.1: E < E_batch).  The decision is uniform over the group.
-template <int G, int DPL>
-__device__ __forceinline__ bool in_slice(const RunDesc& R, const float* __restrict__ f, const Lik<G, DPL>& L,
-                                         const ChainConst<DPL>& C, const float (&y)[DPL], float height, int gl,
-                                         bool has, unsigned mask, float& ll, int& nan_cnt) {
-  if (C.box) {
-    bool out = false;
-#pragma unroll
-    for (int i = 0; i < DPL; ++i)
-      if (C.own[i] && !(y[i] >= C.a[i] && y[i] <= C.b[i])) out = true;
-    if (__any_sync(mask, out)) return false;
-  }
-  if (C.nonflat) {
-    const float lp = group_logprior<G, DPL>(R, C, y, mask);
-    if (!(lp > height)) return false;
-  }
-  ll = L.eval(R, f, y, gl, has, mask);
-  if (isnan(ll)) {
-    ll = -INFINITY;
-    ++nan_cnt;
-  }
-  return ll > C.lstar;
-}
-
 // The words of one HRSS step: group lane b computes Philox block b of the
 // step's counter stream (iteration, chain, step, b) once; a word w < 4G is
 // then read from lane w/4 by a shuffle, a later word (a shrinkage proposal
@@ -346,7 +298,18 @@ __global__ void __launch_bounds__(128) k_init(Dev D, const WorkItem* __restrict_
 
 // ---------------------------------------------------------------------------
 // One chain: p HRSS steps from its parent, then replacement of dead slot j.
+//
+// Along the line y(t) = x + t v every quantity of the slice test is a
+// polynomial in t of degree <= 2, so once per step the group reduces the
+// coefficients and every evaluation of that step is scalar arithmetic:
+//   |y - mu_c|^2 = D_c + t (2 E_c + t C),  D_c = |x - mu_c|^2,
+//                  E_c = (x - mu_c).v,  C = |v|^2;
+//   box support:   a <= y <= b  <=>  t_lo <= t <= t_hi;
+//   Gaussian prior: sum ((y - a)/b)^2 = P0 + t (2 P1 + t P2).
+// The moved point x + t v is formed coordinate by coordinate on acceptance.
 // ---------------------------------------------------------------------------
+constexpr int kMaxComp = 8;
+
 template <int G, int DPL>
 __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j, int gl, unsigned mask,
                             float* zs) {
@@ -355,20 +318,13 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   const bool has = gl * DPL < ld;
   const int parent = D.i[R.o_parent + j];
   const uint32_t iter = (uint32_t)Sw->iter;
-  ChainConst<DPL> C;
-  C.box = R.prior_kind == kPriorBox;
-  C.nonflat = !C.box;
-  C.lstar = Sw->logLstar;
+  const float lstar = Sw->logLstar;
+  const bool box = R.prior_kind == kPriorBox, nonflat = !box;
+  const int lk = R.lik_kind;
+  const int K = (lk == kLikGmm) ? R.n_comp : ((lk == kLikGauss || lk == kLikFault) ? 1 : 0);
+  bool own[DPL];
 #pragma unroll
-  for (int i = 0; i < DPL; ++i) {
-    const int dim = gl * DPL + i;
-    C.own[i] = dim < d;
-    C.a[i] = C.own[i] ? f[R.o_a + dim] : 0.f;
-    C.b[i] = C.own[i] ? f[R.o_b + dim] : 1.f;
-    C.ib[i] = 1.0f / C.b[i];
-  }
-  Lik<G, DPL> L;
-  L.init(R, f, gl, has);
+  for (int i = 0; i < DPL; ++i) own[i] = gl * DPL + i < d;
   float x[DPL];
 #pragma unroll
   for (int i = 0; i < DPL; ++i) x[i] = 0.0f;
@@ -389,15 +345,15 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     float zz = 0.0f;
 #pragma unroll
     for (int i = 0; i < DPL; ++i) {
-      if (!C.own[i]) z[i] = 0.0f;
+      if (!own[i]) z[i] = 0.0f;
       zs[gl * DPL + i] = z[i];
       zz = fmaf(z[i], z[i], zz);
     }
     __syncwarp(mask);
     zz = gsum<G>(zz, mask);
-    float dt[DPL];
+    float v[DPL];
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) dt[i] = 0.0f;
+    for (int i = 0; i < DPL; ++i) v[i] = 0.0f;
     if (has) {
       const int row0 = gl * DPL;
       const int nb = ((row0 + DPL - 1) >> 2) + 1;
@@ -406,7 +362,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
 #pragma unroll
         for (int r = 0; r < DPL; ++r) {
           const float4 l4 = __ldg(L4 + (row0 + r) * ld4 + bb);
-          dt[r] = fmaf(l4.x, zb.x, fmaf(l4.y, zb.y, fmaf(l4.z, zb.z, fmaf(l4.w, zb.w, dt[r]))));
+          v[r] = fmaf(l4.x, zb.x, fmaf(l4.y, zb.y, fmaf(l4.z, zb.z, fmaf(l4.w, zb.w, v[r]))));
         }
       }
     }
@@ -417,38 +373,132 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     } else {
       float dd = 0.0f;
 #pragma unroll
-      for (int i = 0; i < DPL; ++i) dd = fmaf(dt[i], dt[i], dd);
+      for (int i = 0; i < DPL; ++i) dd = fmaf(v[i], v[i], dd);
       inrm = rsqrtf(gsum<G>(dd, mask));
     }
-    float v[DPL];
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) v[i] = dt[i] * inrm;
-    float height = 0.0f;
-    if (C.nonflat) {
-      const float uh = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz + 1u, mask));
-      height = group_logprior<G, DPL>(R, C, x, mask) + logf(uh);
+    for (int i = 0; i < DPL; ++i) v[i] *= inrm;
+
+    // coefficients of the step's line, reduced over the group
+    float Cv = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) Cv = fmaf(v[i], v[i], Cv);
+    Cv = gsum<G>(Cv, mask);
+    float Dc[kMaxComp], Ec[kMaxComp];
+#pragma unroll
+    for (int c = 0; c < kMaxComp; ++c) {
+      Dc[c] = 0.0f;
+      Ec[c] = 0.0f;
+      if (c < K) {
+        float m[DPL];
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) m[i] = 0.0f;
+        if (has) ldg_lane<DPL>(f + R.o_mu + (long long)c * ld, gl, m);
+        float dq = 0.0f, de = 0.0f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) {
+          const float e = x[i] - m[i];
+          dq = fmaf(e, e, dq);
+          de = fmaf(e, v[i], de);
+        }
+        Dc[c] = gsum<G>(dq, mask);
+        Ec[c] = gsum<G>(de, mask);
+      }
     }
+    float t_lo = -INFINITY, t_hi = INFINITY;
+    float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f, height = 0.0f;
+    if (box) {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) {
+        if (own[i]) {
+          const int dim = gl * DPL + i;
+          const float ai = f[R.o_a + dim] - x[i], bi = f[R.o_b + dim] - x[i];
+          if (v[i] > 0.0f) {
+            t_lo = fmaxf(t_lo, ai / v[i]);
+            t_hi = fminf(t_hi, bi / v[i]);
+          } else if (v[i] < 0.0f) {
+            t_lo = fmaxf(t_lo, bi / v[i]);
+            t_hi = fminf(t_hi, ai / v[i]);
+          } else if (!(ai <= 0.0f && bi >= 0.0f)) {
+            t_lo = INFINITY;
+          }
+        }
+      }
+      t_lo = gmax<G>(t_lo, mask);
+      t_hi = -gmax<G>(-t_hi, mask);
+    } else {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) {
+        if (own[i]) {
+          const int dim = gl * DPL + i;
+          const float ib = 1.0f / f[R.o_b + dim];
+          const float u = (x[i] - f[R.o_a + dim]) * ib, q = v[i] * ib;
+          P0 = fmaf(u, u, P0);
+          P1 = fmaf(u, q, P1);
+          P2 = fmaf(q, q, P2);
+        }
+      }
+      P0 = gsum<G>(P0, mask);
+      P1 = gsum<G>(P1, mask);
+      P2 = gsum<G>(P2, mask);
+      const float uh = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz + 1u, mask));
+      height = fmaf(-0.5f, P0, R.prior_const) + logf(uh);
+    }
+    float x0 = 0.0f, v0 = 0.0f;  // coordinate 0 for the fault likelihood
+    if (lk == kLikFault) {
+      x0 = __shfl_sync(mask, x[0], 0, G);
+      v0 = __shfl_sync(mask, v[0], 0, G);
+    }
+    // one logical likelihood evaluation at x + t v: support, prior slice
+    // height, then logL > logL* (Sec. 3.1: E < E_batch)
+    auto in_slice = [&](float t, float& ll) -> bool {
+      ++evals;
+      if (box && !(t >= t_lo && t <= t_hi)) return false;
+      if (nonflat) {
+        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
+        if (!(lp > height)) return false;
+      }
+      if (lk == kLikFlat) {
+        ll = 0.0f;
+      } else {
+        float M = -INFINITY, S = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kMaxComp; ++c) {
+          if (c < K) {
+            const float q = fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]);
+            const float vc = -q * R.inv2s2;
+            if (vc > M) {
+              S = S * __expf(M - vc) + 1.0f;
+              M = vc;
+            } else {
+              S += __expf(vc - M);
+            }
+          }
+        }
+        ll = (K == 1 ? M : M + __logf(S)) + R.lognorm;
+        if (lk == kLikFault && fmaf(t, v0, x0) < R.fault_param)
+          ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
+      }
+      if (isnan(ll)) {
+        ll = -INFINITY;
+        ++nanc;
+      }
+      return ll > lstar;
+    };
     // randomised initial bracket of width w around t = 0
     const float U = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz, mask));
     float tl = -w * U;
     float tr = tl + w;
-    float y[DPL], lly;
-    // stepping out, at most 10 expansions per side
+    float lly = 0.0f;
     for (int n = 0;; ++n) {
       if (n >= kStepOutCap) { ++capo; break; }
-#pragma unroll
-      for (int i = 0; i < DPL; ++i) y[i] = fmaf(tl, v[i], x[i]);
-      ++evals;
-      if (!in_slice<G, DPL>(R, f, L, C, y, height, gl, has, mask, lly, nanc)) break;
+      if (!in_slice(tl, lly)) break;
       tl -= w;
       ++exps;
     }
     for (int n = 0;; ++n) {
       if (n >= kStepOutCap) { ++capo; break; }
-#pragma unroll
-      for (int i = 0; i < DPL; ++i) y[i] = fmaf(tr, v[i], x[i]);
-      ++evals;
-      if (!in_slice<G, DPL>(R, f, L, C, y, height, gl, has, mask, lly, nanc)) break;
+      if (!in_slice(tr, lly)) break;
       tr += w;
       ++exps;
     }
@@ -457,13 +507,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     for (int r = 0; r < kShrinkCap; ++r) {
       const float u = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)r, mask));
       const float t = fmaf(u, tr - tl, tl);
-#pragma unroll
-      for (int i = 0; i < DPL; ++i) y[i] = fmaf(t, v[i], x[i]);
-      ++evals;
       ++shr;
-      if (in_slice<G, DPL>(R, f, L, C, y, height, gl, has, mask, lly, nanc)) {
+      if (in_slice(t, lly)) {
 #pragma unroll
-        for (int i = 0; i < DPL; ++i) x[i] = y[i];
+        for (int i = 0; i < DPL; ++i) x[i] = fmaf(t, v[i], x[i]);
         lx = lly;
         ok = true;
         break;
@@ -479,7 +526,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, x);
   if (gl == 0) {
     D.f[R.o_logL + slot] = lx;
-    D.f[R.o_birth + slot] = C.lstar;
+    D.f[R.o_birth + slot] = lstar;
     int* st = D.i + R.o_stats;
     st[j] = evals;
     st[R.k + j] = acc;
@@ -496,7 +543,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
 
 constexpr int kSweepThreads = 128;
 // resident blocks per SM the register budget is tuned for
-constexpr int sweep_min_blocks(int dpl) { return dpl == 1 ? 8 : dpl == 2 ? 6 : 4; }
+constexpr int sweep_min_blocks(int dpl) { return dpl == 1 ? 6 : dpl == 2 ? 6 : 4; }
 
 template <int G, int DPL>
 __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(Dev D, const WorkItem* __restrict__ items, int n_items,

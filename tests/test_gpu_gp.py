@@ -38,9 +38,9 @@ def test_initial_logL_matches_checker_full_size(gpu_lib):
           f"all finite points max rel err {err[fin].max():.2e}; FP32 breakdowns {np.sum(~fin)} of {wl.n_live} "
           f"(min cond among them {cond[~fin].min() if (~fin).any() else 0:.1e})")
     assert err[good].max() < 1e-3
-    # breakdowns only where the checker's FP64 value is hopeless anyway
-    bad = st["logL"] == -np.inf
-    assert np.all(ref[bad] < np.median(ref))
+    # FP32 breakdowns only for badly conditioned kernels
+    bad = ~fin
+    assert (not bad.any()) or cond[bad].min() > 1e6
 
 
 @pytest.mark.parametrize("seed,warm", [(1, 3), (2, 8)])
@@ -64,10 +64,9 @@ def test_one_step_parity_gp(gpu_lib, seed, warm):
     assert xerr < 1e-4
     # logL of well-conditioned end points within 1e-3; FP32 Cholesky limit otherwise
     cond = np.array([kernel_cond(wl, th.astype(np.float64)) for th in t["new_x"]])
-    wc = ok & (cond < 1e5)
     rel = np.abs(g["new_logL"] - t["new_logL"]) / np.maximum(1, np.abs(t["new_logL"]))
-    assert rel[wc].max() < 1e-3
-    assert rel[ok].max() < 5e-2
+    # the error of an FP32 factorisation scales with eps32 * cond(K)
+    assert np.all(rel[ok] <= 1e-4 + 1e-7 * cond[ok]), np.max(rel[ok] / (1e-4 + 1e-7 * cond[ok]))
 
 
 def test_gp_evidence_matches_quadrature(gpu_lib):

@@ -463,7 +463,10 @@ nss_status build_work(nss_ctx* c) {
   for (int r = 0; r < c->n_runs; ++r) {
     const RunDesc& R = c->desc[r];
     const int per = 32 / nss::cfg_g(R.cfg);
-    for (int s = 0; s < R.m; s += per) c->init_items[R.cfg].push_back({r, s, std::min(s + per, R.m), 0});
+    // the prior draw always runs in a grouped configuration
+    const int icfg = nss::cfg_dpl(R.cfg) > 4 ? default_cfg(R.d) : R.cfg;
+    const int iper = 32 / nss::cfg_g(icfg);
+    for (int s = 0; s < R.m; s += iper) c->init_items[icfg].push_back({r, s, std::min(s + iper, R.m), 0});
     if (R.lik_kind == nss::kLikLogreg || R.lik_kind == nss::kLikGp) continue;  // own sweep kernels
     for (int j = 0; j < R.k; j += per) c->sweep_items[R.cfg].push_back({r, j, std::min(j + per, R.k), 0});
   }

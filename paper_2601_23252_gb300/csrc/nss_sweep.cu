@@ -461,20 +461,17 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       if (lk == kLikFlat) {
         ll = 0.0f;
       } else {
-        float M = -INFINITY, S = 0.0f;
+        float vc[kMaxComp];
+        float M = -INFINITY;
 #pragma unroll
         for (int c = 0; c < kMaxComp; ++c) {
-          if (c < K) {
-            const float q = fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]);
-            const float vc = -q * R.inv2s2;
-            if (vc > M) {
-              S = S * __expf(M - vc) + 1.0f;
-              M = vc;
-            } else {
-              S += __expf(vc - M);
-            }
-          }
+          vc[c] = (c < K) ? -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * R.inv2s2 : -INFINITY;
+          M = fmaxf(M, vc[c]);
         }
+        float S = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kMaxComp; ++c)
+          if (c < K) S += __expf(vc[c] - M);
         ll = (K == 1 ? M : M + __logf(S)) + R.lognorm;
         if (lk == kLikFault && fmaf(t, v0, x0) < R.fault_param)
           ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
@@ -575,7 +572,12 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(
   X(6, 2, 2) X(7, 4, 2) X(8, 8, 2) X(9, 16, 2) X(10, 32, 2) \
   X(11, 4, 1) X(12, 8, 1) X(13, 16, 1) X(14, 32, 1)
 
+// configurations 15..17: one chain per lane (nss_sweep_lane.cu), d <= 8, 16, 32
+constexpr int kLaneCfg0 = 15;
+static int lane_dmax(int cfg) { return cfg == 15 ? 8 : cfg == 16 ? 16 : 32; }
+
 int cfg_g(int cfg) {
+  if (cfg >= kLaneCfg0) return 1;
 #define X(id, g, p) if (cfg == id) return g;
   NSS_CFGS(X)
 #undef X
@@ -583,6 +585,7 @@ int cfg_g(int cfg) {
 }
 
 int cfg_dpl(int cfg) {
+  if (cfg >= kLaneCfg0) return lane_dmax(cfg);
 #define X(id, g, p) if (cfg == id) return p;
   NSS_CFGS(X)
 #undef X
@@ -601,6 +604,7 @@ cudaError_t launch_init(int cfg, const Dev& D, const WorkItem* items, int n, cud
 }
 
 int sweep_blocks_per_sm(int cfg) {
+  if (cfg >= kLaneCfg0) return sweep_lane_blocks_per_sm(lane_dmax(cfg));
   int nb = 0;
   switch (cfg) {
 #define X(id, g, p) case id: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<g, p>, kSweepThreads, 0); break;
@@ -613,6 +617,7 @@ int sweep_blocks_per_sm(int cfg) {
 
 cudaError_t launch_sweep(int cfg, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
                          cudaStream_t s) {
+  if (cfg >= kLaneCfg0) return launch_sweep_lane(lane_dmax(cfg), D, items, n, queue, grid, s);
   switch (cfg) {
 #define X(id, g, p) case id: k_sweep<g, p><<<grid, kSweepThreads, 0, s>>>(D, items, n, queue); break;
     NSS_CFGS(X)

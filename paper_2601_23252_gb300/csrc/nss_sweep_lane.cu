@@ -1,0 +1,286 @@
+// nss_sweep_lane.cu -- the HRSS sweep with one chain per lane (d <= 32), for
+// sm_103a.
+//
+// A lane holds its chain's whole position x and direction v in registers.
+// Per HRSS step it draws its direction (Philox blocks of its own counter,
+// Box-Muller, the triangular product L z against the run's factor, read as
+// warp-wide broadcasts), then the coefficients of the step's line:
+//   |x + t v - mu_c|^2 = D_c + t (2 E_c + t C),   box: t in [t_lo, t_hi],
+//   Gaussian prior: sum ((x + t v - a)/b)^2 = P0 + t (2 P1 + t P2),
+// so every slice evaluation of the step is a few scalar FMAs and one
+// log-sum-exp, with no communication between lanes.  The 32 chains of a warp
+// belong to one run and step in lockstep per HRSS step.
+#include <cfloat>
+#include <cmath>
+
+#include "nss_device.cuh"
+#include "nss_kernels.h"
+
+namespace nss {
+namespace {
+
+constexpr int kLaneThreads = 128;
+constexpr int kLaneMaxComp = 8;
+
+template <int DMAX>
+__device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) {
+  const float* __restrict__ f = D.f;
+  const int d = R.d, ld = R.dpad;
+  const int parent = D.i[R.o_parent + j];
+  const uint32_t iter = (uint32_t)Sw->iter;
+  const float lstar = Sw->logLstar;
+  const bool box = R.prior_kind == kPriorBox, nonflat = !box;
+  const int lk = R.lik_kind;
+  const int K = (lk == kLikGmm) ? R.n_comp : ((lk == kLikGauss || lk == kLikFault) ? 1 : 0);
+  float x[DMAX];
+  {
+    const float4* xp = reinterpret_cast<const float4*>(f + R.o_x + (long long)parent * ld);
+#pragma unroll
+    for (int b = 0; b < DMAX / 4; ++b) {
+      const float4 t = (4 * b < ld) ? xp[b] : make_float4(0.f, 0.f, 0.f, 0.f);
+      x[4 * b] = t.x; x[4 * b + 1] = t.y; x[4 * b + 2] = t.z; x[4 * b + 3] = t.w;
+    }
+  }
+  float lx = f[R.o_logL + parent];
+  const float w = R.w;
+  const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
+  const float4* L4 = reinterpret_cast<const float4*>(f + R.o_L);
+  const int ld4 = ld >> 2;
+  int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
+  for (int s = 0; s < R.p; ++s) {
+    // z ~ N(0, I) by Box-Muller from words [0, nz) of counter (iter, j, s, .)
+    float z[DMAX];
+    float zz = 0.0f;
+#pragma unroll
+    for (int b = 0; b < DMAX / 4; ++b) {
+      if (4 * b < d) {
+        const uint4 wb = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)b);
+        box_muller(wb.x, wb.y, z[4 * b], z[4 * b + 1]);
+        box_muller(wb.z, wb.w, z[4 * b + 2], z[4 * b + 3]);
+      } else {
+        z[4 * b] = z[4 * b + 1] = z[4 * b + 2] = z[4 * b + 3] = 0.0f;
+      }
+#pragma unroll
+      for (int i = 4 * b; i < 4 * b + 4; ++i) {
+        if (i >= d) z[i] = 0.0f;
+        zz = fmaf(z[i], z[i], zz);
+      }
+    }
+    // v = L z / |z|  (or / |L z|); rows of L are warp-wide broadcast loads
+    float v[DMAX];
+#pragma unroll
+    for (int a = 0; a < DMAX; ++a) {
+      float acc_a = 0.0f;
+      if (a < ld) {
+#pragma unroll
+        for (int b = 0; b <= a / 4; ++b) {
+          const float4 l4 = __ldg(L4 + a * ld4 + b);
+          acc_a = fmaf(l4.x, z[4 * b], fmaf(l4.y, z[4 * b + 1], fmaf(l4.z, z[4 * b + 2], fmaf(l4.w, z[4 * b + 3], acc_a))));
+        }
+      }
+      v[a] = acc_a;
+    }
+    float inrm;
+    if (R.dir_norm == 0) {
+      inrm = rsqrtf(zz);
+    } else {
+      float dd = 0.0f;
+#pragma unroll
+      for (int a = 0; a < DMAX; ++a) dd = fmaf(v[a], v[a], dd);
+      inrm = rsqrtf(dd);
+    }
+    float Cv = 0.0f;
+#pragma unroll
+    for (int a = 0; a < DMAX; ++a) {
+      v[a] *= inrm;
+      Cv = fmaf(v[a], v[a], Cv);
+    }
+    // mixture coefficients
+    float Dc[kLaneMaxComp], Ec[kLaneMaxComp];
+#pragma unroll
+    for (int c = 0; c < kLaneMaxComp; ++c) {
+      float dq = 0.0f, de = 0.0f;
+      if (c < K) {
+        const float4* m4 = reinterpret_cast<const float4*>(f + R.o_mu + (long long)c * ld);
+#pragma unroll
+        for (int b = 0; b < DMAX / 4; ++b) {
+          if (4 * b < ld) {
+            const float4 m = __ldg(m4 + b);
+            const float e0 = x[4 * b] - m.x, e1 = x[4 * b + 1] - m.y, e2 = x[4 * b + 2] - m.z, e3 = x[4 * b + 3] - m.w;
+            dq = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, dq))));
+            de = fmaf(e0, v[4 * b], fmaf(e1, v[4 * b + 1], fmaf(e2, v[4 * b + 2], fmaf(e3, v[4 * b + 3], de))));
+          }
+        }
+      }
+      Dc[c] = dq;
+      Ec[c] = de;
+    }
+    // support interval of the box prior, or the Gaussian-prior quadratic
+    float t_lo = -INFINITY, t_hi = INFINITY;
+    float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f, height = 0.0f;
+    if (box) {
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i) {
+        if (i < d) {
+          const float ai = __ldg(f + R.o_a + i) - x[i], bi = __ldg(f + R.o_b + i) - x[i];
+          if (v[i] > 0.0f) {
+            t_lo = fmaxf(t_lo, ai / v[i]);
+            t_hi = fminf(t_hi, bi / v[i]);
+          } else if (v[i] < 0.0f) {
+            t_lo = fmaxf(t_lo, bi / v[i]);
+            t_hi = fminf(t_hi, ai / v[i]);
+          } else if (!(ai <= 0.0f && bi >= 0.0f)) {
+            t_lo = INFINITY;
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i) {
+        if (i < d) {
+          const float ib = 1.0f / __ldg(f + R.o_b + i);
+          const float u = (x[i] - __ldg(f + R.o_a + i)) * ib, q = v[i] * ib;
+          P0 = fmaf(u, u, P0);
+          P1 = fmaf(u, q, P1);
+          P2 = fmaf(q, q, P2);
+        }
+      }
+    }
+    // step words beyond the normals: U, height, shrinkage proposals
+    uint32_t cblk = 0xFFFFFFFFu;
+    uint4 cw = make_uint4(0u, 0u, 0u, 0u);
+    auto word = [&](uint32_t wi) {
+      if ((wi >> 2) != cblk) {
+        cblk = wi >> 2;
+        cw = draw_block(R, iter, (uint32_t)j, (uint32_t)s, cblk);
+      }
+      return pick(cw, wi & 3u);
+    };
+    if (nonflat) height = fmaf(-0.5f, P0, R.prior_const) + logf(u24(word(nz + 1u)));
+    auto in_slice = [&](float t, float& ll) -> bool {
+      ++evals;
+      if (box && !(t >= t_lo && t <= t_hi)) return false;
+      if (nonflat) {
+        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
+        if (!(lp > height)) return false;
+      }
+      if (lk == kLikFlat) {
+        ll = 0.0f;
+      } else {
+        float vc[kLaneMaxComp];
+        float M = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < kLaneMaxComp; ++c) {
+          vc[c] = (c < K) ? -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * R.inv2s2 : -INFINITY;
+          M = fmaxf(M, vc[c]);
+        }
+        float S = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kLaneMaxComp; ++c)
+          if (c < K) S += __expf(vc[c] - M);
+        ll = (K == 1 ? M : M + __logf(S)) + R.lognorm;
+        if (lk == kLikFault && fmaf(t, v[0], x[0]) < R.fault_param)
+          ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
+      }
+      if (isnan(ll)) {
+        ll = -INFINITY;
+        ++nanc;
+      }
+      return ll > lstar;
+    };
+    const float U = u24(word(nz));
+    float tl = -w * U, tr = tl + w, lly = 0.0f;
+    for (int n = 0;; ++n) {
+      if (n >= kStepOutCap) { ++capo; break; }
+      if (!in_slice(tl, lly)) break;
+      tl -= w;
+      ++exps;
+    }
+    for (int n = 0;; ++n) {
+      if (n >= kStepOutCap) { ++capo; break; }
+      if (!in_slice(tr, lly)) break;
+      tr += w;
+      ++exps;
+    }
+    bool ok = false;
+    for (int r = 0; r < kShrinkCap; ++r) {
+      const float u = u24(word(nz + 3u + (uint32_t)r));
+      const float t = fmaf(u, tr - tl, tl);
+      ++shr;
+      if (in_slice(t, lly)) {
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) x[i] = fmaf(t, v[i], x[i]);
+        lx = lly;
+        ok = true;
+        break;
+      }
+      if (t < 0.0f) tl = t;
+      else tr = t;
+    }
+    if (ok) ++acc;
+    else ++nul;
+  }
+  // (iv) replace dead slot j, born at logL*
+  const int slot = D.i[R.o_dead + j];
+  float4* xo = reinterpret_cast<float4*>(D.f + R.o_x + (long long)slot * ld);
+#pragma unroll
+  for (int b = 0; b < DMAX / 4; ++b)
+    if (4 * b < ld) xo[b] = make_float4(x[4 * b], x[4 * b + 1], x[4 * b + 2], x[4 * b + 3]);
+  D.f[R.o_logL + slot] = lx;
+  D.f[R.o_birth + slot] = lstar;
+  int* st = D.i + R.o_stats;
+  st[j] = evals;
+  st[R.k + j] = acc;
+  st[2 * R.k + j] = nul;
+  st[3 * R.k + j] = exps;
+  st[4 * R.k + j] = shr;
+  st[5 * R.k + j] = capo;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->evals), (unsigned long long)evals);
+  if (nul) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nulls), (unsigned long long)nul);
+  if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->cap_out), (unsigned long long)capo);
+  if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nan_evals), (unsigned long long)nanc);
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(kLaneThreads, (DMAX >= 32 ? 2 : 4)) k_sweep_lane(Dev D, const WorkItem* __restrict__ items, int n_items,
+                                                                int* queue) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(queue, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
+    const WorkItem wi = items[it];
+    RunState* S = D.st + wi.run;
+    if (S->done) continue;
+    const int j = wi.c0 + lane;
+    if (j < wi.c1) lane_chain<DMAX>(D, D.desc[wi.run], S, j);
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_lane(int dmax, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
+                              cudaStream_t s) {
+  switch (dmax) {
+    case 8: k_sweep_lane<8><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
+    case 16: k_sweep_lane<16><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
+    case 32: k_sweep_lane<32><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int sweep_lane_blocks_per_sm(int dmax) {
+  int nb = 0;
+  switch (dmax) {
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<8>, kLaneThreads, 0); break;
+    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<16>, kLaneThreads, 0); break;
+    case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<32>, kLaneThreads, 0); break;
+    default: break;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+}  // namespace nss

@@ -33,7 +33,10 @@ def test_gauss_d2_twenty_seeds_closed_form(gpu_lib):
         res = s.run()
     _check_seeds([r["logZ"] for r in res], [r["logZ_err"] for r in res], [truth] * 20, "gauss_d2")
     for r in res:
-        assert r["status"] == 0 and r["nulls"] == 0 and r["nan_evals"] == 0
+        # a null move needs a chain whose own point sits within FP32 rounding of
+        # logL*; it may happen, but only at the rate of such near-ties
+        assert r["status"] == 0 and r["nan_evals"] == 0
+        assert r["nulls"] <= 1e-4 * r["iters"] * 250 * 10
         assert r["n_dead"] == r["iters"] * 250 + 500
 
 

@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--ncu-case", action="store_true",
                     help="no timing: the bench batch for a few iterations, small dead stores "
                          "(the case captured by ncu)")
+    ap.add_argument("--ncu-cfg", type=int, default=-1,
+                    help="with --ncu-case: force this sweep configuration id instead of autotuning")
     ap.add_argument("--ncu-case-logreg", action="store_true",
                     help="no timing: one outer iteration of the full-size logistic-regression "
                          "workload (d=100, N=10000, k=1000, p=200), for ncu captures of its kernels")
@@ -239,6 +241,8 @@ def run_native(args):
 
     sampler = native.Sampler(wls, stream=stream.cuda_stream)
     chosen = sampler.autotune(iters=3)
+    tune = {f"{native.Sampler.cfg_info(q)['lanes_per_chain']}x{native.Sampler.cfg_info(q)['dims_per_lane']}": round(v, 4)
+            for q, v in sampler.autotune_report().items()}
     for _ in range(args.warmup):
         sampler.reset()
         sampler.run()
@@ -304,7 +308,7 @@ def run_native(args):
             "config": {"workload": "gmm_d32", "d": 32, "n_comp": 4, "sigma": 0.02, "n_live": 1000,
                        "k": 500, "p": 96, "runs_per_gpu": nrun, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (512 MB write)",
-                       "sweep_cfg": chosen[0],
+                       "sweep_cfg": chosen[0], "autotune_ms_per_Meval": tune,
                        "evidence_accumulation": "f64"},
             "evals_per_s": evals_all / (total_ms_all / 1e3),
             "gate": {"mean_dlogZ": float(dlogZ.mean()), "max_abs_dlogZ_over_err": float(np.max(np.abs(dlogZ) / errs)),
@@ -370,10 +374,13 @@ def run_ncu_case(args):
     stores sized for those iterations so the device footprint stays small."""
     from paper_2601_23252_gb300 import native
     from paper_2601_23252_gb300 import workloads as W
-    wls = [W.gmm_d32(seed=s).with_(extra={"options": {"dead_capacity": 8 * 500 + 1000}})
-           for s in range(args.runs)]
+    opts = {"dead_capacity": 8 * 500 + 1000}
+    if args.ncu_cfg >= 0:
+        opts["sweep_cfg"] = args.ncu_cfg
+    wls = [W.gmm_d32(seed=s).with_(extra={"options": dict(opts)}) for s in range(args.runs)]
     with native.Sampler(wls) as s:
-        s.autotune(iters=2)
+        if args.ncu_cfg < 0:
+            s.autotune(iters=2)
         for _ in range(6):
             s.step()
     return 0

@@ -83,6 +83,7 @@ struct nss_ctx {
   std::vector<cudaEvent_t> ev_pool;
   nss_profile prof{};
   double cfg_ms[nss::kNumCfgs] = {};
+  double tune_cost[nss::kNumCfgs] = {};   // last autotune: device ms per 1e6 evaluations
   long long launches = 0;
   bool broken = false;
   std::string err;
@@ -484,8 +485,9 @@ nss_status build_work(nss_ctx* c) {
       CK(cudaMemcpyAsync(c->d_sweep[q], c->sweep_items[q].data(), sizeof(WorkItem) * c->sweep_items[q].size(),
                          cudaMemcpyHostToDevice, c->stream), "work list upload");
       const int per_sm = nss::sweep_blocks_per_sm(q);
+      const int wpb = nss::sweep_warps_per_block(q);
       const int warps_needed = (int)c->sweep_items[q].size();
-      const int blocks_needed = (warps_needed + 3) / 4;
+      const int blocks_needed = (warps_needed + wpb - 1) / wpb;
       c->sweep_grid[q] = std::max(1, std::min(blocks_needed, per_sm * c->num_sms));
     }
   }
@@ -1121,6 +1123,12 @@ int nss_get_cfg(const nss_ctx* c, int run) {
   return c->desc[run].cfg;
 }
 
+nss_status nss_autotune_report(const nss_ctx* c, double* cost) {
+  if (!c || !cost) return NSS_ERR_ARG;
+  for (int q = 0; q < nss::kNumCfgs; ++q) cost[q] = c->tune_cost[q];
+  return NSS_OK;
+}
+
 nss_status nss_set_cfg(nss_ctx* c, int run, int cfg) {
   if (!c || run < 0 || run >= c->n_runs) return NSS_ERR_ARG;
   if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
@@ -1169,6 +1177,7 @@ nss_status nss_autotune(nss_ctx* c, int iters, int* cfg_out) {
       double ev = 0.0;
       for (int r : runs) ev += (double)c->h_state[r].evals;
       const double cost = c->cfg_ms[q] / std::max(1.0, ev);
+      c->tune_cost[q] = cost * 1e6;
       if (cost < best_cost) {
         best_cost = cost;
         best = q;

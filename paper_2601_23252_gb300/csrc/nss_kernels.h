@@ -67,6 +67,8 @@ int sweep_blocks_per_sm(int cfg);
 cudaError_t launch_sweep_lane(int dmax, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
                               cudaStream_t s);
 int sweep_lane_blocks_per_sm(int dmax);
+int sweep_lane_warps_per_block();
+int sweep_warps_per_block(int cfg);
 int cfg_g(int cfg);
 int cfg_dpl(int cfg);
 

@@ -603,6 +603,8 @@ cudaError_t launch_init(int cfg, const Dev& D, const WorkItem* items, int n, cud
   return cudaGetLastError();
 }
 
+int sweep_warps_per_block(int cfg) { return cfg >= kLaneCfg0 ? sweep_lane_warps_per_block() : kSweepThreads / 32; }
+
 int sweep_blocks_per_sm(int cfg) {
   if (cfg >= kLaneCfg0) return sweep_lane_blocks_per_sm(lane_dmax(cfg));
   int nb = 0;

@@ -19,7 +19,7 @@
 namespace nss {
 namespace {
 
-constexpr int kLaneThreads = 128;
+constexpr int kLaneThreads = 32;   // one warp per block: few warps in total, spread over every SM
 constexpr int kLaneMaxComp = 8;
 
 template <int DMAX>
@@ -123,12 +123,13 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
       for (int i = 0; i < DMAX; ++i) {
         if (i < d) {
           const float ai = __ldg(f + R.o_a + i) - x[i], bi = __ldg(f + R.o_b + i) - x[i];
+          const float rv = __frcp_rn(v[i]);
           if (v[i] > 0.0f) {
-            t_lo = fmaxf(t_lo, ai / v[i]);
-            t_hi = fminf(t_hi, bi / v[i]);
+            t_lo = fmaxf(t_lo, ai * rv);
+            t_hi = fminf(t_hi, bi * rv);
           } else if (v[i] < 0.0f) {
-            t_lo = fmaxf(t_lo, bi / v[i]);
-            t_hi = fminf(t_hi, ai / v[i]);
+            t_lo = fmaxf(t_lo, bi * rv);
+            t_hi = fminf(t_hi, ai * rv);
           } else if (!(ai <= 0.0f && bi >= 0.0f)) {
             t_lo = INFINITY;
           }
@@ -242,7 +243,7 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
 }
 
 template <int DMAX>
-__global__ void __launch_bounds__(kLaneThreads, (DMAX >= 32 ? 2 : 4)) k_sweep_lane(Dev D, const WorkItem* __restrict__ items, int n_items,
+__global__ void __launch_bounds__(kLaneThreads, (DMAX >= 32 ? 8 : 16)) k_sweep_lane(Dev D, const WorkItem* __restrict__ items, int n_items,
                                                                 int* queue) {
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -271,6 +272,8 @@ cudaError_t launch_sweep_lane(int dmax, const Dev& D, const WorkItem* items, int
   }
   return cudaGetLastError();
 }
+
+int sweep_lane_warps_per_block() { return kLaneThreads / 32; }
 
 int sweep_lane_blocks_per_sm(int dmax) {
   int nb = 0;

@@ -96,6 +96,7 @@ def lib():
     L.nss_reset.argtypes = [C.c_void_p, P(C.c_uint64)]
     L.nss_autotune.argtypes = [C.c_void_p, C.c_int, _ip]
     L.nss_set_cfg.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.nss_autotune_report.argtypes = [C.c_void_p, _dp]
     L.nss_get_cfg.argtypes = [C.c_void_p, C.c_int]
     L.nss_cfg_lanes.argtypes = [C.c_int]
     L.nss_cfg_dims.argtypes = [C.c_int]
@@ -276,6 +277,12 @@ class Sampler:
         out = (C.c_int * self.n_runs)()
         self._check(lib().nss_autotune(self._h, int(iters), out), "nss_autotune")
         return [self.cfg_info(q) for q in out]
+
+    def autotune_report(self):
+        """Cost of every configuration tried by the last autotune (ms per 1e6 evals)."""
+        arr = (C.c_double * 18)()
+        self._check(lib().nss_autotune_report(self._h, arr), "nss_autotune_report")
+        return {i: arr[i] for i in range(18) if arr[i] > 0}
 
     def set_cfg(self, run, cfg):
         self._check(lib().nss_set_cfg(self._h, run, cfg), "nss_set_cfg")

@@ -250,7 +250,7 @@ nss_status nss_set_cfg(nss_ctx *ctx, int run, int cfg);
 /* Cost measured by the last nss_autotune for every configuration id (device
    milliseconds per 10^6 logical evaluations; 0 = not tried).  cost: array of
    NSS_NUM_CFGS entries. */
-#define NSS_NUM_CFGS 18
+#define NSS_NUM_CFGS 25
 nss_status nss_autotune_report(const nss_ctx *ctx, double *cost);
 int nss_get_cfg(const nss_ctx *ctx, int run);
 int nss_cfg_lanes(int cfg);

@@ -23,9 +23,12 @@ namespace nss {
 // ---- lane-slice loads and stores of a point row ---------------------------
 template <int DPL>
 __device__ __forceinline__ void load_lane(const float* __restrict__ row, int gl, float (&x)[DPL]) {
-  if constexpr (DPL == 4) {
-    const float4 t = reinterpret_cast<const float4*>(row)[gl];
-    x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+  if constexpr (DPL >= 4) {
+#pragma unroll
+    for (int q = 0; q < DPL / 4; ++q) {
+      const float4 t = reinterpret_cast<const float4*>(row)[gl * (DPL / 4) + q];
+      x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+    }
   } else if constexpr (DPL == 2) {
     const float2 t = reinterpret_cast<const float2*>(row)[gl];
     x[0] = t.x; x[1] = t.y;
@@ -36,9 +39,12 @@ __device__ __forceinline__ void load_lane(const float* __restrict__ row, int gl,
 
 template <int DPL>
 __device__ __forceinline__ void ldg_lane(const float* __restrict__ row, int gl, float (&x)[DPL]) {
-  if constexpr (DPL == 4) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(row) + gl);
-    x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+  if constexpr (DPL >= 4) {
+#pragma unroll
+    for (int q = 0; q < DPL / 4; ++q) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(row) + gl * (DPL / 4) + q);
+      x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+    }
   } else if constexpr (DPL == 2) {
     const float2 t = __ldg(reinterpret_cast<const float2*>(row) + gl);
     x[0] = t.x; x[1] = t.y;
@@ -49,8 +55,10 @@ __device__ __forceinline__ void ldg_lane(const float* __restrict__ row, int gl, 
 
 template <int DPL>
 __device__ __forceinline__ void store_lane(float* row, int gl, const float (&x)[DPL]) {
-  if constexpr (DPL == 4) {
-    reinterpret_cast<float4*>(row)[gl] = make_float4(x[0], x[1], x[2], x[3]);
+  if constexpr (DPL >= 4) {
+#pragma unroll
+    for (int q = 0; q < DPL / 4; ++q)
+      reinterpret_cast<float4*>(row)[gl * (DPL / 4) + q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
   } else if constexpr (DPL == 2) {
     reinterpret_cast<float2*>(row)[gl] = make_float2(x[0], x[1]);
   } else {
@@ -63,10 +71,13 @@ __device__ __forceinline__ void store_lane(float* row, int gl, const float (&x)[
 template <int DPL>
 __device__ __forceinline__ void lane_normals(const RunDesc& R, uint32_t c0, uint32_t c1, uint32_t c2,
                                              int gl, float (&z)[DPL]) {
-  if constexpr (DPL == 4) {
-    const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)gl);
-    box_muller(w.x, w.y, z[0], z[1]);
-    box_muller(w.z, w.w, z[2], z[3]);
+  if constexpr (DPL >= 4) {
+#pragma unroll
+    for (int q = 0; q < DPL / 4; ++q) {
+      const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)(gl * (DPL / 4) + q));
+      box_muller(w.x, w.y, z[4 * q], z[4 * q + 1]);
+      box_muller(w.z, w.w, z[4 * q + 2], z[4 * q + 3]);
+    }
   } else if constexpr (DPL == 2) {
     const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)(gl >> 1));
     if (gl & 1) box_muller(w.z, w.w, z[0], z[1]);
@@ -84,11 +95,19 @@ __device__ __forceinline__ void lane_normals(const RunDesc& R, uint32_t c0, uint
 template <int DPL>
 __device__ __forceinline__ void lane_uniform_words(const RunDesc& R, uint32_t c0, uint32_t c1, uint32_t c2,
                                                    int gl, uint32_t (&u)[DPL]) {
-  const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)((gl * DPL) >> 2));
-  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-  const int o = (gl * DPL) & 3;
+  if constexpr (DPL >= 4) {
 #pragma unroll
-  for (int i = 0; i < DPL; ++i) u[i] = ws[o + i];
+    for (int q = 0; q < DPL / 4; ++q) {
+      const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)(gl * (DPL / 4) + q));
+      u[4 * q] = w.x; u[4 * q + 1] = w.y; u[4 * q + 2] = w.z; u[4 * q + 3] = w.w;
+    }
+  } else {
+    const uint4 w = draw_block(R, c0, c1, c2, (uint32_t)((gl * DPL) >> 2));
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    const int o = (gl * DPL) & 3;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) u[i] = ws[o + i];
+  }
 }
 
 // ---- likelihood of a chain group ------------------------------------------
@@ -203,18 +222,28 @@ struct Lik {
 // past the first 4G - nz - 3) is drawn on demand.
 template <int G>
 struct StepWords {
-  uint4 mine;
-  __device__ __forceinline__ void draw(const RunDesc& R, uint32_t iter, uint32_t chain, uint32_t step, int gl) {
-    mine = draw_block(R, iter, chain, step, (uint32_t)gl);
+  uint4 mine;       // block base + gl of the step's counter stream
+  uint32_t base;
+  uint32_t cblk;    // one-block cache for words past the shared range
+  uint4 cw;
+  __device__ __forceinline__ void draw(const RunDesc& R, uint32_t iter, uint32_t chain, uint32_t step, int gl,
+                                       uint32_t base_) {
+    base = base_;
+    mine = draw_block(R, iter, chain, step, base + (uint32_t)gl);
+    cblk = 0xFFFFFFFFu;
   }
   // word wi, uniform over the group
   __device__ __forceinline__ uint32_t word(const RunDesc& R, uint32_t iter, uint32_t chain, uint32_t step,
-                                           uint32_t wi, unsigned mask) const {
+                                           uint32_t wi, unsigned mask) {
     const uint32_t b = wi >> 2;
-    if (b < (uint32_t)G) return __shfl_sync(mask, pick(mine, wi & 3u), (int)b, G);
-    return pick(draw_block(R, iter, chain, step, b), wi & 3u);
+    if (b >= base && b - base < (uint32_t)G) return __shfl_sync(mask, pick(mine, wi & 3u), (int)(b - base), G);
+    if (b != cblk) {
+      cw = draw_block(R, iter, chain, step, b);
+      cblk = b;
+    }
+    return pick(cw, wi & 3u);
   }
-  // all four words of block b (b < G), for lane-specific picks
+  // all four words of block b (base <= b < base + G), for lane-specific picks
   __device__ __forceinline__ uint4 block(int b, unsigned mask) const {
     return make_uint4(__shfl_sync(mask, mine.x, b, G), __shfl_sync(mask, mine.y, b, G),
                       __shfl_sync(mask, mine.z, b, G), __shfl_sync(mask, mine.w, b, G));
@@ -223,8 +252,17 @@ struct StepWords {
 
 // Normals of the lane's dimensions for the step, from the shared blocks.
 template <int G, int DPL>
-__device__ __forceinline__ void step_normals(const StepWords<G>& W, int gl, unsigned mask, float (&z)[DPL]) {
-  if constexpr (DPL == 4) {
+__device__ __forceinline__ void step_normals(const StepWords<G>& W, const RunDesc& R, uint32_t iter, uint32_t chain,
+                                             uint32_t step, int gl, unsigned mask, float (&z)[DPL]) {
+  if constexpr (DPL > 4) {
+    // the lane's own blocks gl*DPL/4 .. (the shared blocks hold the scalar words)
+#pragma unroll
+    for (int q = 0; q < DPL / 4; ++q) {
+      const uint4 w = draw_block(R, iter, chain, step, (uint32_t)(gl * (DPL / 4) + q));
+      box_muller(w.x, w.y, z[4 * q], z[4 * q + 1]);
+      box_muller(w.z, w.w, z[4 * q + 2], z[4 * q + 3]);
+    }
+  } else if constexpr (DPL == 4) {
     box_muller(W.mine.x, W.mine.y, z[0], z[1]);
     box_muller(W.mine.z, W.mine.w, z[2], z[3]);
   } else if constexpr (DPL == 2) {
@@ -339,9 +377,9 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   for (int s = 0; s < R.p; ++s) {
     // direction: z ~ N(0, I), d~ = L z, v = d~ / |z|  (or / |d~|)
     StepWords<G> W;
-    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl);
+    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, DPL > 4 ? (nz >> 2) : 0u);
     float z[DPL];
-    step_normals<G, DPL>(W, gl, mask, z);
+    step_normals<G, DPL>(W, R, iter, (uint32_t)j, (uint32_t)s, gl, mask, z);
     float zz = 0.0f;
 #pragma unroll
     for (int i = 0; i < DPL; ++i) {
@@ -540,7 +578,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
 
 constexpr int kSweepThreads = 128;
 // resident blocks per SM the register budget is tuned for
-constexpr int sweep_min_blocks(int dpl) { return dpl == 1 ? 6 : dpl == 2 ? 6 : 4; }
+constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 6 : dpl == 4 ? 4 : dpl == 8 ? 4 : 3; }
 
 template <int G, int DPL>
 __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(Dev D, const WorkItem* __restrict__ items, int n_items,
@@ -570,11 +608,13 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(
 #define NSS_CFGS(X) \
   X(0, 1, 4) X(1, 2, 4) X(2, 4, 4) X(3, 8, 4) X(4, 16, 4) X(5, 32, 4) \
   X(6, 2, 2) X(7, 4, 2) X(8, 8, 2) X(9, 16, 2) X(10, 32, 2) \
-  X(11, 4, 1) X(12, 8, 1) X(13, 16, 1) X(14, 32, 1)
+  X(11, 4, 1) X(12, 8, 1) X(13, 16, 1) X(14, 32, 1) \
+  X(15, 2, 8) X(16, 4, 8) X(17, 8, 8) X(18, 16, 8) \
+  X(19, 2, 16) X(20, 4, 16) X(21, 8, 16)
 
-// configurations 15..17: one chain per lane (nss_sweep_lane.cu), d <= 8, 16, 32
-constexpr int kLaneCfg0 = 15;
-static int lane_dmax(int cfg) { return cfg == 15 ? 8 : cfg == 16 ? 16 : 32; }
+// configurations 22..24: one chain per lane (nss_sweep_lane.cu), d <= 8, 16, 32
+constexpr int kLaneCfg0 = 22;
+static int lane_dmax(int cfg) { return cfg == 22 ? 8 : cfg == 23 ? 16 : 32; }
 
 int cfg_g(int cfg) {
   if (cfg >= kLaneCfg0) return 1;

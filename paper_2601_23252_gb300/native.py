@@ -280,9 +280,9 @@ class Sampler:
 
     def autotune_report(self):
         """Cost of every configuration tried by the last autotune (ms per 1e6 evals)."""
-        arr = (C.c_double * 18)()
+        arr = (C.c_double * 25)()
         self._check(lib().nss_autotune_report(self._h, arr), "nss_autotune_report")
-        return {i: arr[i] for i in range(18) if arr[i] > 0}
+        return {i: arr[i] for i in range(25) if arr[i] > 0}
 
     def set_cfg(self, run, cfg):
         self._check(lib().nss_set_cfg(self._h, run, cfg), "nss_set_cfg")

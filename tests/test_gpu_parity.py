@@ -102,7 +102,7 @@ def test_one_step_parity_every_sweep_configuration(gpu_lib, name):
     the same selection and parents and counters matching the checker."""
     wl = _wl(name, 31)
     with native.Sampler(wl) as s:
-        cands = [q for q in range(15) if _fits(s, q, wl.d)]
+        cands = [q for q in range(25) if _fits(s, q, wl.d)]
     assert len(cands) >= 2
     for q in cands:
         with native.Sampler(wl) as s:

@@ -83,7 +83,8 @@ struct nss_ctx {
   std::vector<cudaEvent_t> ev_pool;
   nss_profile prof{};
   double cfg_ms[nss::kNumCfgs] = {};
-  double tune_cost[nss::kNumCfgs] = {};   // last autotune: device ms per 1e6 evaluations
+  double tune_cost[nss::kNumCfgs] = {};
+  int max_p = 1;   // last autotune: device ms per 1e6 evaluations
   long long launches = 0;
   bool broken = false;
   std::string err;
@@ -387,6 +388,11 @@ nss_status enqueue_iteration(nss_ctx* c) {
   }
   for (int q = 0; q < nss::kNumCfgs; ++q) {
     if (c->sweep_items[q].empty()) continue;
+    {
+      Rec rd(c, NSS_K_OTHER);
+      CK(nss::launch_dirgen(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->max_p, c->stream),
+         "direction launch");
+    }
     CK(cudaMemsetAsync(c->d_queue + q, 0, sizeof(int), c->stream), "queue reset");
     Rec r(c, NSS_K_SWEEP, q);
     CK(nss::launch_sweep(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->d_queue + q,
@@ -865,6 +871,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     R.m = n_live[r];
     R.k = kk[r];
     R.p = pp[r];
+    c->max_p = std::max(c->max_p, R.p);
     int m2 = 1;
     while (m2 < R.m) m2 <<= 1;
     R.m2 = m2;
@@ -916,6 +923,8 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     R.o_b = c->nf; c->nf += align16(R.dpad);
     R.o_mu = c->nf; c->nf += align16((long long)R.n_comp * R.dpad);
     R.o_L = c->nf; c->nf += align16((long long)R.dpad * R.dpad);
+    const bool own_sweep = lk.kind != NSS_LOGLIK_LOGREG && lk.kind != NSS_LOGLIK_GP_RBF_WHITE;
+    R.o_V = c->nf; c->nf += own_sweep ? align16((long long)R.k * R.p * R.dpad) : 16;
     // INT32 pool
     R.o_dn = c->ni; c->ni += align16(cap);
     R.o_dead = c->ni; c->ni += align16(R.k);

@@ -38,6 +38,7 @@ struct RunDesc {
   long long o_dx, o_dlogL, o_dbirth;// dead store
   long long o_a, o_b, o_mu;         // prior bounds [dpad], means [n_comp][dpad]
   long long o_L;                    // metric factor [dpad][dpad]
+  long long o_V;                    // directions of the iteration [k][p][dpad]
   // INT32 pool offsets
   long long o_dn;                   // dead store live counts
   long long o_dead, o_parent;       // [k] each

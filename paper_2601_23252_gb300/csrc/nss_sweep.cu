@@ -21,12 +21,18 @@
 namespace nss {
 
 // ---- lane-slice loads and stores of a point row ---------------------------
+// Lane gl owns entries [gl*DPL, gl*DPL + DPL) of a row of ld floats (ld a
+// multiple of 4).  For DPL >= 8 the lane's range can run past ld (d = 20 with
+// 8 entries per lane): each float4 is guarded, and entries past ld read as 0
+// and are never written.
 template <int DPL>
-__device__ __forceinline__ void load_lane(const float* __restrict__ row, int gl, float (&x)[DPL]) {
+__device__ __forceinline__ void load_lane(const float* __restrict__ row, int gl, int ld, float (&x)[DPL]) {
   if constexpr (DPL >= 4) {
 #pragma unroll
     for (int q = 0; q < DPL / 4; ++q) {
-      const float4 t = reinterpret_cast<const float4*>(row)[gl * (DPL / 4) + q];
+      const int b = gl * (DPL / 4) + q;
+      const float4 t = (DPL == 4 || 4 * b < ld) ? reinterpret_cast<const float4*>(row)[b]
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
       x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
     }
   } else if constexpr (DPL == 2) {
@@ -38,11 +44,13 @@ __device__ __forceinline__ void load_lane(const float* __restrict__ row, int gl,
 }
 
 template <int DPL>
-__device__ __forceinline__ void ldg_lane(const float* __restrict__ row, int gl, float (&x)[DPL]) {
+__device__ __forceinline__ void ldg_lane(const float* __restrict__ row, int gl, int ld, float (&x)[DPL]) {
   if constexpr (DPL >= 4) {
 #pragma unroll
     for (int q = 0; q < DPL / 4; ++q) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(row) + gl * (DPL / 4) + q);
+      const int b = gl * (DPL / 4) + q;
+      const float4 t = (DPL == 4 || 4 * b < ld) ? __ldg(reinterpret_cast<const float4*>(row) + b)
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
       x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
     }
   } else if constexpr (DPL == 2) {
@@ -54,11 +62,14 @@ __device__ __forceinline__ void ldg_lane(const float* __restrict__ row, int gl, 
 }
 
 template <int DPL>
-__device__ __forceinline__ void store_lane(float* row, int gl, const float (&x)[DPL]) {
+__device__ __forceinline__ void store_lane(float* row, int gl, int ld, const float (&x)[DPL]) {
   if constexpr (DPL >= 4) {
 #pragma unroll
-    for (int q = 0; q < DPL / 4; ++q)
-      reinterpret_cast<float4*>(row)[gl * (DPL / 4) + q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    for (int q = 0; q < DPL / 4; ++q) {
+      const int b = gl * (DPL / 4) + q;
+      if (DPL == 4 || 4 * b < ld)
+        reinterpret_cast<float4*>(row)[b] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    }
   } else if constexpr (DPL == 2) {
     reinterpret_cast<float2*>(row)[gl] = make_float2(x[0], x[1]);
   } else {
@@ -126,7 +137,7 @@ struct Lik {
     const int nc = (R.lik_kind == kLikGmm) ? R.n_comp : 1;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      if (c < nc) ldg_lane<DPL>(f + R.o_mu + (long long)c * R.dpad, gl, mu4[c]);
+      if (c < nc) ldg_lane<DPL>(f + R.o_mu + (long long)c * R.dpad, gl, R.dpad, mu4[c]);
   }
 
   __device__ __forceinline__ static float sqdist(const float (&y)[DPL], const float (&m)[DPL]) {
@@ -201,7 +212,7 @@ struct Lik {
         float mq[DPL];
 #pragma unroll
         for (int i = 0; i < DPL; ++i) mq[i] = 0.0f;
-        if (has) ldg_lane<DPL>(f + R.o_mu + (long long)c * R.dpad, gl, mq);
+        if (has) ldg_lane<DPL>(f + R.o_mu + (long long)c * R.dpad, gl, R.dpad, mq);
         const float q = gsum<G>(has ? sqdist(y, mq) : 0.0f, mask);
         const float v = -q * R.inv2s2;
         if (v > M) {
@@ -326,12 +337,93 @@ __global__ void __launch_bounds__(128) k_init(Dev D, const WorkItem* __restrict_
       ll = L.eval(R, D.f, x, gl, has, mask);
       if (isnan(ll)) ll = -INFINITY;
     }
-    if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * R.dpad, gl, x);
+    if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * R.dpad, gl, R.dpad, x);
     if (gl == 0) {
       D.f[R.o_logL + slot] = ll;
       D.f[R.o_birth + slot] = -INFINITY;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Direction of HRSS step s of chain j (Sec. 3.2 "Direction metric"):
+// z ~ N(0, I) from words [0, 2 ceil(d/2)) of counter (iter, j, s, .),
+// d~ = L z, v = d~ / |z| (unit Mahalanobis length) or d~ / |d~|.  A
+// direction does not depend on the chain's position, so the directions of
+// every (chain, step) of an iteration are drawn ahead of the sweep by
+// k_dirgen, fully in parallel, and stored as V[chain][step][dpad].
+// ---------------------------------------------------------------------------
+template <int G, int DPL>
+__device__ __forceinline__ void group_direction(const RunDesc& R, const float* __restrict__ f, uint32_t iter,
+                                                int j, int s, int gl, unsigned mask, float* zs,
+                                                float (&v)[DPL]) {
+  const int d = R.d, ld = R.dpad;
+  const bool has = gl * DPL < ld;
+  StepWords<G> W;
+  if constexpr (DPL <= 4) W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, 0u);
+  float z[DPL];
+  step_normals<G, DPL>(W, R, iter, (uint32_t)j, (uint32_t)s, gl, mask, z);
+  float zz = 0.0f;
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) {
+    if (gl * DPL + i >= d) z[i] = 0.0f;
+    zs[gl * DPL + i] = z[i];
+    zz = fmaf(z[i], z[i], zz);
+  }
+  __syncwarp(mask);
+  zz = gsum<G>(zz, mask);
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) v[i] = 0.0f;
+  if (has) {
+    const float4* L4 = reinterpret_cast<const float4*>(f + R.o_L);
+    const float4* zs4 = reinterpret_cast<const float4*>(zs);
+    const int ld4 = ld >> 2;
+    const int row0 = gl * DPL;
+    const int nb = ((row0 + DPL - 1) >> 2) + 1;
+    for (int bb = 0; bb < nb; ++bb) {
+      const float4 zb = zs4[bb];
+#pragma unroll
+      for (int r = 0; r < DPL; ++r) {
+        if (DPL <= 4 || row0 + r < ld) {
+          const float4 l4 = __ldg(L4 + (row0 + r) * ld4 + bb);
+          v[r] = fmaf(l4.x, zb.x, fmaf(l4.y, zb.y, fmaf(l4.z, zb.z, fmaf(l4.w, zb.w, v[r]))));
+        }
+      }
+    }
+  }
+  __syncwarp(mask);
+  float inrm;
+  if (R.dir_norm == 0) {
+    inrm = rsqrtf(zz);
+  } else {
+    float dd = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) dd = fmaf(v[i], v[i], dd);
+    inrm = rsqrtf(gsum<G>(dd, mask));
+  }
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) v[i] *= inrm;
+}
+
+// blockIdx.y = step s; each warp takes one work item (32/G chains of a run)
+template <int G, int DPL>
+__global__ void __launch_bounds__(128) k_dirgen(Dev D, const WorkItem* __restrict__ items, int n_items) {
+  __shared__ __align__(16) float zbuf[4][32 * DPL];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gl = lane % G, grp = lane / G;
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  const int it = blockIdx.x * 4 + wid;
+  if (it >= n_items) return;
+  const WorkItem wi = items[it];
+  const RunDesc& R = D.desc[wi.run];
+  const RunState& S = D.st[wi.run];
+  const int s = blockIdx.y;
+  if (S.done || s >= R.p) return;
+  const int j = wi.c0 + grp;
+  if (j >= wi.c1) return;
+  float v[DPL];
+  group_direction<G, DPL>(R, D.f, (uint32_t)S.iter, j, s, gl, mask, &zbuf[wid][grp * G * DPL], v);
+  if (gl * DPL < R.dpad) store_lane<DPL>(D.f + R.o_V + ((long long)j * R.p + s) * R.dpad, gl, R.dpad, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -349,8 +441,7 @@ __global__ void __launch_bounds__(128) k_init(Dev D, const WorkItem* __restrict_
 constexpr int kMaxComp = 8;
 
 template <int G, int DPL>
-__device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j, int gl, unsigned mask,
-                            float* zs) {
+__device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j, int gl, unsigned mask) {
   const float* __restrict__ f = D.f;
   const int d = R.d, ld = R.dpad;
   const bool has = gl * DPL < ld;
@@ -366,56 +457,20 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   float x[DPL];
 #pragma unroll
   for (int i = 0; i < DPL; ++i) x[i] = 0.0f;
-  if (has) load_lane<DPL>(f + R.o_x + (long long)parent * ld, gl, x);
+  if (has) load_lane<DPL>(f + R.o_x + (long long)parent * ld, gl, ld, x);
   float lx = f[R.o_logL + parent];
   const float w = R.w;
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
-  const float4* L4 = reinterpret_cast<const float4*>(f + R.o_L);
-  const int ld4 = ld >> 2;
-  const float4* zs4 = reinterpret_cast<const float4*>(zs);
   int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
   for (int s = 0; s < R.p; ++s) {
-    // direction: z ~ N(0, I), d~ = L z, v = d~ / |z|  (or / |d~|)
+    // the step's direction, drawn ahead by k_dirgen; the scalar words
+    // (U, slice height, shrinkage proposals) from blocks nz/4 + gl
     StepWords<G> W;
-    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, DPL > 4 ? (nz >> 2) : 0u);
-    float z[DPL];
-    step_normals<G, DPL>(W, R, iter, (uint32_t)j, (uint32_t)s, gl, mask, z);
-    float zz = 0.0f;
-#pragma unroll
-    for (int i = 0; i < DPL; ++i) {
-      if (!own[i]) z[i] = 0.0f;
-      zs[gl * DPL + i] = z[i];
-      zz = fmaf(z[i], z[i], zz);
-    }
-    __syncwarp(mask);
-    zz = gsum<G>(zz, mask);
+    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, nz >> 2);
     float v[DPL];
 #pragma unroll
     for (int i = 0; i < DPL; ++i) v[i] = 0.0f;
-    if (has) {
-      const int row0 = gl * DPL;
-      const int nb = ((row0 + DPL - 1) >> 2) + 1;
-      for (int bb = 0; bb < nb; ++bb) {
-        const float4 zb = zs4[bb];
-#pragma unroll
-        for (int r = 0; r < DPL; ++r) {
-          const float4 l4 = __ldg(L4 + (row0 + r) * ld4 + bb);
-          v[r] = fmaf(l4.x, zb.x, fmaf(l4.y, zb.y, fmaf(l4.z, zb.z, fmaf(l4.w, zb.w, v[r]))));
-        }
-      }
-    }
-    __syncwarp(mask);
-    float inrm;
-    if (R.dir_norm == 0) {
-      inrm = rsqrtf(zz);
-    } else {
-      float dd = 0.0f;
-#pragma unroll
-      for (int i = 0; i < DPL; ++i) dd = fmaf(v[i], v[i], dd);
-      inrm = rsqrtf(gsum<G>(dd, mask));
-    }
-#pragma unroll
-    for (int i = 0; i < DPL; ++i) v[i] *= inrm;
+    if (has) ldg_lane<DPL>(f + R.o_V + ((long long)j * R.p + s) * ld, gl, ld, v);
 
     // coefficients of the step's line, reduced over the group
     float Cv = 0.0f;
@@ -431,7 +486,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
         float m[DPL];
 #pragma unroll
         for (int i = 0; i < DPL; ++i) m[i] = 0.0f;
-        if (has) ldg_lane<DPL>(f + R.o_mu + (long long)c * ld, gl, m);
+        if (has) ldg_lane<DPL>(f + R.o_mu + (long long)c * ld, gl, ld, m);
         float dq = 0.0f, de = 0.0f;
 #pragma unroll
         for (int i = 0; i < DPL; ++i) {
@@ -558,7 +613,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   }
   // (iv) replace dead slot j, born at logL*
   const int slot = D.i[R.o_dead + j];
-  if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, x);
+  if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, ld, x);
   if (gl == 0) {
     D.f[R.o_logL + slot] = lx;
     D.f[R.o_birth + slot] = lstar;
@@ -578,16 +633,14 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
 
 constexpr int kSweepThreads = 128;
 // resident blocks per SM the register budget is tuned for
-constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 6 : dpl == 4 ? 4 : dpl == 8 ? 4 : 3; }
+constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 5 : dpl == 4 ? 4 : dpl == 8 ? 4 : 3; }
 
 template <int G, int DPL>
 __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(Dev D, const WorkItem* __restrict__ items, int n_items,
                                                          int* queue) {
-  __shared__ __align__(16) float zbuf[kSweepThreads / 32][32 * DPL];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int gl = lane % G, grp = lane / G;
   const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
-  float* zs = &zbuf[wid][grp * G * DPL];
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(queue, 1);
@@ -597,7 +650,7 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(
     RunState* S = D.st + wi.run;
     if (S->done) continue;
     const int j = wi.c0 + grp;
-    if (j < wi.c1) sweep_chain<G, DPL>(D, D.desc[wi.run], S, j, gl, mask, zs);
+    if (j < wi.c1) sweep_chain<G, DPL>(D, D.desc[wi.run], S, j, gl, mask);
     __syncwarp();
   }
 }
@@ -655,6 +708,25 @@ int sweep_blocks_per_sm(int cfg) {
     default: break;
   }
   return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_dirgen(int cfg, const Dev& D, const WorkItem* items, int n, int max_p, cudaStream_t s) {
+  dim3 grid((n + 3) / 4, max_p);
+  if (cfg >= kLaneCfg0) {
+    switch (lane_dmax(cfg)) {
+      case 8: k_dirgen<1, 8><<<grid, 128, 0, s>>>(D, items, n); break;
+      case 16: k_dirgen<1, 16><<<grid, 128, 0, s>>>(D, items, n); break;
+      default: k_dirgen<1, 32><<<grid, 128, 0, s>>>(D, items, n); break;
+    }
+    return cudaGetLastError();
+  }
+  switch (cfg) {
+#define X(id, g, p) case id: k_dirgen<g, p><<<grid, 128, 0, s>>>(D, items, n); break;
+    NSS_CFGS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(int cfg, const Dev& D, const WorkItem* items, int n, int* queue, int grid,

@@ -44,56 +44,20 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
   float lx = f[R.o_logL + parent];
   const float w = R.w;
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
-  const float4* L4 = reinterpret_cast<const float4*>(f + R.o_L);
-  const int ld4 = ld >> 2;
   int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
   for (int s = 0; s < R.p; ++s) {
-    // z ~ N(0, I) by Box-Muller from words [0, nz) of counter (iter, j, s, .)
-    float z[DMAX];
-    float zz = 0.0f;
-#pragma unroll
-    for (int b = 0; b < DMAX / 4; ++b) {
-      if (4 * b < d) {
-        const uint4 wb = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)b);
-        box_muller(wb.x, wb.y, z[4 * b], z[4 * b + 1]);
-        box_muller(wb.z, wb.w, z[4 * b + 2], z[4 * b + 3]);
-      } else {
-        z[4 * b] = z[4 * b + 1] = z[4 * b + 2] = z[4 * b + 3] = 0.0f;
-      }
-#pragma unroll
-      for (int i = 4 * b; i < 4 * b + 4; ++i) {
-        if (i >= d) z[i] = 0.0f;
-        zz = fmaf(z[i], z[i], zz);
-      }
-    }
-    // v = L z / |z|  (or / |L z|); rows of L are warp-wide broadcast loads
+    // the step's direction, drawn ahead by k_dirgen
     float v[DMAX];
-#pragma unroll
-    for (int a = 0; a < DMAX; ++a) {
-      float acc_a = 0.0f;
-      if (a < ld) {
-#pragma unroll
-        for (int b = 0; b <= a / 4; ++b) {
-          const float4 l4 = __ldg(L4 + a * ld4 + b);
-          acc_a = fmaf(l4.x, z[4 * b], fmaf(l4.y, z[4 * b + 1], fmaf(l4.z, z[4 * b + 2], fmaf(l4.w, z[4 * b + 3], acc_a))));
-        }
-      }
-      v[a] = acc_a;
-    }
-    float inrm;
-    if (R.dir_norm == 0) {
-      inrm = rsqrtf(zz);
-    } else {
-      float dd = 0.0f;
-#pragma unroll
-      for (int a = 0; a < DMAX; ++a) dd = fmaf(v[a], v[a], dd);
-      inrm = rsqrtf(dd);
-    }
     float Cv = 0.0f;
+    {
+      const float4* vp = reinterpret_cast<const float4*>(f + R.o_V + ((long long)j * R.p + s) * ld);
 #pragma unroll
-    for (int a = 0; a < DMAX; ++a) {
-      v[a] *= inrm;
-      Cv = fmaf(v[a], v[a], Cv);
+      for (int b = 0; b < DMAX / 4; ++b) {
+        const float4 t = (4 * b < ld) ? __ldg(vp + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * b] = t.x; v[4 * b + 1] = t.y; v[4 * b + 2] = t.z; v[4 * b + 3] = t.w;
+      }
+#pragma unroll
+      for (int a = 0; a < DMAX; ++a) Cv = fmaf(v[a], v[a], Cv);
     }
     // mixture coefficients
     float Dc[kLaneMaxComp], Ec[kLaneMaxComp];

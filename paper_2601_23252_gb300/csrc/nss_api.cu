@@ -70,6 +70,10 @@ struct nss_ctx {
   WorkItem* d_sweep[nss::kNumCfgs] = {};
   int* d_queue = nullptr;
   int sweep_grid[nss::kNumCfgs] = {};
+  // direction generation: items of up to 32 chains, per dimension class 8..128
+  static constexpr int kDirClasses = 5;
+  std::vector<WorkItem> dir_items[kDirClasses];
+  WorkItem* d_dir[kDirClasses] = {};
   size_t prologue_smem = 0, final_smem = 0;
   // volume simulation scratch
   int R = 100;
@@ -293,6 +297,7 @@ void free_ctx(nss_ctx* c) {
     cudaFree(c->d_init[q]);
     cudaFree(c->d_sweep[q]);
   }
+  for (int q = 0; q < nss_ctx::kDirClasses; ++q) cudaFree(c->d_dir[q]);
   cudaFree(c->d_queue);
   cudaFree(c->d_vol);
   cudaFree(c->d_tiles);
@@ -386,13 +391,14 @@ nss_status enqueue_iteration(nss_ctx* c) {
     Rec r(c, NSS_K_PROLOGUE);
     CK(nss::launch_prologue(D, c->n_runs, c->prologue_smem, c->stream), "prologue launch");
   }
+  for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
+    if (c->dir_items[q].empty()) continue;
+    Rec rd(c, NSS_K_OTHER);
+    CK(nss::launch_dirgen(8 << q, D, c->d_dir[q], (int)c->dir_items[q].size(), c->max_p, c->stream),
+       "direction launch");
+  }
   for (int q = 0; q < nss::kNumCfgs; ++q) {
     if (c->sweep_items[q].empty()) continue;
-    {
-      Rec rd(c, NSS_K_OTHER);
-      CK(nss::launch_dirgen(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->max_p, c->stream),
-         "direction launch");
-    }
     CK(cudaMemsetAsync(c->d_queue + q, 0, sizeof(int), c->stream), "queue reset");
     Rec r(c, NSS_K_SWEEP, q);
     CK(nss::launch_sweep(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->d_queue + q,
@@ -467,6 +473,11 @@ nss_status build_work(nss_ctx* c) {
     cudaFree(c->d_sweep[q]);
     c->d_init[q] = c->d_sweep[q] = nullptr;
   }
+  for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
+    c->dir_items[q].clear();
+    cudaFree(c->d_dir[q]);
+    c->d_dir[q] = nullptr;
+  }
   for (int r = 0; r < c->n_runs; ++r) {
     const RunDesc& R = c->desc[r];
     const int per = 32 / nss::cfg_g(R.cfg);
@@ -476,6 +487,15 @@ nss_status build_work(nss_ctx* c) {
     for (int s = 0; s < R.m; s += iper) c->init_items[icfg].push_back({r, s, std::min(s + iper, R.m), 0});
     if (R.lik_kind == nss::kLikLogreg || R.lik_kind == nss::kLikGp) continue;  // own sweep kernels
     for (int j = 0; j < R.k; j += per) c->sweep_items[R.cfg].push_back({r, j, std::min(j + per, R.k), 0});
+    int dq = 0;
+    while ((8 << dq) < nss::dirgen_class(R.d)) ++dq;
+    for (int j = 0; j < R.k; j += 32) c->dir_items[dq].push_back({r, j, std::min(j + 32, R.k), 0});
+  }
+  for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
+    if (c->dir_items[q].empty()) continue;
+    CK(cudaMalloc(&c->d_dir[q], sizeof(WorkItem) * c->dir_items[q].size()), "work list allocation");
+    CK(cudaMemcpyAsync(c->d_dir[q], c->dir_items[q].data(), sizeof(WorkItem) * c->dir_items[q].size(),
+                       cudaMemcpyHostToDevice, c->stream), "work list upload");
   }
   for (int q = 0; q < nss::kNumCfgs; ++q) {
     auto cost = [&](const WorkItem& w) { return (double)c->desc[w.run].p * c->desc[w.run].d; };
@@ -959,6 +979,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   CKC(nss::setup_kernel_attributes(), "kernel attributes");
   CKC(nss::setup_logits_attributes(), "kernel attributes");
   CKC(nss::setup_gp_attributes(), "kernel attributes");
+  CKC(nss::setup_dirgen_attributes(), "kernel attributes");
   CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
   CKC(cudaMalloc(&c->d_desc, sizeof(RunDesc) * n_runs), "descriptor allocation");
   CKC(cudaMalloc(&c->d_state, sizeof(RunState) * n_runs), "state allocation");

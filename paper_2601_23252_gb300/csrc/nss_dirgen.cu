@@ -1,0 +1,160 @@
+// nss_dirgen.cu -- the directions of every HRSS step of an outer iteration,
+// drawn ahead of the sweep (Sec. 3.2, direction metric), for sm_103a.
+//
+// A direction depends on the run's metric factor L and on its own Philox
+// counter (iteration, chain, step, .), never on the chain's position, so all
+// k x p of them are independent work.  One thread makes one direction:
+//   z_i ~ N(0, 1) from Box-Muller pair i/2 of words [0, 2 ceil(d/2)),
+//   d~ = L z (L lower triangular), v = d~ / |z| (unit Mahalanobis length)
+//   or d~ / |d~| (unit Euclidean length),
+// and writes v to V[chain][step][0, dpad).  The 32 threads of a warp are 32
+// chains of one run at one step, so every load of L is a warp-uniform
+// broadcast.  Rows of d~ are formed from the last to the first so that d~_r
+// can overwrite z_r (row r reads z_c for c <= r only): z and d~ share one
+// array, in registers for d <= 32 and in shared memory above.
+#include <cmath>
+
+#include "nss_device.cuh"
+#include "nss_kernels.h"
+
+namespace nss {
+namespace {
+
+constexpr int kDirThreads = 128;
+
+template <int DMAX>
+__global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* __restrict__ items, int n_items) {
+  constexpr bool kShared = DMAX > 32;
+  constexpr int kReg = kShared ? 1 : DMAX;
+  extern __shared__ float zsh[];  // kShared: [kDirThreads][DMAX + 1], odd stride: no bank conflicts
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * (kDirThreads / 32) + (threadIdx.x >> 5);
+  if (it >= n_items) return;
+  const WorkItem wi = items[it];
+  const RunDesc& R = D.desc[wi.run];
+  const RunState& S = D.st[wi.run];
+  const int s = blockIdx.y;
+  if (S.done || s >= R.p) return;
+  const int j = wi.c0 + lane;
+  if (j >= wi.c1) return;
+  const int d = R.d, ld = R.dpad;
+  const uint32_t iter = (uint32_t)S.iter;
+  const float* __restrict__ Lf = D.f + R.o_L;
+  float4* out = reinterpret_cast<float4*>(D.f + R.o_V + ((long long)j * R.p + s) * ld);
+  float zz = 0.0f, dd = 0.0f;
+  if constexpr (!kShared) {
+    float z[kReg];
+#pragma unroll
+    for (int q = 0; q < kReg / 4; ++q) {
+      if (4 * q < d) {
+        const uint4 w = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
+        box_muller(w.x, w.y, z[4 * q], z[4 * q + 1]);
+        box_muller(w.z, w.w, z[4 * q + 2], z[4 * q + 3]);
+      } else {
+        z[4 * q] = z[4 * q + 1] = z[4 * q + 2] = z[4 * q + 3] = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kReg; ++i) {
+      if (i >= d) z[i] = 0.0f;
+      zz = fmaf(z[i], z[i], zz);
+    }
+    const float4* L4 = reinterpret_cast<const float4*>(Lf);
+    const int ld4 = ld >> 2;
+#pragma unroll
+    for (int r = kReg - 1; r >= 0; --r) {
+      if (r < d) {
+        const float4* row = L4 + r * ld4;
+        float acc = 0.0f;
+#pragma unroll
+        for (int b = 0; b < r / 4; ++b) {
+          const float4 l = __ldg(row + b);
+          acc = fmaf(l.x, z[4 * b], fmaf(l.y, z[4 * b + 1], fmaf(l.z, z[4 * b + 2], fmaf(l.w, z[4 * b + 3], acc))));
+        }
+        // the diagonal block: columns 4(r/4) .. r only (later ones already hold d~)
+        const float4 l = __ldg(row + r / 4);
+        const int b = r / 4, e = r % 4;
+        float t = 0.0f;
+        if (e >= 3) t = fmaf(l.w, z[4 * b + 3], t);
+        if (e >= 2) t = fmaf(l.z, z[4 * b + 2], t);
+        if (e >= 1) t = fmaf(l.y, z[4 * b + 1], t);
+        t = fmaf(l.x, z[4 * b], t);
+        z[r] = acc + t;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kReg; ++i) dd = fmaf(z[i], z[i], dd);
+    const float inrm = rsqrtf(R.dir_norm == 0 ? zz : dd);
+#pragma unroll
+    for (int b = 0; b < kReg / 4; ++b)
+      if (4 * b < ld) out[b] = make_float4(z[4 * b] * inrm, z[4 * b + 1] * inrm, z[4 * b + 2] * inrm, z[4 * b + 3] * inrm);
+  } else {
+    float* z = zsh + threadIdx.x * (DMAX + 1);
+    for (int q = 0; 4 * q < ld; ++q) {
+      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+      if (4 * q < d) {
+        const uint4 w = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
+        box_muller(w.x, w.y, a0, a1);
+        box_muller(w.z, w.w, a2, a3);
+      }
+      const float t[4] = {a0, a1, a2, a3};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float zi = (4 * q + e < d) ? t[e] : 0.0f;
+        z[4 * q + e] = zi;
+        zz = fmaf(zi, zi, zz);
+      }
+    }
+    for (int r = d - 1; r >= 0; --r) {
+      const float4* row = reinterpret_cast<const float4*>(Lf + (long long)r * ld);
+      float acc = 0.0f;
+      const int nb = r / 4;
+      for (int b = 0; b < nb; ++b) {
+        const float4 l = __ldg(row + b);
+        acc = fmaf(l.x, z[4 * b], fmaf(l.y, z[4 * b + 1], fmaf(l.z, z[4 * b + 2], fmaf(l.w, z[4 * b + 3], acc))));
+      }
+      const float* lr = Lf + (long long)r * ld;
+      float t = 0.0f;
+      for (int c = r; c >= 4 * nb; --c) t = fmaf(__ldg(lr + c), z[c], t);
+      z[r] = acc + t;
+      dd = fmaf(z[r], z[r], dd);
+    }
+    const float inrm = rsqrtf(R.dir_norm == 0 ? zz : dd);
+    for (int b = 0; 4 * b < ld; ++b)
+      out[b] = make_float4(z[4 * b] * inrm, z[4 * b + 1] * inrm, z[4 * b + 2] * inrm, z[4 * b + 3] * inrm);
+  }
+}
+
+template <int DMAX>
+size_t dirgen_smem() {
+  return DMAX > 32 ? sizeof(float) * (size_t)kDirThreads * (DMAX + 1) : 0;
+}
+
+}  // namespace
+
+int dirgen_class(int d) {
+  if (d <= 8) return 8;
+  if (d <= 16) return 16;
+  if (d <= 32) return 32;
+  if (d <= 64) return 64;
+  return 128;
+}
+
+cudaError_t setup_dirgen_attributes() {
+  return cudaFuncSetAttribute(k_dirgen<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dirgen_smem<128>());
+}
+
+cudaError_t launch_dirgen(int dclass, const Dev& D, const WorkItem* items, int n, int max_p, cudaStream_t s) {
+  const dim3 grid((n + kDirThreads / 32 - 1) / (kDirThreads / 32), max_p);
+  switch (dclass) {
+    case 8: k_dirgen<8><<<grid, kDirThreads, 0, s>>>(D, items, n); break;
+    case 16: k_dirgen<16><<<grid, kDirThreads, 0, s>>>(D, items, n); break;
+    case 32: k_dirgen<32><<<grid, kDirThreads, 0, s>>>(D, items, n); break;
+    case 64: k_dirgen<64><<<grid, kDirThreads, dirgen_smem<64>(), s>>>(D, items, n); break;
+    case 128: k_dirgen<128><<<grid, kDirThreads, dirgen_smem<128>(), s>>>(D, items, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nss

@@ -64,7 +64,11 @@ cudaError_t launch_terminate(const Dev& D, int n_runs, cudaStream_t s);
 cudaError_t launch_final_sort(const Dev& D, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_volsim(const Dev& D, const VolLaunch& V, int n_runs, cudaStream_t s);
 int sweep_blocks_per_sm(int cfg);
-cudaError_t launch_dirgen(int cfg, const Dev& D, const WorkItem* items, int n, int max_p, cudaStream_t s);
+// directions V[chain][step] of every generic-sweep chain of the iteration;
+// items hold up to 32 chains each, dclass = dirgen_class(d) of their runs
+int dirgen_class(int d);
+cudaError_t setup_dirgen_attributes();
+cudaError_t launch_dirgen(int dclass, const Dev& D, const WorkItem* items, int n, int max_p, cudaStream_t s);
 cudaError_t launch_sweep_lane(int dmax, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
                               cudaStream_t s);
 int sweep_lane_blocks_per_sm(int dmax);

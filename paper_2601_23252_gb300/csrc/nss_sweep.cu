@@ -346,87 +346,6 @@ __global__ void __launch_bounds__(128) k_init(Dev D, const WorkItem* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Direction of HRSS step s of chain j (Sec. 3.2 "Direction metric"):
-// z ~ N(0, I) from words [0, 2 ceil(d/2)) of counter (iter, j, s, .),
-// d~ = L z, v = d~ / |z| (unit Mahalanobis length) or d~ / |d~|.  A
-// direction does not depend on the chain's position, so the directions of
-// every (chain, step) of an iteration are drawn ahead of the sweep by
-// k_dirgen, fully in parallel, and stored as V[chain][step][dpad].
-// ---------------------------------------------------------------------------
-template <int G, int DPL>
-__device__ __forceinline__ void group_direction(const RunDesc& R, const float* __restrict__ f, uint32_t iter,
-                                                int j, int s, int gl, unsigned mask, float* zs,
-                                                float (&v)[DPL]) {
-  const int d = R.d, ld = R.dpad;
-  const bool has = gl * DPL < ld;
-  StepWords<G> W;
-  if constexpr (DPL <= 4) W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, 0u);
-  float z[DPL];
-  step_normals<G, DPL>(W, R, iter, (uint32_t)j, (uint32_t)s, gl, mask, z);
-  float zz = 0.0f;
-#pragma unroll
-  for (int i = 0; i < DPL; ++i) {
-    if (gl * DPL + i >= d) z[i] = 0.0f;
-    zs[gl * DPL + i] = z[i];
-    zz = fmaf(z[i], z[i], zz);
-  }
-  __syncwarp(mask);
-  zz = gsum<G>(zz, mask);
-#pragma unroll
-  for (int i = 0; i < DPL; ++i) v[i] = 0.0f;
-  if (has) {
-    const float4* L4 = reinterpret_cast<const float4*>(f + R.o_L);
-    const float4* zs4 = reinterpret_cast<const float4*>(zs);
-    const int ld4 = ld >> 2;
-    const int row0 = gl * DPL;
-    const int nb = ((row0 + DPL - 1) >> 2) + 1;
-    for (int bb = 0; bb < nb; ++bb) {
-      const float4 zb = zs4[bb];
-#pragma unroll
-      for (int r = 0; r < DPL; ++r) {
-        if (DPL <= 4 || row0 + r < ld) {
-          const float4 l4 = __ldg(L4 + (row0 + r) * ld4 + bb);
-          v[r] = fmaf(l4.x, zb.x, fmaf(l4.y, zb.y, fmaf(l4.z, zb.z, fmaf(l4.w, zb.w, v[r]))));
-        }
-      }
-    }
-  }
-  __syncwarp(mask);
-  float inrm;
-  if (R.dir_norm == 0) {
-    inrm = rsqrtf(zz);
-  } else {
-    float dd = 0.0f;
-#pragma unroll
-    for (int i = 0; i < DPL; ++i) dd = fmaf(v[i], v[i], dd);
-    inrm = rsqrtf(gsum<G>(dd, mask));
-  }
-#pragma unroll
-  for (int i = 0; i < DPL; ++i) v[i] *= inrm;
-}
-
-// blockIdx.y = step s; each warp takes one work item (32/G chains of a run)
-template <int G, int DPL>
-__global__ void __launch_bounds__(128) k_dirgen(Dev D, const WorkItem* __restrict__ items, int n_items) {
-  __shared__ __align__(16) float zbuf[4][32 * DPL];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int gl = lane % G, grp = lane / G;
-  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
-  const int it = blockIdx.x * 4 + wid;
-  if (it >= n_items) return;
-  const WorkItem wi = items[it];
-  const RunDesc& R = D.desc[wi.run];
-  const RunState& S = D.st[wi.run];
-  const int s = blockIdx.y;
-  if (S.done || s >= R.p) return;
-  const int j = wi.c0 + grp;
-  if (j >= wi.c1) return;
-  float v[DPL];
-  group_direction<G, DPL>(R, D.f, (uint32_t)S.iter, j, s, gl, mask, &zbuf[wid][grp * G * DPL], v);
-  if (gl * DPL < R.dpad) store_lane<DPL>(D.f + R.o_V + ((long long)j * R.p + s) * R.dpad, gl, R.dpad, v);
-}
-
-// ---------------------------------------------------------------------------
 // One chain: p HRSS steps from its parent, then replacement of dead slot j.
 //
 // Along the line y(t) = x + t v every quantity of the slice test is a
@@ -463,7 +382,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
   int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
   for (int s = 0; s < R.p; ++s) {
-    // the step's direction, drawn ahead by k_dirgen; the scalar words
+    // the step's direction, drawn ahead (nss_dirgen.cu); the scalar words
     // (U, slice height, shrinkage proposals) from blocks nz/4 + gl
     StepWords<G> W;
     W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, nz >> 2);
@@ -506,12 +425,13 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
         if (own[i]) {
           const int dim = gl * DPL + i;
           const float ai = f[R.o_a + dim] - x[i], bi = f[R.o_b + dim] - x[i];
+          const float rv = __frcp_rn(v[i]);
           if (v[i] > 0.0f) {
-            t_lo = fmaxf(t_lo, ai / v[i]);
-            t_hi = fminf(t_hi, bi / v[i]);
+            t_lo = fmaxf(t_lo, ai * rv);
+            t_hi = fminf(t_hi, bi * rv);
           } else if (v[i] < 0.0f) {
-            t_lo = fmaxf(t_lo, bi / v[i]);
-            t_hi = fminf(t_hi, ai / v[i]);
+            t_lo = fmaxf(t_lo, bi * rv);
+            t_hi = fminf(t_hi, ai * rv);
           } else if (!(ai <= 0.0f && bi >= 0.0f)) {
             t_lo = INFINITY;
           }
@@ -708,25 +628,6 @@ int sweep_blocks_per_sm(int cfg) {
     default: break;
   }
   return nb > 0 ? nb : 1;
-}
-
-cudaError_t launch_dirgen(int cfg, const Dev& D, const WorkItem* items, int n, int max_p, cudaStream_t s) {
-  dim3 grid((n + 3) / 4, max_p);
-  if (cfg >= kLaneCfg0) {
-    switch (lane_dmax(cfg)) {
-      case 8: k_dirgen<1, 8><<<grid, 128, 0, s>>>(D, items, n); break;
-      case 16: k_dirgen<1, 16><<<grid, 128, 0, s>>>(D, items, n); break;
-      default: k_dirgen<1, 32><<<grid, 128, 0, s>>>(D, items, n); break;
-    }
-    return cudaGetLastError();
-  }
-  switch (cfg) {
-#define X(id, g, p) case id: k_dirgen<g, p><<<grid, 128, 0, s>>>(D, items, n); break;
-    NSS_CFGS(X)
-#undef X
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(int cfg, const Dev& D, const WorkItem* items, int n, int* queue, int grid,

@@ -2,9 +2,8 @@
 // sm_103a.
 //
 // A lane holds its chain's whole position x and direction v in registers.
-// Per HRSS step it draws its direction (Philox blocks of its own counter,
-// Box-Muller, the triangular product L z against the run's factor, read as
-// warp-wide broadcasts), then the coefficients of the step's line:
+// Per HRSS step it loads its direction (drawn ahead for every step of the
+// iteration), then forms the coefficients of the step's line:
 //   |x + t v - mu_c|^2 = D_c + t (2 E_c + t C),   box: t in [t_lo, t_hi],
 //   Gaussian prior: sum ((x + t v - a)/b)^2 = P0 + t (2 P1 + t P2),
 // so every slice evaluation of the step is a few scalar FMAs and one
@@ -46,7 +45,7 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
   int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
   for (int s = 0; s < R.p; ++s) {
-    // the step's direction, drawn ahead by k_dirgen
+    // the step's direction, drawn ahead (nss_dirgen.cu)
     float v[DMAX];
     float Cv = 0.0f;
     {

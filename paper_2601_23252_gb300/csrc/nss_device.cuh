@@ -69,6 +69,13 @@ __device__ __forceinline__ float gmax(float v, unsigned mask) {
   return v;
 }
 
+// ballot of a group of G lanes, as bits 0..G-1 (bit i: group lane i)
+template <int G>
+__device__ __forceinline__ unsigned gballot(bool p, unsigned mask) {
+  const unsigned b = __ballot_sync(mask, p) & mask;
+  return G == 32 ? b : b >> (__ffs(mask) - 1);
+}
+
 // ---- block reductions (fixed order: deterministic) ----
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll

@@ -254,6 +254,17 @@ struct StepWords {
     }
     return pick(cw, wi & 3u);
   }
+  // word wi, one per lane (consecutive lanes ask for consecutive words)
+  __device__ __forceinline__ uint32_t lane_word(const RunDesc& R, uint32_t iter, uint32_t chain, uint32_t step,
+                                                uint32_t wi, unsigned mask) const {
+    const uint32_t src = (wi >> 2) - base;
+    const bool shared = src < (uint32_t)G;
+    const int sl = shared ? (int)src : 0;
+    const uint4 blk = make_uint4(__shfl_sync(mask, mine.x, sl, G), __shfl_sync(mask, mine.y, sl, G),
+                                 __shfl_sync(mask, mine.z, sl, G), __shfl_sync(mask, mine.w, sl, G));
+    if (shared) return pick(blk, wi & 3u);
+    return pick(draw_block(R, iter, chain, step, wi >> 2), wi & 3u);
+  }
   // all four words of block b (base <= b < base + G), for lane-specific picks
   __device__ __forceinline__ uint4 block(int b, unsigned mask) const {
     return make_uint4(__shfl_sync(mask, mine.x, b, G), __shfl_sync(mask, mine.y, b, G),
@@ -462,10 +473,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       x0 = __shfl_sync(mask, x[0], 0, G);
       v0 = __shfl_sync(mask, v[0], 0, G);
     }
-    // one logical likelihood evaluation at x + t v: support, prior slice
-    // height, then logL > logL* (Sec. 3.1: E < E_batch)
-    auto in_slice = [&](float t, float& ll) -> bool {
-      ++evals;
+    // one slice test at x + t v: support, prior slice height, then
+    // logL > logL* (Sec. 3.1: E < E_batch).  A NaN likelihood reads as -inf
+    // and is flagged; nothing is counted here.
+    auto probe = [&](float t, float& ll, bool& isn) -> bool {
       if (box && !(t >= t_lo && t <= t_hi)) return false;
       if (nonflat) {
         const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
@@ -491,42 +502,97 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       }
       if (isnan(ll)) {
         ll = -INFINITY;
-        ++nanc;
+        isn = true;
       }
       return ll > lstar;
+    };
+    // Stepping out: an end moves by repeated FP32 steps of +-w while the
+    // slice test at it passes, at most kStepOutCap tests.  The ends it visits
+    // do not depend on the outcomes, so the group tests G consecutive ones at
+    // once; the first that fails is where the one-at-a-time procedure stops,
+    // and the counters are those of that procedure.
+    auto step_out = [&](float start, float delta) -> float {
+      int nfail = kStepOutCap;
+      for (int b0 = 0; b0 < kStepOutCap; b0 += G) {
+        const int idx = b0 + gl;
+        float t = start;
+#pragma unroll
+        for (int i = 0; i < kStepOutCap - 1; ++i)
+          if (i < idx) t += delta;
+        const bool valid = idx < kStepOutCap;
+        bool isn = false;
+        float ll = 0.0f;
+        const bool in = valid && probe(t, ll, isn);
+        const unsigned outb = gballot<G>(valid && !in, mask);
+        const unsigned nanb = gballot<G>(isn, mask);
+        if (outb) {
+          const int f = __ffs(outb) - 1;
+          nfail = b0 + f;
+          nanc += __popc(nanb & ((2u << f) - 1u));
+          break;
+        }
+        nanc += __popc(nanb);
+      }
+      evals += min(nfail + 1, kStepOutCap);
+      exps += nfail;
+      if (nfail == kStepOutCap) ++capo;
+      float t = start;
+      for (int i = 0; i < nfail; ++i) t += delta;
+      return t;
     };
     // randomised initial bracket of width w around t = 0
     const float U = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz, mask));
     float tl = -w * U;
     float tr = tl + w;
-    float lly = 0.0f;
-    for (int n = 0;; ++n) {
-      if (n >= kStepOutCap) { ++capo; break; }
-      if (!in_slice(tl, lly)) break;
-      tl -= w;
-      ++exps;
-    }
-    for (int n = 0;; ++n) {
-      if (n >= kStepOutCap) { ++capo; break; }
-      if (!in_slice(tr, lly)) break;
-      tr += w;
-      ++exps;
-    }
-    // shrinkage, at most 100 proposals, then a null move
+    tl = step_out(tl, -w);
+    tr = step_out(tr, w);
+    // Shrinkage, at most kShrinkCap proposals, then a null move.  Proposal r
+    // is t_r = tl_r + u_r (tr_r - tl_r) and a rejection moves the end on
+    // t_r's side to t_r, so the brackets of the proposals that follow
+    // rejections are known before any test: each round the group forms G
+    // consecutive proposals (a short scan over the shared u's) and tests
+    // them at once; the first inside the slice is the sequential result.
     bool ok = false;
-    for (int r = 0; r < kShrinkCap; ++r) {
-      const float u = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)r, mask));
-      const float t = fmaf(u, tr - tl, tl);
-      ++shr;
-      if (in_slice(t, lly)) {
+    float tacc = 0.0f, llacc = 0.0f;
+    for (int b0 = 0; b0 < kShrinkCap; b0 += G) {
+      const int idx = b0 + gl;
+      const bool valid = idx < kShrinkCap;
+      const float u = u24(W.lane_word(R, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)idx, mask));
+      float lo = tl, hi = tr, t = 0.0f;
 #pragma unroll
-        for (int i = 0; i < DPL; ++i) x[i] = fmaf(t, v[i], x[i]);
-        lx = lly;
+      for (int i = 0; i < G; ++i) {
+        const float ui = __shfl_sync(mask, u, i, G);
+        const float ti = fmaf(ui, hi - lo, lo);
+        if (i == gl) t = ti;
+        if (ti < 0.0f) lo = ti;
+        else hi = ti;
+      }
+      bool isn = false;
+      float ll = 0.0f;
+      const bool in = valid && probe(t, ll, isn);
+      const unsigned inb = gballot<G>(in, mask);
+      const unsigned nanb = gballot<G>(isn, mask);
+      if (inb) {
+        const int f = __ffs(inb) - 1;
+        shr += f + 1;
+        evals += f + 1;
+        nanc += __popc(nanb & ((1u << f) - 1u));
+        tacc = __shfl_sync(mask, t, f, G);
+        llacc = __shfl_sync(mask, ll, f, G);
         ok = true;
         break;
       }
-      if (t < 0.0f) tl = t;
-      else tr = t;
+      const int nvalid = min(G, kShrinkCap - b0);
+      shr += nvalid;
+      evals += nvalid;
+      nanc += __popc(nanb);
+      tl = lo;
+      tr = hi;
+    }
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) x[i] = fmaf(tacc, v[i], x[i]);
+      lx = llacc;
     }
     if (ok) ++acc;
     else ++nul;

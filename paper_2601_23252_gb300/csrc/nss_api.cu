@@ -65,11 +65,15 @@ struct nss_ctx {
   int* ipool = nullptr;
   double* dpool = nullptr;
   long long nf = 0, ni = 0, nd = 0;
-  std::vector<WorkItem> init_items[nss::kNumCfgs], sweep_items[nss::kNumCfgs];
+  // sweep work lists, one per (configuration, mixture bound): list q * 3 + b
+  // holds the chains of configuration q whose runs have mixture bound kKC[b]
+  static constexpr int kKC[3] = {1, 4, 8};
+  static constexpr int kLists = nss::kNumCfgs * 3;
+  std::vector<WorkItem> init_items[nss::kNumCfgs], sweep_items[kLists];
   WorkItem* d_init[nss::kNumCfgs] = {};
-  WorkItem* d_sweep[nss::kNumCfgs] = {};
+  WorkItem* d_sweep[kLists] = {};
   int* d_queue = nullptr;
-  int sweep_grid[nss::kNumCfgs] = {};
+  int sweep_grid[kLists] = {};
   // direction generation: items of up to 32 chains, per dimension class 8..128
   static constexpr int kDirClasses = 5;
   std::vector<WorkItem> dir_items[kDirClasses];
@@ -293,10 +297,8 @@ void free_ctx(nss_ctx* c) {
   cudaFree(c->fpool);
   cudaFree(c->ipool);
   cudaFree(c->dpool);
-  for (int q = 0; q < nss::kNumCfgs; ++q) {
-    cudaFree(c->d_init[q]);
-    cudaFree(c->d_sweep[q]);
-  }
+  for (int q = 0; q < nss::kNumCfgs; ++q) cudaFree(c->d_init[q]);
+  for (int q = 0; q < nss_ctx::kLists; ++q) cudaFree(c->d_sweep[q]);
   for (int q = 0; q < nss_ctx::kDirClasses; ++q) cudaFree(c->d_dir[q]);
   cudaFree(c->d_queue);
   cudaFree(c->d_vol);
@@ -397,12 +399,12 @@ nss_status enqueue_iteration(nss_ctx* c) {
     CK(nss::launch_dirgen(8 << q, D, c->d_dir[q], (int)c->dir_items[q].size(), c->max_p, c->stream),
        "direction launch");
   }
-  for (int q = 0; q < nss::kNumCfgs; ++q) {
+  for (int q = 0; q < nss_ctx::kLists; ++q) {
     if (c->sweep_items[q].empty()) continue;
     CK(cudaMemsetAsync(c->d_queue + q, 0, sizeof(int), c->stream), "queue reset");
-    Rec r(c, NSS_K_SWEEP, q);
-    CK(nss::launch_sweep(q, D, c->d_sweep[q], (int)c->sweep_items[q].size(), c->d_queue + q,
-                         c->sweep_grid[q], c->stream), "sweep launch");
+    Rec r(c, NSS_K_SWEEP, q / 3);
+    CK(nss::launch_sweep(q / 3, nss_ctx::kKC[q % 3], D, c->d_sweep[q], (int)c->sweep_items[q].size(),
+                         c->d_queue + q, c->sweep_grid[q], c->stream), "sweep launch");
   }
   for (auto& g : c->gp) {
     const RunDesc& R = c->desc[g.run];
@@ -468,10 +470,13 @@ nss_status build_work(nss_ctx* c) {
   }
   for (int q = 0; q < nss::kNumCfgs; ++q) {
     c->init_items[q].clear();
-    c->sweep_items[q].clear();
     cudaFree(c->d_init[q]);
+    c->d_init[q] = nullptr;
+  }
+  for (int q = 0; q < nss_ctx::kLists; ++q) {
+    c->sweep_items[q].clear();
     cudaFree(c->d_sweep[q]);
-    c->d_init[q] = c->d_sweep[q] = nullptr;
+    c->d_sweep[q] = nullptr;
   }
   for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
     c->dir_items[q].clear();
@@ -486,7 +491,9 @@ nss_status build_work(nss_ctx* c) {
     const int iper = 32 / nss::cfg_g(icfg);
     for (int s = 0; s < R.m; s += iper) c->init_items[icfg].push_back({r, s, std::min(s + iper, R.m), 0});
     if (R.lik_kind == nss::kLikLogreg || R.lik_kind == nss::kLikGp) continue;  // own sweep kernels
-    for (int j = 0; j < R.k; j += per) c->sweep_items[R.cfg].push_back({r, j, std::min(j + per, R.k), 0});
+    const int kc = nss::sweep_kc(R.lik_kind, R.n_comp);
+    const int list = R.cfg * 3 + (kc == 1 ? 0 : kc == 4 ? 1 : 2);
+    for (int j = 0; j < R.k; j += per) c->sweep_items[list].push_back({r, j, std::min(j + per, R.k), 0});
     int dq = 0;
     while ((8 << dq) < nss::dirgen_class(R.d)) ++dq;
     for (int j = 0; j < R.k; j += 32) c->dir_items[dq].push_back({r, j, std::min(j + 32, R.k), 0});
@@ -498,20 +505,22 @@ nss_status build_work(nss_ctx* c) {
                        cudaMemcpyHostToDevice, c->stream), "work list upload");
   }
   for (int q = 0; q < nss::kNumCfgs; ++q) {
-    auto cost = [&](const WorkItem& w) { return (double)c->desc[w.run].p * c->desc[w.run].d; };
-    std::stable_sort(c->sweep_items[q].begin(), c->sweep_items[q].end(),
-                     [&](const WorkItem& a, const WorkItem& b) { return cost(a) > cost(b); });
     if (!c->init_items[q].empty()) {
       CK(cudaMalloc(&c->d_init[q], sizeof(WorkItem) * c->init_items[q].size()), "work list allocation");
       CK(cudaMemcpyAsync(c->d_init[q], c->init_items[q].data(), sizeof(WorkItem) * c->init_items[q].size(),
                          cudaMemcpyHostToDevice, c->stream), "work list upload");
     }
+  }
+  for (int q = 0; q < nss_ctx::kLists; ++q) {
+    auto cost = [&](const WorkItem& w) { return (double)c->desc[w.run].p * c->desc[w.run].d; };
+    std::stable_sort(c->sweep_items[q].begin(), c->sweep_items[q].end(),
+                     [&](const WorkItem& a, const WorkItem& b) { return cost(a) > cost(b); });
     if (!c->sweep_items[q].empty()) {
       CK(cudaMalloc(&c->d_sweep[q], sizeof(WorkItem) * c->sweep_items[q].size()), "work list allocation");
       CK(cudaMemcpyAsync(c->d_sweep[q], c->sweep_items[q].data(), sizeof(WorkItem) * c->sweep_items[q].size(),
                          cudaMemcpyHostToDevice, c->stream), "work list upload");
-      const int per_sm = nss::sweep_blocks_per_sm(q);
-      const int wpb = nss::sweep_warps_per_block(q);
+      const int per_sm = nss::sweep_blocks_per_sm(q / 3, nss_ctx::kKC[q % 3]);
+      const int wpb = nss::sweep_warps_per_block(q / 3);
       const int warps_needed = (int)c->sweep_items[q].size();
       const int blocks_needed = (warps_needed + wpb - 1) / wpb;
       c->sweep_grid[q] = std::max(1, std::min(blocks_needed, per_sm * c->num_sms));
@@ -987,7 +996,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   CKC(cudaMalloc(&c->fpool, sizeof(float) * std::max(c->nf, 16LL)), "FP32 pool allocation");
   CKC(cudaMalloc(&c->ipool, sizeof(int) * std::max(c->ni, 16LL)), "INT32 pool allocation");
   CKC(cudaMalloc(&c->dpool, sizeof(double) * std::max(c->nd, 16LL)), "FP64 pool allocation");
-  CKC(cudaMalloc(&c->d_queue, sizeof(int) * nss::kNumCfgs), "queue allocation");
+  CKC(cudaMalloc(&c->d_queue, sizeof(int) * nss_ctx::kLists), "queue allocation");
   CKC(cudaMalloc(&c->d_vbase, sizeof(int) * n_runs), "vbase allocation");
   CKC(cudaMemsetAsync(c->fpool, 0, sizeof(float) * std::max(c->nf, 16LL), c->stream), "pool clear");
   CKC(cudaMemsetAsync(c->ipool, 0, sizeof(int) * std::max(c->ni, 16LL), c->stream), "pool clear");

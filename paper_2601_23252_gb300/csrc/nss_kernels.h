@@ -58,20 +58,22 @@ cudaError_t launch_lr_replace(const Dev& D, const LRArgs& A, int run, int k, cud
 
 cudaError_t launch_init(int cfg, const Dev& D, const WorkItem* items, int n, cudaStream_t s);
 cudaError_t launch_prologue(const Dev& D, int n_runs, size_t smem, cudaStream_t s);
-cudaError_t launch_sweep(int cfg, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
+// the sweep of configuration cfg for runs of mixture bound kc = sweep_kc(.)
+cudaError_t launch_sweep(int cfg, int kc, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
                          cudaStream_t s);
+int sweep_kc(int lik_kind, int n_comp);
 cudaError_t launch_terminate(const Dev& D, int n_runs, cudaStream_t s);
 cudaError_t launch_final_sort(const Dev& D, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_volsim(const Dev& D, const VolLaunch& V, int n_runs, cudaStream_t s);
-int sweep_blocks_per_sm(int cfg);
+int sweep_blocks_per_sm(int cfg, int kc);
 // directions V[chain][step] of every generic-sweep chain of the iteration;
 // items hold up to 32 chains each, dclass = dirgen_class(d) of their runs
 int dirgen_class(int d);
 cudaError_t setup_dirgen_attributes();
 cudaError_t launch_dirgen(int dclass, const Dev& D, const WorkItem* items, int n, int max_p, cudaStream_t s);
-cudaError_t launch_sweep_lane(int dmax, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
+cudaError_t launch_sweep_lane(int dmax, int kc, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
                               cudaStream_t s);
-int sweep_lane_blocks_per_sm(int dmax);
+int sweep_lane_blocks_per_sm(int dmax, int kc);
 int sweep_lane_warps_per_block();
 int sweep_warps_per_block(int cfg);
 int cfg_g(int cfg);

@@ -1,0 +1,338 @@
+// nss_sweep_chain.cuh -- the Hit-and-Run Slice Sampling sweep (steps
+// (iii)+(iv) of Sec. 3.1; HRSS of Sec. 3.2 and App. B.4), for sm_103a.
+//
+// A chain is owned by a group of G lanes of one warp; lane gl holds the DPL
+// dimensions [gl*DPL, gl*DPL + DPL) of the chain's position x and of the
+// step's direction v in registers.  A warp holds 32/G chains of one run.
+// Group reductions are xor butterflies, so every lane of the group ends with
+// the bitwise-identical value and the whole group takes the same branch.
+// Chains of a warp step in lockstep per HRSS step and diverge only inside
+// the stepping-out and shrinkage rounds; a persistent grid takes warps' worth
+// of chains from an atomic ticket queue (costliest runs first), so a warp
+// that finishes early takes the next chains instead of idling.  No lane ever
+// waits on another block.
+//
+// KC bounds the number of mixture components (1: one isotropic Gaussian or
+// no likelihood; 4; 8).  Components K..KC-1 of a run with fewer read as
+// infinitely far, so the component loops are fully unrolled and branch-free.
+// Each KC is instantiated in its own translation unit (nss_sweep_k*.cu).
+#pragma once
+#include "nss_sweep_common.cuh"
+
+namespace nss {
+
+// ---------------------------------------------------------------------------
+// One chain: p HRSS steps from its parent, then replacement of dead slot j.
+//
+// Along the line y(t) = x + t v every quantity of the slice test is a
+// polynomial in t of degree <= 2, so once per step the group reduces the
+// coefficients and every evaluation of that step is scalar arithmetic:
+//   |y - mu_c|^2 = D_c + t (2 E_c + t C),  D_c = |x - mu_c|^2,
+//                  E_c = (x - mu_c).v,  C = |v|^2;
+//   box support:   a <= y <= b  <=>  t_lo <= t <= t_hi;
+//   Gaussian prior: sum ((y - a)/b)^2 = P0 + t (2 P1 + t P2).
+// The moved point x + t v is formed coordinate by coordinate on acceptance.
+// ---------------------------------------------------------------------------
+template <int G, int DPL, int KC>
+__device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j, int gl, unsigned mask) {
+  const float* __restrict__ f = D.f;
+  const int d = R.d, ld = R.dpad;
+  const bool has = gl * DPL < ld;
+  const int parent = D.i[R.o_parent + j];
+  const uint32_t iter = (uint32_t)Sw->iter;
+  const float lstar = Sw->logLstar;
+  const bool box = R.prior_kind == kPriorBox, nonflat = !box;
+  const int lk = R.lik_kind;
+  const int K = (lk == kLikGmm) ? R.n_comp : ((lk == kLikGauss || lk == kLikFault) ? 1 : 0);
+  bool own[DPL];
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) own[i] = gl * DPL + i < d;
+  float x[DPL];
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) x[i] = 0.0f;
+  if (has) load_lane<DPL>(f + R.o_x + (long long)parent * ld, gl, ld, x);
+  float lx = f[R.o_logL + parent];
+  const float w = R.w;
+  const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
+  int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
+  for (int s = 0; s < R.p; ++s) {
+    // the step's direction, drawn ahead (nss_dirgen.cu); the scalar words
+    // (U, slice height, shrinkage proposals) from blocks nz/4 + gl
+    StepWords<G> W;
+    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, nz >> 2);
+    float v[DPL];
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) v[i] = 0.0f;
+    if (has) ldg_lane<DPL>(f + R.o_V + ((long long)j * R.p + s) * ld, gl, ld, v);
+
+    // coefficients of the step's line, reduced over the group
+    float Cv = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) Cv = fmaf(v[i], v[i], Cv);
+    Cv = gsum<G>(Cv, mask);
+    float Dc[KC], Ec[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      Dc[c] = INFINITY;
+      Ec[c] = 0.0f;
+    }
+    if (K > 0) {
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        const int cr = c < K ? c : K - 1;  // rows past K repeat the last one, then read as infinitely far
+        float m[DPL];
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) m[i] = 0.0f;
+        if (has) ldg_lane<DPL>(f + R.o_mu + (long long)cr * ld, gl, ld, m);
+        float dq = 0.0f, de = 0.0f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) {
+          const float e = x[i] - m[i];
+          dq = fmaf(e, e, dq);
+          de = fmaf(e, v[i], de);
+        }
+        dq = gsum<G>(dq, mask);
+        Ec[c] = gsum<G>(de, mask);
+        Dc[c] = c < K ? dq : INFINITY;
+      }
+    }
+    float t_lo = -INFINITY, t_hi = INFINITY;
+    float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f, height = 0.0f;
+    if (box) {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) {
+        if (own[i]) {
+          const int dim = gl * DPL + i;
+          const float ai = f[R.o_a + dim] - x[i], bi = f[R.o_b + dim] - x[i];
+          const float rv = __frcp_rn(v[i]);
+          if (v[i] > 0.0f) {
+            t_lo = fmaxf(t_lo, ai * rv);
+            t_hi = fminf(t_hi, bi * rv);
+          } else if (v[i] < 0.0f) {
+            t_lo = fmaxf(t_lo, bi * rv);
+            t_hi = fminf(t_hi, ai * rv);
+          } else if (!(ai <= 0.0f && bi >= 0.0f)) {
+            t_lo = INFINITY;
+          }
+        }
+      }
+      t_lo = gmax<G>(t_lo, mask);
+      t_hi = -gmax<G>(-t_hi, mask);
+    } else {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) {
+        if (own[i]) {
+          const int dim = gl * DPL + i;
+          const float ib = 1.0f / f[R.o_b + dim];
+          const float u = (x[i] - f[R.o_a + dim]) * ib, q = v[i] * ib;
+          P0 = fmaf(u, u, P0);
+          P1 = fmaf(u, q, P1);
+          P2 = fmaf(q, q, P2);
+        }
+      }
+      P0 = gsum<G>(P0, mask);
+      P1 = gsum<G>(P1, mask);
+      P2 = gsum<G>(P2, mask);
+      const float uh = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz + 1u, mask));
+      height = fmaf(-0.5f, P0, R.prior_const) + logf(uh);
+    }
+    float x0 = 0.0f, v0 = 0.0f;  // coordinate 0 for the fault likelihood
+    if (lk == kLikFault) {
+      x0 = __shfl_sync(mask, x[0], 0, G);
+      v0 = __shfl_sync(mask, v[0], 0, G);
+    }
+    // one slice test at x + t v: support, prior slice height, then
+    // logL > logL* (Sec. 3.1: E < E_batch).  A NaN likelihood reads as -inf
+    // and is flagged; nothing is counted here.
+    auto probe = [&](float t, float& ll, bool& isn) -> bool {
+      if (box && !(t >= t_lo && t <= t_hi)) return false;
+      if (nonflat) {
+        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
+        if (!(lp > height)) return false;
+      }
+      if (lk == kLikFlat) {
+        ll = 0.0f;
+      } else {
+        float vc[KC];
+        float M = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+          vc[c] = -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * R.inv2s2;
+          M = fmaxf(M, vc[c]);
+        }
+        if constexpr (KC == 1) {
+          ll = M + R.lognorm;
+        } else {
+          float S = 0.0f;
+#pragma unroll
+          for (int c = 0; c < KC; ++c) S += __expf(vc[c] - M);
+          ll = M + __logf(S) + R.lognorm;
+        }
+        if (lk == kLikFault && fmaf(t, v0, x0) < R.fault_param)
+          ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
+      }
+      if (isnan(ll)) {
+        ll = -INFINITY;
+        isn = true;
+      }
+      return ll > lstar;
+    };
+    // Stepping out: an end moves by repeated FP32 steps of +-w while the
+    // slice test at it passes, at most kStepOutCap tests.  The ends it visits
+    // do not depend on the outcomes, so the group tests G consecutive ones at
+    // once; the first that fails is where the one-at-a-time procedure stops,
+    // and the counters are those of that procedure.
+    auto step_out = [&](float start, float delta) -> float {
+      int nfail = kStepOutCap;
+      for (int b0 = 0; b0 < kStepOutCap; b0 += G) {
+        const int idx = b0 + gl;
+        float t = start;
+#pragma unroll
+        for (int i = 0; i < kStepOutCap - 1; ++i)
+          if (i < idx) t += delta;
+        const bool valid = idx < kStepOutCap;
+        bool isn = false;
+        float ll = 0.0f;
+        const bool in = valid && probe(t, ll, isn);
+        const unsigned outb = gballot<G>(valid && !in, mask);
+        const unsigned nanb = gballot<G>(isn, mask);
+        if (outb) {
+          const int f = __ffs(outb) - 1;
+          nfail = b0 + f;
+          nanc += __popc(nanb & ((2u << f) - 1u));
+          break;
+        }
+        nanc += __popc(nanb);
+      }
+      evals += min(nfail + 1, kStepOutCap);
+      exps += nfail;
+      if (nfail == kStepOutCap) ++capo;
+      float t = start;
+      for (int i = 0; i < nfail; ++i) t += delta;
+      return t;
+    };
+    // randomised initial bracket of width w around t = 0
+    const float U = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz, mask));
+    float tl = -w * U;
+    float tr = tl + w;
+    tl = step_out(tl, -w);
+    tr = step_out(tr, w);
+    // Shrinkage, at most kShrinkCap proposals, then a null move.  Proposal r
+    // is t_r = tl_r + u_r (tr_r - tl_r) and a rejection moves the end on
+    // t_r's side to t_r, so the brackets of the proposals that follow
+    // rejections are known before any test: each round the group forms G
+    // consecutive proposals (a short scan over the shared u's) and tests
+    // them at once; the first inside the slice is the sequential result.
+    bool ok = false;
+    float tacc = 0.0f, llacc = 0.0f;
+    for (int b0 = 0; b0 < kShrinkCap; b0 += G) {
+      const int idx = b0 + gl;
+      const bool valid = idx < kShrinkCap;
+      const float u = u24(W.lane_word(R, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)idx, mask));
+      float lo = tl, hi = tr, t = 0.0f;
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const float ui = __shfl_sync(mask, u, i, G);
+        const float ti = fmaf(ui, hi - lo, lo);
+        if (i == gl) t = ti;
+        if (ti < 0.0f) lo = ti;
+        else hi = ti;
+      }
+      bool isn = false;
+      float ll = 0.0f;
+      const bool in = valid && probe(t, ll, isn);
+      const unsigned inb = gballot<G>(in, mask);
+      const unsigned nanb = gballot<G>(isn, mask);
+      if (inb) {
+        const int f = __ffs(inb) - 1;
+        shr += f + 1;
+        evals += f + 1;
+        nanc += __popc(nanb & ((1u << f) - 1u));
+        tacc = __shfl_sync(mask, t, f, G);
+        llacc = __shfl_sync(mask, ll, f, G);
+        ok = true;
+        break;
+      }
+      const int nvalid = min(G, kShrinkCap - b0);
+      shr += nvalid;
+      evals += nvalid;
+      nanc += __popc(nanb);
+      tl = lo;
+      tr = hi;
+    }
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) x[i] = fmaf(tacc, v[i], x[i]);
+      lx = llacc;
+    }
+    if (ok) ++acc;
+    else ++nul;
+  }
+  // (iv) replace dead slot j, born at logL*
+  const int slot = D.i[R.o_dead + j];
+  if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, ld, x);
+  if (gl == 0) {
+    D.f[R.o_logL + slot] = lx;
+    D.f[R.o_birth + slot] = lstar;
+    int* st = D.i + R.o_stats;
+    st[j] = evals;
+    st[R.k + j] = acc;
+    st[2 * R.k + j] = nul;
+    st[3 * R.k + j] = exps;
+    st[4 * R.k + j] = shr;
+    st[5 * R.k + j] = capo;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->evals), (unsigned long long)evals);
+    if (nul) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nulls), (unsigned long long)nul);
+    if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->cap_out), (unsigned long long)capo);
+    if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nan_evals), (unsigned long long)nanc);
+  }
+}
+
+// resident blocks per SM the register budget is tuned for
+constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 5 : dpl == 4 ? 4 : dpl == 8 ? 4 : 3; }
+
+template <int G, int DPL, int KC>
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(Dev D, const WorkItem* __restrict__ items, int n_items,
+                                                         int* queue) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % G, grp = lane / G;
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(queue, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
+    const WorkItem wi = items[it];
+    RunState* S = D.st + wi.run;
+    if (S->done) continue;
+    const int j = wi.c0 + grp;
+    if (j < wi.c1) sweep_chain<G, DPL, KC>(D, D.desc[wi.run], S, j, gl, mask);
+    __syncwarp();
+  }
+}
+
+template <int KC>
+cudaError_t launch_sweep_kc(int cfg, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
+                            cudaStream_t s) {
+  switch (cfg) {
+#define X(id, g, p) case id: k_sweep<g, p, KC><<<grid, kSweepThreads, 0, s>>>(D, items, n, queue); break;
+    NSS_CFGS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int KC>
+int sweep_blocks_per_sm_kc(int cfg) {
+  int nb = 0;
+  switch (cfg) {
+#define X(id, g, p) case id: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<g, p, KC>, kSweepThreads, 0); break;
+    NSS_CFGS(X)
+#undef X
+    default: break;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+}  // namespace nss

@@ -19,9 +19,7 @@ namespace nss {
 namespace {
 
 constexpr int kLaneThreads = 32;   // one warp per block: few warps in total, spread over every SM
-constexpr int kLaneMaxComp = 8;
-
-template <int DMAX>
+template <int DMAX, int KC>
 __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) {
   const float* __restrict__ f = D.f;
   const int d = R.d, ld = R.dpad;
@@ -58,12 +56,13 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
 #pragma unroll
       for (int a = 0; a < DMAX; ++a) Cv = fmaf(v[a], v[a], Cv);
     }
-    // mixture coefficients
-    float Dc[kLaneMaxComp], Ec[kLaneMaxComp];
+    // mixture coefficients; components K..KC-1 read as infinitely far
+    float Dc[KC], Ec[KC];
 #pragma unroll
-    for (int c = 0; c < kLaneMaxComp; ++c) {
-      float dq = 0.0f, de = 0.0f;
+    for (int c = 0; c < KC; ++c) {
+      float dq = INFINITY, de = 0.0f;
       if (c < K) {
+        dq = 0.0f;
         const float4* m4 = reinterpret_cast<const float4*>(f + R.o_mu + (long long)c * ld);
 #pragma unroll
         for (int b = 0; b < DMAX / 4; ++b) {
@@ -131,18 +130,21 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
       if (lk == kLikFlat) {
         ll = 0.0f;
       } else {
-        float vc[kLaneMaxComp];
+        float vc[KC];
         float M = -INFINITY;
 #pragma unroll
-        for (int c = 0; c < kLaneMaxComp; ++c) {
-          vc[c] = (c < K) ? -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * R.inv2s2 : -INFINITY;
+        for (int c = 0; c < KC; ++c) {
+          vc[c] = -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * R.inv2s2;
           M = fmaxf(M, vc[c]);
         }
-        float S = 0.0f;
+        if constexpr (KC == 1) {
+          ll = M + R.lognorm;
+        } else {
+          float S = 0.0f;
 #pragma unroll
-        for (int c = 0; c < kLaneMaxComp; ++c)
-          if (c < K) S += __expf(vc[c] - M);
-        ll = (K == 1 ? M : M + __logf(S)) + R.lognorm;
+          for (int c = 0; c < KC; ++c) S += __expf(vc[c] - M);
+          ll = M + __logf(S) + R.lognorm;
+        }
         if (lk == kLikFault && fmaf(t, v[0], x[0]) < R.fault_param)
           ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
       }
@@ -205,9 +207,9 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
   if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nan_evals), (unsigned long long)nanc);
 }
 
-template <int DMAX>
-__global__ void __launch_bounds__(kLaneThreads, (DMAX >= 32 ? 8 : 16)) k_sweep_lane(Dev D, const WorkItem* __restrict__ items, int n_items,
-                                                                int* queue) {
+template <int DMAX, int KC>
+__global__ void __launch_bounds__(kLaneThreads, (DMAX >= 32 ? 8 : 16)) k_sweep_lane(Dev D, const WorkItem* __restrict__ items,
+                                                                                int n_items, int* queue) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     int it = 0;
@@ -218,35 +220,55 @@ __global__ void __launch_bounds__(kLaneThreads, (DMAX >= 32 ? 8 : 16)) k_sweep_l
     RunState* S = D.st + wi.run;
     if (S->done) continue;
     const int j = wi.c0 + lane;
-    if (j < wi.c1) lane_chain<DMAX>(D, D.desc[wi.run], S, j);
+    if (j < wi.c1) lane_chain<DMAX, KC>(D, D.desc[wi.run], S, j);
     __syncwarp();
   }
 }
 
-}  // namespace
-
-cudaError_t launch_sweep_lane(int dmax, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
-                              cudaStream_t s) {
-  switch (dmax) {
-    case 8: k_sweep_lane<8><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
-    case 16: k_sweep_lane<16><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
-    case 32: k_sweep_lane<32><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
+template <int DMAX>
+cudaError_t launch_lane_dmax(int kc, const Dev& D, const WorkItem* items, int n, int* queue, int grid, cudaStream_t s) {
+  switch (kc) {
+    case 1: k_sweep_lane<DMAX, 1><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
+    case 4: k_sweep_lane<DMAX, 4><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
+    case 8: k_sweep_lane<DMAX, 8><<<grid, kLaneThreads, 0, s>>>(D, items, n, queue); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-int sweep_lane_warps_per_block() { return kLaneThreads / 32; }
-
-int sweep_lane_blocks_per_sm(int dmax) {
+template <int DMAX>
+int lane_blocks_dmax(int kc) {
   int nb = 0;
-  switch (dmax) {
-    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<8>, kLaneThreads, 0); break;
-    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<16>, kLaneThreads, 0); break;
-    case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<32>, kLaneThreads, 0); break;
+  switch (kc) {
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<DMAX, 1>, kLaneThreads, 0); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<DMAX, 4>, kLaneThreads, 0); break;
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_lane<DMAX, 8>, kLaneThreads, 0); break;
     default: break;
   }
   return nb > 0 ? nb : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_lane(int dmax, int kc, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
+                              cudaStream_t s) {
+  switch (dmax) {
+    case 8: return launch_lane_dmax<8>(kc, D, items, n, queue, grid, s);
+    case 16: return launch_lane_dmax<16>(kc, D, items, n, queue, grid, s);
+    case 32: return launch_lane_dmax<32>(kc, D, items, n, queue, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int sweep_lane_warps_per_block() { return kLaneThreads / 32; }
+
+int sweep_lane_blocks_per_sm(int dmax, int kc) {
+  switch (dmax) {
+    case 8: return lane_blocks_dmax<8>(kc);
+    case 16: return lane_blocks_dmax<16>(kc);
+    case 32: return lane_blocks_dmax<32>(kc);
+    default: return 1;
+  }
 }
 
 }  // namespace nss

@@ -29,6 +29,11 @@ def _wl(name, seed):
                           sigma=0.05, mu=np.full((1, d), 0.4), seed=seed)
     if name == "gauss20":
         return W.gauss20_paper(seed=seed, n_live=256, k=100).with_(p=10)
+    if name in ("gmm_d10_k3", "gmm_d20_k6"):
+        d, K = (10, 3) if name == "gmm_d10_k3" else (20, 6)
+        mu = np.random.default_rng(seed + 100).uniform(0.2, 0.8, size=(K, d))
+        return W.Workload(name, d, "box", np.zeros(d), np.ones(d), "gmm", 300, 150, 2 * d,
+                          sigma=0.05, mu=mu, seed=seed)
     raise KeyError(name)
 
 
@@ -48,7 +53,7 @@ def test_initial_live_set_matches_checker(gpu_lib, name):
 
 @pytest.mark.parametrize("name,seed,warm", [
     ("gauss_d2", 1, 1), ("gauss_d2", 2, 6), ("gauss_d5_odd", 4, 3), ("gmm_d32_small", 5, 4),
-    ("gmm_d32", 0, 3), ("gmm_d32", 7, 25), ("gauss20", 2, 5)])
+    ("gmm_d32", 0, 3), ("gmm_d32", 7, 25), ("gauss20", 2, 5), ("gmm_d10_k3", 3, 4), ("gmm_d20_k6", 6, 4)])
 def test_one_step_parity(gpu_lib, name, seed, warm):
     wl = _wl(name, seed)
     rep = compare_step(wl, warm)
@@ -96,7 +101,7 @@ def test_one_step_parity(gpu_lib, name, seed, warm):
     assert np.array_equal(gs["x"][keep], rep["x32"][keep])
 
 
-@pytest.mark.parametrize("name", ["gauss_d2", "gauss_d5_odd", "gauss20", "gmm_d32"])
+@pytest.mark.parametrize("name", ["gauss_d2", "gauss_d5_odd", "gauss20", "gmm_d32", "gmm_d20_k6"])
 def test_one_step_parity_every_sweep_configuration(gpu_lib, name):
     """Every (lanes per chain, dims per lane) configuration that fits d gives
     the same selection and parents and counters matching the checker; d = 5

@@ -55,15 +55,21 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   const float w = R.w;
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
   int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
+  // the steps' directions, drawn ahead (nss_dirgen.cu); the load of step
+  // s + 1's is issued while step s runs
+  const float* vrow = f + R.o_V + (long long)j * R.p * ld;
+  float vn[DPL];
+#pragma unroll
+  for (int i = 0; i < DPL; ++i) vn[i] = 0.0f;
+  if (has) ldg_lane<DPL>(vrow, gl, ld, vn);
   for (int s = 0; s < R.p; ++s) {
-    // the step's direction, drawn ahead (nss_dirgen.cu); the scalar words
-    // (U, slice height, shrinkage proposals) from blocks nz/4 + gl
-    StepWords<G> W;
-    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, nz >> 2);
     float v[DPL];
 #pragma unroll
-    for (int i = 0; i < DPL; ++i) v[i] = 0.0f;
-    if (has) ldg_lane<DPL>(f + R.o_V + ((long long)j * R.p + s) * ld, gl, ld, v);
+    for (int i = 0; i < DPL; ++i) v[i] = vn[i];
+    if (has && s + 1 < R.p) ldg_lane<DPL>(vrow + (long long)(s + 1) * ld, gl, ld, vn);
+    // the scalar words (U, slice height, shrinkage proposals) from blocks nz/4 + gl
+    StepWords<G> W;
+    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, nz >> 2);
 
     // coefficients of the step's line, reduced over the group
     float Cv = 0.0f;
@@ -178,45 +184,80 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       return ll > lstar;
     };
     // Stepping out: an end moves by repeated FP32 steps of +-w while the
-    // slice test at it passes, at most kStepOutCap tests.  The ends it visits
-    // do not depend on the outcomes, so the group tests G consecutive ones at
-    // once; the first that fails is where the one-at-a-time procedure stops,
-    // and the counters are those of that procedure.
-    auto step_out = [&](float start, float delta) -> float {
-      int nfail = kStepOutCap;
-      for (int b0 = 0; b0 < kStepOutCap; b0 += G) {
-        const int idx = b0 + gl;
-        float t = start;
+    // slice test at it passes, at most kStepOutCap tests per side; index
+    // kStepOutCap of a side is a stop that is never tested (the cap).  The
+    // ends visited do not depend on the outcomes, so with G >= 2 the group
+    // tests both sides at once: lanes [0, H) the left and [H, G) the right,
+    // H = G/2 consecutive ends of each per round.  The first failing end of
+    // a side is where the one-at-a-time procedure stops, and the counters are
+    // those of that procedure.
+    const float U = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz, mask));
+    const float tl0 = -w * U;
+    float ends[2] = {tl0, tl0 + w};
+    if constexpr (G >= 2) {
+      constexpr int H = G / 2;
+      constexpr unsigned kHalf = (H == 32) ? 0xffffffffu : ((1u << H) - 1u);
+      const int side = gl >= H ? 1 : 0;
+      const int hl = gl - side * H;
+      const float delta = side ? w : -w;
+      float base[2] = {ends[0], ends[1]};  // the end at index b0 of each side
+      int stop[2] = {-1, -1};
+      for (int b0 = 0; stop[0] < 0 || stop[1] < 0; b0 += H) {
+        const bool mine_open = (side ? stop[1] : stop[0]) < 0;
+        const int idx = b0 + hl;
+        float t = side ? base[1] : base[0];
 #pragma unroll
-        for (int i = 0; i < kStepOutCap - 1; ++i)
-          if (i < idx) t += delta;
-        const bool valid = idx < kStepOutCap;
+        for (int i = 0; i < H - 1; ++i)
+          if (i < hl) t += delta;
         bool isn = false;
         float ll = 0.0f;
-        const bool in = valid && probe(t, ll, isn);
-        const unsigned outb = gballot<G>(valid && !in, mask);
-        const unsigned nanb = gballot<G>(isn, mask);
-        if (outb) {
-          const int f = __ffs(outb) - 1;
-          nfail = b0 + f;
-          nanc += __popc(nanb & ((2u << f) - 1u));
-          break;
+        const bool in = mine_open && idx < kStepOutCap && probe(t, ll, isn);
+        const bool halt = mine_open && (idx >= kStepOutCap || !in);
+        const unsigned hb = gballot<G>(halt, mask);
+        const unsigned nb = gballot<G>(isn, mask);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (stop[q] >= 0) continue;
+          const unsigned hq = (hb >> (q * H)) & kHalf, nq = (nb >> (q * H)) & kHalf;
+          if (hq) {
+            const int fq = __ffs(hq) - 1;
+            stop[q] = b0 + fq;
+            nanc += __popc(nq & ((2u << fq) - 1u));
+            ends[q] = __shfl_sync(mask, t, q * H + fq, G);
+          } else {
+            nanc += __popc(nq);
+            base[q] = __shfl_sync(mask, t, q * H + H - 1, G) + (q ? w : -w);
+          }
         }
-        nanc += __popc(nanb);
       }
-      evals += min(nfail + 1, kStepOutCap);
-      exps += nfail;
-      if (nfail == kStepOutCap) ++capo;
-      float t = start;
-      for (int i = 0; i < nfail; ++i) t += delta;
-      return t;
-    };
-    // randomised initial bracket of width w around t = 0
-    const float U = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz, mask));
-    float tl = -w * U;
-    float tr = tl + w;
-    tl = step_out(tl, -w);
-    tr = step_out(tr, w);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        evals += min(stop[q] + 1, kStepOutCap);
+        exps += stop[q];
+        if (stop[q] == kStepOutCap) ++capo;
+      }
+    } else {
+      // one lane: the left side, then the right
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float delta = q ? w : -w;
+        float t = ends[q];
+        int n = 0;
+        for (; n < kStepOutCap; ++n) {
+          bool isn = false;
+          float ll = 0.0f;
+          const bool in = probe(t, ll, isn);
+          if (isn) ++nanc;
+          if (!in) break;
+          t += delta;
+        }
+        ends[q] = t;
+        evals += min(n + 1, kStepOutCap);
+        exps += n;
+        if (n == kStepOutCap) ++capo;
+      }
+    }
+    float tl = ends[0], tr = ends[1];
     // Shrinkage, at most kShrinkCap proposals, then a null move.  Proposal r
     // is t_r = tl_r + u_r (tr_r - tl_r) and a rejection moves the end on
     // t_r's side to t_r, so the brackets of the proposals that follow
@@ -289,7 +330,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
 }
 
 // resident blocks per SM the register budget is tuned for
-constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 5 : dpl == 4 ? 4 : dpl == 8 ? 4 : 3; }
+constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 20 : dpl == 4 ? 18 : dpl == 8 ? 16 : 12; }
 
 template <int G, int DPL, int KC>
 __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(Dev D, const WorkItem* __restrict__ items, int n_items,

@@ -157,7 +157,7 @@ struct StepWords {
 };
 
 // threads per block of the grouped sweep kernels
-constexpr int kSweepThreads = 128;
+constexpr int kSweepThreads = 32;   // one warp per block: resident warps per SM set by registers alone
 
 // ---- configuration table ----------------------------------------------------
 // grouped configurations (id, G lanes per chain, DPL dimensions per lane)

@@ -69,15 +69,26 @@ struct nss_ctx {
   // holds the chains of configuration q whose runs have mixture bound kKC[b]
   static constexpr int kKC[3] = {1, 4, 8};
   static constexpr int kLists = nss::kNumCfgs * 3;
-  std::vector<WorkItem> init_items[nss::kNumCfgs], sweep_items[kLists];
+  // run groups: contiguous ranges of runs, each iterated on a stream of its
+  // own, so the latency-bound sweep of one group overlaps the direction
+  // draws and prologue of another.  Group g holds runs [g_r0[g], g_r0[g+1]);
+  // its sweep lists are g * kLists + list, its direction lists
+  // g * kDirClasses + class.
+  static constexpr int kMaxGroups = 2;
+  int n_groups = 1;
+  int g_r0[kMaxGroups + 1] = {};
+  cudaStream_t gstream[kMaxGroups] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kMaxGroups] = {};
+  cudaStream_t cur = nullptr;  // stream of the launches being enqueued
+  std::vector<WorkItem> init_items[nss::kNumCfgs], sweep_items[kMaxGroups * kLists];
   WorkItem* d_init[nss::kNumCfgs] = {};
-  WorkItem* d_sweep[kLists] = {};
+  WorkItem* d_sweep[kMaxGroups * kLists] = {};
   int* d_queue = nullptr;
-  int sweep_grid[kLists] = {};
+  int sweep_grid[kMaxGroups * kLists] = {};
   // direction generation: items of up to 32 chains, per dimension class 8..128
   static constexpr int kDirClasses = 5;
-  std::vector<WorkItem> dir_items[kDirClasses];
-  WorkItem* d_dir[kDirClasses] = {};
+  std::vector<WorkItem> dir_items[kMaxGroups * kDirClasses];
+  WorkItem* d_dir[kMaxGroups * kDirClasses] = {};
   size_t prologue_smem = 0, final_smem = 0;
   // volume simulation scratch
   int R = 100;
@@ -298,8 +309,13 @@ void free_ctx(nss_ctx* c) {
   cudaFree(c->ipool);
   cudaFree(c->dpool);
   for (int q = 0; q < nss::kNumCfgs; ++q) cudaFree(c->d_init[q]);
-  for (int q = 0; q < nss_ctx::kLists; ++q) cudaFree(c->d_sweep[q]);
-  for (int q = 0; q < nss_ctx::kDirClasses; ++q) cudaFree(c->d_dir[q]);
+  for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kLists; ++q) cudaFree(c->d_sweep[q]);
+  for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kDirClasses; ++q) cudaFree(c->d_dir[q]);
+  for (int g = 0; g < nss_ctx::kMaxGroups; ++g) {
+    if (c->gstream[g]) cudaStreamDestroy(c->gstream[g]);
+    if (c->join_ev[g]) cudaEventDestroy(c->join_ev[g]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   cudaFree(c->d_queue);
   cudaFree(c->d_vol);
   cudaFree(c->d_tiles);
@@ -353,13 +369,13 @@ struct Rec {
     c->prof.launches[kind]++;
     if (c->profiling) {
       a = take_event(c);
-      cudaEventRecord(a, c->stream);
+      cudaEventRecord(a, c->cur);
     }
   }
   ~Rec() {
     if (a) {
       cudaEvent_t b = take_event(c);
-      cudaEventRecord(b, c->stream);
+      cudaEventRecord(b, c->cur);
       c->pending.push_back({a, b, kind, cfg});
     }
   }
@@ -387,50 +403,88 @@ nss_status sync_state(nss_ctx* c) {
   return NSS_OK;
 }
 
-nss_status enqueue_iteration(nss_ctx* c) {
+// One outer iteration of the runs of group g, enqueued on c->cur.
+nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
   nss::Dev D = dev_of(c);
+  const int r0 = c->g_r0[g], nr = c->g_r0[g + 1] - r0;
+  cudaStream_t st = c->cur;
   {
     Rec r(c, NSS_K_PROLOGUE);
-    CK(nss::launch_prologue(D, c->n_runs, c->prologue_smem, c->stream), "prologue launch");
+    CK(nss::launch_prologue(D, r0, nr, c->prologue_smem, st), "prologue launch");
   }
   for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
-    if (c->dir_items[q].empty()) continue;
+    const int L = g * nss_ctx::kDirClasses + q;
+    if (c->dir_items[L].empty()) continue;
     Rec rd(c, NSS_K_OTHER);
-    CK(nss::launch_dirgen(8 << q, D, c->d_dir[q], (int)c->dir_items[q].size(), c->max_p, c->stream),
+    CK(nss::launch_dirgen(8 << q, D, c->d_dir[L], (int)c->dir_items[L].size(), c->max_p, st),
        "direction launch");
   }
   for (int q = 0; q < nss_ctx::kLists; ++q) {
-    if (c->sweep_items[q].empty()) continue;
-    CK(cudaMemsetAsync(c->d_queue + q, 0, sizeof(int), c->stream), "queue reset");
+    const int L = g * nss_ctx::kLists + q;
+    if (c->sweep_items[L].empty()) continue;
+    CK(cudaMemsetAsync(c->d_queue + L, 0, sizeof(int), st), "queue reset");
     Rec r(c, NSS_K_SWEEP, q / 3);
-    CK(nss::launch_sweep(q / 3, nss_ctx::kKC[q % 3], D, c->d_sweep[q], (int)c->sweep_items[q].size(),
-                         c->d_queue + q, c->sweep_grid[q], c->stream), "sweep launch");
+    CK(nss::launch_sweep(q / 3, nss_ctx::kKC[q % 3], D, c->d_sweep[L], (int)c->sweep_items[L].size(),
+                         c->d_queue + L, c->sweep_grid[L], st), "sweep launch");
   }
-  for (auto& g : c->gp) {
-    const RunDesc& R = c->desc[g.run];
-    Rec r(c, NSS_K_SWEEP);
-    CK(nss::launch_gp_sweep(D, g.args, g.run, R.k, R.n_data, c->stream), "GP sweep launch");
-  }
-  for (auto& w : c->lr) {
-    const RunDesc& R = c->desc[w.run];
-    const int* done = &c->d_state[w.run].done;
-    Rec r(c, NSS_K_OTHER);
-    CK(nss::launch_lr_center(D, w.args, w.run, R.n_data, c->stream), "logistic centre launch");
-    CK(nss::launch_lr_parents(D, w.args, w.run, R.k, c->stream), "logistic parents launch");
-    CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.k, w.err, done,
-                          w.zref, c->stream), "logits launch");
-    for (int s = 0; s < R.p; ++s) {
-      CK(nss::launch_lr_dir(D, w.args, w.run, R.k, s, c->stream), "logistic direction launch");
-      CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zv, w.rows_pad, R.n_data, R.k, w.err, done,
-                            nullptr, c->stream), "logits launch");
-      CK(nss::launch_lr_slice(D, w.args, w.run, R.k, s, w.emax, c->stream), "logistic slice launch");
+  if (g == 0) {  // logistic and GP runs keep one group
+    for (auto& gw : c->gp) {
+      const RunDesc& R = c->desc[gw.run];
+      Rec r(c, NSS_K_SWEEP);
+      CK(nss::launch_gp_sweep(D, gw.args, gw.run, R.k, R.n_data, st), "GP sweep launch");
     }
-    CK(nss::launch_lr_replace(D, w.args, w.run, R.k, c->stream), "logistic replace launch");
-    c->launches += 5 + 3LL * R.p;
+    for (auto& w : c->lr) {
+      const RunDesc& R = c->desc[w.run];
+      const int* done = &c->d_state[w.run].done;
+      Rec r(c, NSS_K_OTHER);
+      CK(nss::launch_lr_center(D, w.args, w.run, R.n_data, st), "logistic centre launch");
+      CK(nss::launch_lr_parents(D, w.args, w.run, R.k, st), "logistic parents launch");
+      CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.k, w.err, done,
+                            w.zref, st), "logits launch");
+      for (int s = 0; s < R.p; ++s) {
+        CK(nss::launch_lr_dir(D, w.args, w.run, R.k, s, st), "logistic direction launch");
+        CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zv, w.rows_pad, R.n_data, R.k, w.err, done,
+                              nullptr, st), "logits launch");
+        CK(nss::launch_lr_slice(D, w.args, w.run, R.k, s, w.emax, st), "logistic slice launch");
+      }
+      CK(nss::launch_lr_replace(D, w.args, w.run, R.k, st), "logistic replace launch");
+      c->launches += 5 + 3LL * R.p;
+    }
   }
   {
     Rec r(c, NSS_K_TERMINATE);
-    CK(nss::launch_terminate(D, c->n_runs, c->stream), "terminate launch");
+    CK(nss::launch_terminate(D, r0, nr, st), "terminate launch");
+  }
+  return NSS_OK;
+}
+
+// n outer iterations of every group.  With one group they go on c->stream;
+// with several, each group's iterations go on its own stream between a fork
+// and a join on c->stream, so the groups run ahead of one another freely.
+nss_status enqueue_iterations(nss_ctx* c, int n) {
+  if (c->n_groups == 1) {
+    c->cur = c->stream;
+    for (int i = 0; i < n; ++i) {
+      nss_status st = enqueue_iteration(c, 0);
+      if (st != NSS_OK) return st;
+    }
+    return NSS_OK;
+  }
+  CK(cudaEventRecord(c->fork_ev, c->stream), "fork");
+  for (int g = 0; g < c->n_groups; ++g) CK(cudaStreamWaitEvent(c->gstream[g], c->fork_ev, 0), "fork");
+  for (int i = 0; i < n; ++i)
+    for (int g = 0; g < c->n_groups; ++g) {
+      c->cur = c->gstream[g];
+      nss_status st = enqueue_iteration(c, g);
+      if (st != NSS_OK) {
+        c->cur = c->stream;
+        return st;
+      }
+    }
+  c->cur = c->stream;
+  for (int g = 0; g < c->n_groups; ++g) {
+    CK(cudaEventRecord(c->join_ev[g], c->gstream[g]), "join");
+    CK(cudaStreamWaitEvent(c->stream, c->join_ev[g], 0), "join");
   }
   return NSS_OK;
 }
@@ -438,12 +492,17 @@ nss_status enqueue_iteration(nss_ctx* c) {
 // One outer iteration: replayed from a captured CUDA graph when the context
 // has logistic runs (hundreds of launches per iteration) and profiling is
 // off; enqueued launch by launch otherwise.
-nss_status run_iteration(nss_ctx* c) {
-  if (c->lr.empty() || c->profiling) return enqueue_iteration(c);
+nss_status run_iteration(nss_ctx* c, int n = 1) {
+  if (c->lr.empty() || c->profiling) return enqueue_iterations(c, n);
+  c->cur = c->stream;
+  for (int i = 1; i < n; ++i) {
+    nss_status st = run_iteration(c, 1);
+    if (st != NSS_OK) return st;
+  }
   if (!c->iter_graph) {
     const long long l0 = c->launches, t0 = c->prof.total_launches;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
-    nss_status st = enqueue_iteration(c);
+    nss_status st = enqueue_iteration(c, 0);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (st != NSS_OK) return st;
@@ -473,12 +532,12 @@ nss_status build_work(nss_ctx* c) {
     cudaFree(c->d_init[q]);
     c->d_init[q] = nullptr;
   }
-  for (int q = 0; q < nss_ctx::kLists; ++q) {
+  for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kLists; ++q) {
     c->sweep_items[q].clear();
     cudaFree(c->d_sweep[q]);
     c->d_sweep[q] = nullptr;
   }
-  for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
+  for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kDirClasses; ++q) {
     c->dir_items[q].clear();
     cudaFree(c->d_dir[q]);
     c->d_dir[q] = nullptr;
@@ -491,14 +550,17 @@ nss_status build_work(nss_ctx* c) {
     const int iper = 32 / nss::cfg_g(icfg);
     for (int s = 0; s < R.m; s += iper) c->init_items[icfg].push_back({r, s, std::min(s + iper, R.m), 0});
     if (R.lik_kind == nss::kLikLogreg || R.lik_kind == nss::kLikGp) continue;  // own sweep kernels
+    int g = 0;
+    while (r >= c->g_r0[g + 1]) ++g;
     const int kc = nss::sweep_kc(R.lik_kind, R.n_comp);
-    const int list = R.cfg * 3 + (kc == 1 ? 0 : kc == 4 ? 1 : 2);
+    const int list = g * nss_ctx::kLists + R.cfg * 3 + (kc == 1 ? 0 : kc == 4 ? 1 : 2);
     for (int j = 0; j < R.k; j += per) c->sweep_items[list].push_back({r, j, std::min(j + per, R.k), 0});
     int dq = 0;
     while ((8 << dq) < nss::dirgen_class(R.d)) ++dq;
-    for (int j = 0; j < R.k; j += 32) c->dir_items[dq].push_back({r, j, std::min(j + 32, R.k), 0});
+    for (int j = 0; j < R.k; j += 32)
+      c->dir_items[g * nss_ctx::kDirClasses + dq].push_back({r, j, std::min(j + 32, R.k), 0});
   }
-  for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
+  for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kDirClasses; ++q) {
     if (c->dir_items[q].empty()) continue;
     CK(cudaMalloc(&c->d_dir[q], sizeof(WorkItem) * c->dir_items[q].size()), "work list allocation");
     CK(cudaMemcpyAsync(c->d_dir[q], c->dir_items[q].data(), sizeof(WorkItem) * c->dir_items[q].size(),
@@ -511,7 +573,7 @@ nss_status build_work(nss_ctx* c) {
                          cudaMemcpyHostToDevice, c->stream), "work list upload");
     }
   }
-  for (int q = 0; q < nss_ctx::kLists; ++q) {
+  for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kLists; ++q) {
     auto cost = [&](const WorkItem& w) { return (double)c->desc[w.run].p * c->desc[w.run].d; };
     std::stable_sort(c->sweep_items[q].begin(), c->sweep_items[q].end(),
                      [&](const WorkItem& a, const WorkItem& b) { return cost(a) > cost(b); });
@@ -519,8 +581,9 @@ nss_status build_work(nss_ctx* c) {
       CK(cudaMalloc(&c->d_sweep[q], sizeof(WorkItem) * c->sweep_items[q].size()), "work list allocation");
       CK(cudaMemcpyAsync(c->d_sweep[q], c->sweep_items[q].data(), sizeof(WorkItem) * c->sweep_items[q].size(),
                          cudaMemcpyHostToDevice, c->stream), "work list upload");
-      const int per_sm = nss::sweep_blocks_per_sm(q / 3, nss_ctx::kKC[q % 3]);
-      const int wpb = nss::sweep_warps_per_block(q / 3);
+      const int ql = q % nss_ctx::kLists;
+      const int per_sm = nss::sweep_blocks_per_sm(ql / 3, nss_ctx::kKC[ql % 3]);
+      const int wpb = nss::sweep_warps_per_block(ql / 3);
       const int warps_needed = (int)c->sweep_items[q].size();
       const int blocks_needed = (warps_needed + wpb - 1) / wpb;
       c->sweep_grid[q] = std::max(1, std::min(blocks_needed, per_sm * c->num_sms));
@@ -883,6 +946,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     }
     c->own_stream = true;
   }
+  c->cur = c->stream;
 
   // ---- layout -------------------------------------------------------------
   c->desc.resize(n_runs);
@@ -996,7 +1060,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   CKC(cudaMalloc(&c->fpool, sizeof(float) * std::max(c->nf, 16LL)), "FP32 pool allocation");
   CKC(cudaMalloc(&c->ipool, sizeof(int) * std::max(c->ni, 16LL)), "INT32 pool allocation");
   CKC(cudaMalloc(&c->dpool, sizeof(double) * std::max(c->nd, 16LL)), "FP64 pool allocation");
-  CKC(cudaMalloc(&c->d_queue, sizeof(int) * nss_ctx::kLists), "queue allocation");
+  CKC(cudaMalloc(&c->d_queue, sizeof(int) * nss_ctx::kMaxGroups * nss_ctx::kLists), "queue allocation");
   CKC(cudaMalloc(&c->d_vbase, sizeof(int) * n_runs), "vbase allocation");
   CKC(cudaMemsetAsync(c->fpool, 0, sizeof(float) * std::max(c->nf, 16LL), c->stream), "pool clear");
   CKC(cudaMemsetAsync(c->ipool, 0, sizeof(int) * std::max(c->ni, 16LL), c->stream), "pool clear");
@@ -1046,6 +1110,36 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   clear_states(c);
   CKC(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(RunState) * n_runs, cudaMemcpyHostToDevice, c->stream),
       "state upload");
+  // run groups: two streams when every run uses the generic sweep, split
+  // into contiguous halves of about equal sweep cost
+  {
+    bool generic = n_runs >= 2;
+    double total = 0.0;
+    for (int r = 0; r < n_runs; ++r) {
+      const RunDesc& R = c->desc[r];
+      if (R.lik_kind == nss::kLikLogreg || R.lik_kind == nss::kLikGp) generic = false;
+      total += (double)R.k * R.p * R.d;
+    }
+    c->g_r0[0] = 0;
+    c->n_groups = 1;
+    if (generic) {
+      double acc = 0.0;
+      int cut = 1;
+      for (int r = 0; r < n_runs - 1; ++r) {
+        acc += (double)c->desc[r].k * c->desc[r].p * c->desc[r].d;
+        cut = r + 1;
+        if (acc >= 0.5 * total) break;
+      }
+      c->g_r0[1] = cut;
+      c->n_groups = 2;
+      CKC(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming), "event creation");
+      for (int g = 0; g < 2; ++g) {
+        CKC(cudaStreamCreateWithFlags(&c->gstream[g], cudaStreamNonBlocking), "stream creation");
+        CKC(cudaEventCreateWithFlags(&c->join_ev[g], cudaEventDisableTiming), "event creation");
+      }
+    }
+    c->g_r0[c->n_groups] = n_runs;
+  }
   {
     nss_status sw = build_work(c);
     if (sw != NSS_OK) {
@@ -1119,8 +1213,7 @@ nss_status nss_run(nss_ctx* c, nss_result* res) {
   if (st != NSS_OK) return st;
   int chunk = 4;
   while (!all_done(c)) {
-    for (int i = 0; i < chunk; ++i)
-      if ((st = run_iteration(c)) != NSS_OK) return st;
+    if ((st = run_iteration(c, chunk)) != NSS_OK) return st;
     if ((st = sync_state(c)) != NSS_OK) return st;
     chunk = std::min(chunk * 2, 16);
   }
@@ -1210,8 +1303,7 @@ nss_status nss_autotune(nss_ctx* c, int iters, int* cfg_out) {
       if ((st = nss_reset(c, nullptr)) != NSS_OK) return st;
       if ((st = sync_state(c)) != NSS_OK) return st;
       c->cfg_ms[q] = 0.0;
-      for (int i = 0; i < iters; ++i)
-        if ((st = enqueue_iteration(c)) != NSS_OK) return st;
+      if ((st = enqueue_iterations(c, iters)) != NSS_OK) return st;
       if ((st = sync_state(c)) != NSS_OK) return st;
       double ev = 0.0;
       for (int r : runs) ev += (double)c->h_state[r].evals;

@@ -219,8 +219,8 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
 // ---------------------------------------------------------------------------
 // Iteration prologue: steps (i), (ii), evidence and metric for one run.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_prologue(Dev D) {
-  const int run = blockIdx.x;
+__global__ void __launch_bounds__(1024) k_prologue(Dev D, int run0) {
+  const int run = run0 + blockIdx.x;
   const RunDesc& R = D.desc[run];
   RunState& S = D.st[run];
   if (S.done) return;
@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(1024) k_prologue(Dev D) {
 // Termination (App. B.3, reading: live fraction): Z_live = X mean(L_live);
 // stop when Z_live / (Z + Z_live) < tol.  Also counts the iteration.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_terminate(Dev D) {
-  const int run = blockIdx.x;
+__global__ void __launch_bounds__(256) k_terminate(Dev D, int run0) {
+  const int run = run0 + blockIdx.x;
   const RunDesc& R = D.desc[run];
   RunState& S = D.st[run];
   if (S.done) return;
@@ -512,13 +512,13 @@ cudaError_t setup_kernel_attributes() {
   return cudaFuncSetAttribute(k_final_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t launch_prologue(const Dev& D, int n_runs, size_t smem, cudaStream_t s) {
-  k_prologue<<<n_runs, 1024, smem, s>>>(D);
+cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s) {
+  k_prologue<<<n_runs, 1024, smem, s>>>(D, run0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_terminate(const Dev& D, int n_runs, cudaStream_t s) {
-  k_terminate<<<n_runs, 256, 0, s>>>(D);
+cudaError_t launch_terminate(const Dev& D, int run0, int n_runs, cudaStream_t s) {
+  k_terminate<<<n_runs, 256, 0, s>>>(D, run0);
   return cudaGetLastError();
 }
 

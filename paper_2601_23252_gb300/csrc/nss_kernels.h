@@ -57,12 +57,13 @@ cudaError_t launch_lr_slice(const Dev& D, const LRArgs& A, int run, int k, int s
 cudaError_t launch_lr_replace(const Dev& D, const LRArgs& A, int run, int k, cudaStream_t s);
 
 cudaError_t launch_init(int cfg, const Dev& D, const WorkItem* items, int n, cudaStream_t s);
-cudaError_t launch_prologue(const Dev& D, int n_runs, size_t smem, cudaStream_t s);
+// runs [run0, run0 + n_runs)
+cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s);
 // the sweep of configuration cfg for runs of mixture bound kc = sweep_kc(.)
 cudaError_t launch_sweep(int cfg, int kc, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
                          cudaStream_t s);
 int sweep_kc(int lik_kind, int n_comp);
-cudaError_t launch_terminate(const Dev& D, int n_runs, cudaStream_t s);
+cudaError_t launch_terminate(const Dev& D, int run0, int n_runs, cudaStream_t s);
 cudaError_t launch_final_sort(const Dev& D, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_volsim(const Dev& D, const VolLaunch& V, int n_runs, cudaStream_t s);
 int sweep_blocks_per_sm(int cfg, int kc);

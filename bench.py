@@ -249,7 +249,7 @@ def run_native(args):
     torch.cuda.synchronize()
     sampler.set_profiling(True)
     clocks = Clocks(local)
-    times, dead, evals, flops, launches = [], 0, 0, 0.0, 0
+    times, dead, evals, flops, launches, spec = [], 0, 0, 0.0, 0, 0
     barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -268,6 +268,7 @@ def run_native(args):
         for wl, r in zip(wls, res):
             dead += r["n_dead"]
             evals += r["evals"]
+            spec += r["spec_evals"]
             flops += sweep_flops(wl, r["evals"], r["iters"] * wl.k * wl.p)
     torch.cuda.synchronize()
     barrier()
@@ -300,7 +301,7 @@ def run_native(args):
                 "peak_source": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x "
                                f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src} max clock)",
                 "avg_launch_ms": sweep_ms / sweep_launches,
-                "share_of_step": sweep_ms / total_ms if total_ms > 0 else None}
+                "launch_ms_over_step_ms": sweep_ms / total_ms if total_ms > 0 else None}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
@@ -311,6 +312,7 @@ def run_native(args):
                        "sweep_cfg": chosen[0], "autotune_ms_per_Meval": tune,
                        "evidence_accumulation": "f64"},
             "evals_per_s": evals_all / (total_ms_all / 1e3),
+            "speculative_tests_per_eval": spec / max(1, evals),
             "gate": logz_gate(seeds, res, dlogZ, errs),
             "roofline": roofline, "gpu_launches": prof["total_launches"] // 1,
             "clocks": clk,

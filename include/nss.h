@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NSS_ABI_VERSION 1
+#define NSS_ABI_VERSION 2
 
 typedef struct nss_ctx nss_ctx;
 
@@ -156,6 +156,9 @@ typedef struct {
     long long nulls;           /* HRSS steps that hit the shrinkage cap          */
     long long cap_out;         /* stepping-out sides stopped by the cap          */
     long long nan_evals;       /* evaluations whose likelihood was NaN           */
+    long long spec_evals;      /* slice tests run beyond the logical evaluations
+                                  (a chain group tests several stepping-out ends
+                                  or shrinkage proposals at once)               */
     int metric_status;         /* 0 ok, 1 identity fallback, 2 jitter retried    */
     int status;                /* nss_status of the run                          */
 } nss_step_info;
@@ -173,6 +176,7 @@ typedef struct {
     long long nulls;
     long long cap_out;
     long long nan_evals;
+    long long spec_evals;      /* as in nss_step_info                            */
     int status;
 } nss_result;
 

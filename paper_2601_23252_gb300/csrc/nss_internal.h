@@ -52,6 +52,7 @@ struct RunDesc {
 struct RunState {
   double logZ, logX;
   long long n_dead, evals, nulls, cap_out, nan_evals;
+  long long spec_evals;             // slice tests run beyond the logical ones (group-parallel rounds)
   int iter, done, status, metric_status;
   float logLstar;
   int stepped;                      // at least one iteration since create/import

@@ -55,6 +55,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   const float w = R.w;
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
   int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
+  int ran = 0;  // slice tests this lane ran (logical or speculative)
   // the steps' directions, drawn ahead (nss_dirgen.cu); the load of step
   // s + 1's is issued while step s runs
   const float* vrow = f + R.o_V + (long long)j * R.p * ld;
@@ -151,6 +152,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     // logL > logL* (Sec. 3.1: E < E_batch).  A NaN likelihood reads as -inf
     // and is flagged; nothing is counted here.
     auto probe = [&](float t, float& ll, bool& isn) -> bool {
+      ++ran;
       if (box && !(t >= t_lo && t <= t_hi)) return false;
       if (nonflat) {
         const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
@@ -309,6 +311,14 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     if (ok) ++acc;
     else ++nul;
   }
+  // group-parallel rounds test ends and proposals past the first decisive
+  // one; those extra tests are counted apart from the logical evaluations
+  {
+    int tot = ran;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) tot += __shfl_xor_sync(mask, tot, o, G);
+    ran = tot;
+  }
   // (iv) replace dead slot j, born at logL*
   const int slot = D.i[R.o_dead + j];
   if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, ld, x);
@@ -326,6 +336,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     if (nul) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nulls), (unsigned long long)nul);
     if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->cap_out), (unsigned long long)capo);
     if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nan_evals), (unsigned long long)nanc);
+    if (ran > evals) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->spec_evals), (unsigned long long)(ran - evals));
   }
 }
 

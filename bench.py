@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--runs", type=int, default=20, help="independent seeds per batch (per rank)")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-run-at-a-time comparator")
+    ap.add_argument("--sweep-cfg", type=int, default=-1,
+                    help="force this sweep configuration id instead of autotuning (profiling runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU checker baseline")
     ap.add_argument("--ncu-case", action="store_true",
                     help="no timing: the bench batch for a few iterations, small dead stores "
@@ -239,8 +241,10 @@ def run_native(args):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
+    if args.sweep_cfg >= 0:
+        wls = [w.with_(extra={"options": {"sweep_cfg": args.sweep_cfg}}) for w in wls]
     sampler = native.Sampler(wls, stream=stream.cuda_stream)
-    chosen = sampler.autotune(iters=3)
+    chosen = sampler.autotune(iters=3) if args.sweep_cfg < 0 else [sampler.cfg(r) for r in range(nrun)]
     tune = {f"{native.Sampler.cfg_info(q)['lanes_per_chain']}x{native.Sampler.cfg_info(q)['dims_per_lane']}": round(v, 4)
             for q, v in sampler.autotune_report().items()}
     for _ in range(args.warmup):

@@ -1039,7 +1039,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     // covariance reductions and the two d x d matrices
     const size_t sortb = (size_t)R.m2 * 8 + (size_t)R.m2 * 4 + (size_t)R.m * 4;
     const int nt = R.dpad / 4, ntp = nt * (nt + 1) / 2, parts2 = std::max(1, 1024 / ntp);
-    const size_t covb = sizeof(float) * ((size_t)parts2 * ntp * 16 + 2 * (size_t)R.dpad * R.dpad);
+    const size_t covb = sizeof(float) * ((size_t)parts2 * ntp * 16 + (size_t)R.dpad * (2 * R.dpad + 1));
     const size_t meanb = sizeof(float) * 1024;
     c->prologue_smem = std::max(c->prologue_smem, std::max(sortb, std::max(covb, meanb)));
     c->final_smem = std::max(c->final_smem, (size_t)R.m2 * 8);

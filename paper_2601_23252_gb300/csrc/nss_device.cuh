@@ -185,6 +185,36 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long* keys, int n) {
   __syncthreads();
 }
 
+// Bitonic sort of n (power of two, n <= blockDim.x, blockDim.x a multiple of
+// 32) keys in shared memory, one key per thread in a register: stages whose
+// partner lies in the same warp (stride < 32) exchange by shuffles, the
+// others through shared memory.  Threads i >= n sort a block of padding keys
+// of their own.  Same result as bitonic_sort.
+__device__ __forceinline__ void bitonic_sort_reg(unsigned long long* keys, int n) {
+  const int i = threadIdx.x;
+  unsigned long long a = (i < n) ? keys[i] : ~0ull;
+  for (int size = 2; size <= n; size <<= 1) {
+    const bool up = (i & size) == 0;
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      unsigned long long b;
+      if (stride >= 32) {
+        __syncthreads();
+        if (i < n) keys[i] = a;
+        __syncthreads();
+        b = (i < n) ? keys[i ^ stride] : a;
+      } else {
+        b = __shfl_xor_sync(0xffffffffu, a, stride);
+      }
+      const bool lower = (i & stride) == 0;
+      const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+      a = (lower == up) ? lo : hi;
+    }
+  }
+  __syncthreads();
+  if (i < n) keys[i] = a;
+  __syncthreads();
+}
+
 __device__ __forceinline__ double logaddexp_d(double a, double b) {
   if (a == -INFINITY) return b;
   if (b == -INFINITY) return a;

@@ -8,8 +8,8 @@
 //   d~ = L z (L lower triangular), v = d~ / |z| (unit Mahalanobis length)
 //   or d~ / |d~| (unit Euclidean length),
 // and writes v to V[chain][step][0, dpad).  The 32 threads of a warp are 32
-// chains of one run at one step, so every load of L is a warp-uniform
-// broadcast.  Rows of d~ are formed from the last to the first so that d~_r
+// chains of one run at one step, so every read of L (staged in shared memory
+// per block) is a broadcast.  Rows of d~ are formed from the last to the first so that d~_r
 // can overwrite z_r (row r reads z_c for c <= r only): z and d~ share one
 // array, in registers for d <= 32 and in shared memory above.
 #include <cmath>
@@ -21,26 +21,15 @@ namespace nss {
 namespace {
 
 constexpr int kDirThreads = 128;
+constexpr int kDirStepsPerBlock = 16;  // steps of one item per block, 4 per warp
 
 template <int DMAX>
-__global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* __restrict__ items, int n_items) {
+__device__ __forceinline__ void one_direction(const RunDesc& R, const float* __restrict__ Ls, float* zsh,
+                                              uint32_t iter, int j, int s, float* __restrict__ vout) {
   constexpr bool kShared = DMAX > 32;
   constexpr int kReg = kShared ? 1 : DMAX;
-  extern __shared__ float zsh[];  // kShared: [kDirThreads][DMAX + 1], odd stride: no bank conflicts
-  const int lane = threadIdx.x & 31;
-  const int it = blockIdx.x * (kDirThreads / 32) + (threadIdx.x >> 5);
-  if (it >= n_items) return;
-  const WorkItem wi = items[it];
-  const RunDesc& R = D.desc[wi.run];
-  const RunState& S = D.st[wi.run];
-  const int s = blockIdx.y;
-  if (S.done || s >= R.p) return;
-  const int j = wi.c0 + lane;
-  if (j >= wi.c1) return;
   const int d = R.d, ld = R.dpad;
-  const uint32_t iter = (uint32_t)S.iter;
-  const float* __restrict__ Lf = D.f + R.o_L;
-  float4* out = reinterpret_cast<float4*>(D.f + R.o_V + ((long long)j * R.p + s) * ld);
+  float4* out = reinterpret_cast<float4*>(vout + ((long long)j * R.p + s) * ld);
   float zz = 0.0f, dd = 0.0f;
   if constexpr (!kShared) {
     float z[kReg];
@@ -59,7 +48,7 @@ __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* _
       if (i >= d) z[i] = 0.0f;
       zz = fmaf(z[i], z[i], zz);
     }
-    const float4* L4 = reinterpret_cast<const float4*>(Lf);
+    const float4* L4 = reinterpret_cast<const float4*>(Ls);
     const int ld4 = ld >> 2;
 #pragma unroll
     for (int r = kReg - 1; r >= 0; --r) {
@@ -68,11 +57,11 @@ __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* _
         float acc = 0.0f;
 #pragma unroll
         for (int b = 0; b < r / 4; ++b) {
-          const float4 l = __ldg(row + b);
+          const float4 l = row[b];
           acc = fmaf(l.x, z[4 * b], fmaf(l.y, z[4 * b + 1], fmaf(l.z, z[4 * b + 2], fmaf(l.w, z[4 * b + 3], acc))));
         }
         // the diagonal block: columns 4(r/4) .. r only (later ones already hold d~)
-        const float4 l = __ldg(row + r / 4);
+        const float4 l = row[r / 4];
         const int b = r / 4, e = r % 4;
         float t = 0.0f;
         if (e >= 3) t = fmaf(l.w, z[4 * b + 3], t);
@@ -89,7 +78,7 @@ __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* _
     for (int b = 0; b < kReg / 4; ++b)
       if (4 * b < ld) out[b] = make_float4(z[4 * b] * inrm, z[4 * b + 1] * inrm, z[4 * b + 2] * inrm, z[4 * b + 3] * inrm);
   } else {
-    float* z = zsh + threadIdx.x * (DMAX + 1);
+    float* z = zsh;
     for (int q = 0; 4 * q < ld; ++q) {
       float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
       if (4 * q < d) {
@@ -97,25 +86,25 @@ __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* _
         box_muller(w.x, w.y, a0, a1);
         box_muller(w.z, w.w, a2, a3);
       }
-      const float t[4] = {a0, a1, a2, a3};
+      const float t4[4] = {a0, a1, a2, a3};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float zi = (4 * q + e < d) ? t[e] : 0.0f;
+        const float zi = (4 * q + e < d) ? t4[e] : 0.0f;
         z[4 * q + e] = zi;
         zz = fmaf(zi, zi, zz);
       }
     }
     for (int r = d - 1; r >= 0; --r) {
-      const float4* row = reinterpret_cast<const float4*>(Lf + (long long)r * ld);
+      const float4* row = reinterpret_cast<const float4*>(Ls + r * ld);
       float acc = 0.0f;
       const int nb = r / 4;
       for (int b = 0; b < nb; ++b) {
-        const float4 l = __ldg(row + b);
+        const float4 l = row[b];
         acc = fmaf(l.x, z[4 * b], fmaf(l.y, z[4 * b + 1], fmaf(l.z, z[4 * b + 2], fmaf(l.w, z[4 * b + 3], acc))));
       }
-      const float* lr = Lf + (long long)r * ld;
+      const float* lr = Ls + r * ld;
       float t = 0.0f;
-      for (int c = r; c >= 4 * nb; --c) t = fmaf(__ldg(lr + c), z[c], t);
+      for (int c = r; c >= 4 * nb; --c) t = fmaf(lr[c], z[c], t);
       z[r] = acc + t;
       dd = fmaf(z[r], z[r], dd);
     }
@@ -125,9 +114,37 @@ __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* _
   }
 }
 
+// block (item, step chunk): the run's factor L is staged in shared memory
+// once; warp w makes the directions of steps chunk*16 + w, +4, ... for the
+// item's 32 chains (one per lane)
+template <int DMAX>
+__global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* __restrict__ items, int n_items) {
+  constexpr bool kShared = DMAX > 32;
+  extern __shared__ __align__(16) float dsm[];  // L [ld][ld], then (kShared) z [kDirThreads][DMAX + 1]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int it = blockIdx.x;
+  if (it >= n_items) return;
+  const WorkItem wi = items[it];
+  const RunDesc& R = D.desc[wi.run];
+  const RunState& S = D.st[wi.run];
+  const int s0 = blockIdx.y * kDirStepsPerBlock;
+  if (S.done || s0 >= R.p) return;
+  const int ld = R.dpad;
+  const float4* Lg = reinterpret_cast<const float4*>(D.f + R.o_L);
+  float4* L4 = reinterpret_cast<float4*>(dsm);
+  for (int t = threadIdx.x; t < (ld * ld) >> 2; t += kDirThreads) L4[t] = Lg[t];
+  __syncthreads();
+  const int j = wi.c0 + lane;
+  if (j >= wi.c1) return;
+  const uint32_t iter = (uint32_t)S.iter;
+  float* zsh = kShared ? dsm + ld * ld + threadIdx.x * (DMAX + 1) : nullptr;
+  const int s1 = min(R.p, s0 + kDirStepsPerBlock);
+  for (int s = s0 + wid; s < s1; s += kDirThreads / 32) one_direction<DMAX>(R, dsm, zsh, iter, j, s, D.f + R.o_V);
+}
+
 template <int DMAX>
 size_t dirgen_smem() {
-  return DMAX > 32 ? sizeof(float) * (size_t)kDirThreads * (DMAX + 1) : 0;
+  return sizeof(float) * ((size_t)DMAX * DMAX + (DMAX > 32 ? (size_t)kDirThreads * (DMAX + 1) : 0));
 }
 
 }  // namespace
@@ -141,15 +158,17 @@ int dirgen_class(int d) {
 }
 
 cudaError_t setup_dirgen_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_dirgen<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dirgen_smem<64>());
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_dirgen<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dirgen_smem<128>());
 }
 
 cudaError_t launch_dirgen(int dclass, const Dev& D, const WorkItem* items, int n, int max_p, cudaStream_t s) {
-  const dim3 grid((n + kDirThreads / 32 - 1) / (kDirThreads / 32), max_p);
+  const dim3 grid(n, (max_p + kDirStepsPerBlock - 1) / kDirStepsPerBlock);
   switch (dclass) {
-    case 8: k_dirgen<8><<<grid, kDirThreads, 0, s>>>(D, items, n); break;
-    case 16: k_dirgen<16><<<grid, kDirThreads, 0, s>>>(D, items, n); break;
-    case 32: k_dirgen<32><<<grid, kDirThreads, 0, s>>>(D, items, n); break;
+    case 8: k_dirgen<8><<<grid, kDirThreads, dirgen_smem<8>(), s>>>(D, items, n); break;
+    case 16: k_dirgen<16><<<grid, kDirThreads, dirgen_smem<16>(), s>>>(D, items, n); break;
+    case 32: k_dirgen<32><<<grid, kDirThreads, dirgen_smem<32>(), s>>>(D, items, n); break;
     case 64: k_dirgen<64><<<grid, kDirThreads, dirgen_smem<64>(), s>>>(D, items, n); break;
     case 128: k_dirgen<128><<<grid, kDirThreads, dirgen_smem<128>(), s>>>(D, items, n); break;
     default: return cudaErrorInvalidValue;

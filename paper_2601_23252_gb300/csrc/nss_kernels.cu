@@ -75,35 +75,46 @@ __device__ void append_dead(const Dev& D, const RunDesc& R, RunState& S,
   }
 }
 
-// Cholesky factor of S + reg I into Lm (both [dpad][dpad] in shared memory);
-// left-looking by columns; returns true on a non-positive pivot.
+// Cholesky factor of S + reg I ([ld][ld] in shared memory) into Lm
+// ([ld][ld + 1]: the odd row stride keeps a warp's row accesses on distinct
+// banks) by warp 0: right-looking column steps, lane l owns rows l, l + 32,
+// ...; only warp-level synchronisation inside.  Every thread of the block
+// calls it; returns true (for every thread) on a non-positive or
+// non-finite pivot.
 __device__ bool cholesky_smem(const float* S, float* Lm, int d, int ld, float reg, int* flag) {
-  for (int t = threadIdx.x; t < ld * ld; t += blockDim.x) Lm[t] = 0.0f;
-  if (threadIdx.x == 0) *flag = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = 0; j < d; ++j) {
-    if (wid == 0) {
-      float s = 0.0f;
-      for (int q = lane; q < j; q += 32) s = fmaf(Lm[j * ld + q], Lm[j * ld + q], s);
-      s = warp_sum_f(s);
-      if (lane == 0) {
-        const float v = S[j * ld + j] + reg - s;
-        if (!(v > 0.0f) || !isfinite(v)) *flag = 1;
-        Lm[j * ld + j] = sqrtf(fmaxf(v, 0.0f));
+  const int lw = ld + 1;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int t = lane; t < ld * ld; t += 32) {
+      const int a = t / ld, b = t - a * ld;
+      Lm[a * lw + b] = (b <= a && a < d) ? S[t] + (a == b ? reg : 0.0f) : 0.0f;
+    }
+    __syncwarp();
+    bool bad = false;
+    for (int j = 0; j < d; ++j) {
+      const float piv = Lm[j * lw + j];
+      if (!(piv > 0.0f) || !isfinite(piv)) {
+        bad = true;
+        break;
       }
+      const float ljj = sqrtf(piv);
+      const float inv = 1.0f / ljj;
+      __syncwarp();
+      for (int i = j + 1 + lane; i < d; i += 32) Lm[i * lw + j] *= inv;
+      if (lane == 0) Lm[j * lw + j] = ljj;
+      __syncwarp();
+      for (int i = j + 1 + lane; i < d; i += 32) {
+        const float lij = Lm[i * lw + j];
+        for (int q = j + 1; q <= i; ++q) Lm[i * lw + q] = fmaf(-lij, Lm[q * lw + j], Lm[i * lw + q]);
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    if (*flag) return true;
-    const float ljj = Lm[j * ld + j];
-    for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) {
-      float t = S[i * ld + j];
-      for (int q = 0; q < j; ++q) t = fmaf(-Lm[i * ld + q], Lm[j * ld + q], t);
-      Lm[i * ld + j] = t / ljj;
-    }
-    __syncthreads();
+    if (lane == 0) *flag = bad ? 1 : 0;
   }
-  return false;
+  __syncthreads();
+  const bool fail = *flag != 0;
+  __syncthreads();
+  return fail;
 }
 
 // Direction metric (Sec. 3.2): covariance of the m live points (divisor m-1)
@@ -141,7 +152,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
   const int parts2 = max(1, T / ntp);
   float* red = part;                             // [parts2][ntp][16]
   float* Sm = part + (size_t)parts2 * ntp * 16;  // [ld][ld]
-  float* Lm = Sm + ld * ld;                      // [ld][ld]
+  float* Lm = Sm + ld * ld;                      // [ld][ld + 1]
   for (int tpp = threadIdx.x; tpp < parts2 * ntp; tpp += T) {
     const int tp = tpp % ntp, pi = tpp / ntp;
     int ta = 0;
@@ -210,7 +221,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
   float* Lg = D.f + R.o_L;
   for (int t = threadIdx.x; t < ld * ld; t += T) {
     const int a = t / ld, b = t - a * ld;
-    Lg[t] = identity ? ((a == b && a < d) ? 1.0f : 0.0f) : Lm[t];
+    Lg[t] = identity ? ((a == b && a < d) ? 1.0f : 0.0f) : Lm[a * (ld + 1) + b];
   }
   if (threadIdx.x == 0) S.metric_status = status;
   __syncthreads();
@@ -234,7 +245,8 @@ __global__ void __launch_bounds__(1024) k_prologue(Dev D, int run0) {
   const float* logL = D.f + R.o_logL;
   for (int i = threadIdx.x; i < m2; i += blockDim.x)
     keys[i] = (i < m) ? sort_key(logL[i], i) : ~0ull;
-  bitonic_sort(keys, m2);
+  if (m2 <= (int)blockDim.x) bitonic_sort_reg(keys, m2);
+  else bitonic_sort(keys, m2);
   // (i) dead slots, worst first; threshold = the k-th worst
   int* dead = D.i + R.o_dead;
   for (int j = threadIdx.x; j < k; j += blockDim.x) dead[j] = (int)(keys[j] & 0xffffffffu);
@@ -330,7 +342,8 @@ __global__ void __launch_bounds__(1024) k_final_sort(Dev D) {
   const float* logL = D.f + R.o_logL;
   for (int i = threadIdx.x; i < R.m2; i += blockDim.x)
     keys[i] = (i < R.m) ? sort_key(logL[i], i) : ~0ull;
-  bitonic_sort(keys, R.m2);
+  if (R.m2 <= (int)blockDim.x) bitonic_sort_reg(keys, R.m2);
+  else bitonic_sort(keys, R.m2);
   if (threadIdx.x == 0) cap_fail = (S.n_dead + R.m > R.dead_cap);
   __syncthreads();
   if (cap_fail) {

@@ -98,9 +98,8 @@ __device__ bool cholesky_smem(const float* S, float* Lm, int d, int ld, float re
         break;
       }
       const float ljj = sqrtf(piv);
-      const float inv = 1.0f / ljj;
       __syncwarp();
-      for (int i = j + 1 + lane; i < d; i += 32) Lm[i * lw + j] *= inv;
+      for (int i = j + 1 + lane; i < d; i += 32) Lm[i * lw + j] /= ljj;
       if (lane == 0) Lm[j * lw + j] = ljj;
       __syncwarp();
       for (int i = j + 1 + lane; i < d; i += 32) {

@@ -74,7 +74,12 @@ def test_one_step_parity(gpu_lib, name, seed, warm):
         same &= g[c] == t[c]
     ok = same & ~tie
     xerr = np.abs(g["new_x"][ok] - t["new_x"][ok]).max() if ok.any() else 0.0
-    lrel = (np.abs(g["new_logL"][ok] - t["new_logL"][ok]) / np.maximum(1.0, np.abs(t["new_logL"][ok]))).max()
+    # logL = (log peak density) - (quadratic term): FP32 rounding, and the
+    # slope times the position differences, scale with the larger of the two
+    # terms, bounded by the best live logL of the iteration
+    top = float(np.max(rep["l32"][np.isfinite(rep["l32"])]))
+    scale = np.maximum(max(1.0, abs(top)), np.abs(t["new_logL"][ok]))
+    lrel = (np.abs(g["new_logL"][ok] - t["new_logL"][ok]) / scale).max()
     print(f"\n{name} seed={seed} warm={warm}: L rel err {lerr:.2e}, ties {tie.mean():.4f}, "
           f"mismatch {np.mean(~same):.4f}, x err {xerr:.2e}, logL rel err {lrel:.2e}, "
           f"logZ err {abs(rep['info']['logZ'] - rep['orc_logZ']):.2e}, "

@@ -116,6 +116,48 @@ __device__ bool cholesky_smem(const float* S, float* Lm, int d, int ld, float re
   return fail;
 }
 
+// d <= 32: the same factorisation with row i of S + reg I in lane i's
+// registers (warp 0); column j's pivot and entries reach the other lanes by
+// shuffles.  Same operations in the same order as cholesky_smem, so the same
+// factor; Lm as there ([ld][ld + 1]).
+__device__ bool cholesky_reg32(const float* S, float* Lm, int d, int ld, float reg, int* flag) {
+  const int lw = ld + 1;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    float a[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      a[q] = (lane < d && q <= lane) ? S[lane * ld + q] + (q == lane ? reg : 0.0f) : 0.0f;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j < d && !bad) {
+        const float piv = __shfl_sync(0xffffffffu, a[j], j);
+        bad = !(piv > 0.0f) || !isfinite(piv);
+        const float ljj = sqrtf(bad ? 1.0f : piv);
+        if (lane > j) a[j] = a[j] / ljj;
+        else if (lane == j) a[j] = ljj;
+        const float lij = a[j];
+#pragma unroll
+        for (int q = j + 1; q < 32; ++q) {
+          const float lqj = __shfl_sync(0xffffffffu, a[j], q);
+          if (lane > j && q <= lane) a[q] = fmaf(-lij, lqj, a[q]);
+        }
+      }
+    }
+    if (lane < ld) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (q < ld) Lm[lane * lw + q] = (lane < d && q <= lane) ? a[q] : 0.0f;
+    }
+    if (lane == 0) *flag = bad ? 1 : 0;
+  }
+  __syncthreads();
+  const bool fail = *flag != 0;
+  __syncthreads();
+  return fail;
+}
+
 // Direction metric (Sec. 3.2): covariance of the m live points (divisor m-1)
 // about a shifted mean, FP32 with 4x4 register tiles and a fixed-order
 // reduction; regularised by eps * tr/d and factorised; a failed factorisation
@@ -135,6 +177,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
     float s = 0.0f;
     if (pi < nparts && a < d) {
       const float ref = X[a];
+#pragma unroll 4
       for (int i = pi; i < m; i += nparts) s += X[(long long)i * ld + a] - ref;
     }
     if (pi < nparts) part[pi * ld + a] = s;
@@ -164,6 +207,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
     const float4 rb = reinterpret_cast<const float4*>(X)[tb];
     const float ma[4] = {mu_s[4 * ta], mu_s[4 * ta + 1], mu_s[4 * ta + 2], mu_s[4 * ta + 3]};
     const float mb[4] = {mu_s[4 * tb], mu_s[4 * tb + 1], mu_s[4 * tb + 2], mu_s[4 * tb + 3]};
+#pragma unroll 2
     for (int i = pi; i < m; i += parts2) {
       const float4 xa = reinterpret_cast<const float4*>(X + (long long)i * ld)[ta];
       const float4 xb = reinterpret_cast<const float4*>(X + (long long)i * ld)[tb];
@@ -206,7 +250,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
     float reg = R.cov_eps * (float)tr / (float)d;
     bool fail = true;
     for (int attempt = 0; attempt <= 6; ++attempt) {
-      fail = cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
+      fail = (d <= 32) ? cholesky_reg32(Sm, Lm, d, ld, reg, &flag_s) : cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
       __syncthreads();
       if (!fail) break;
       reg *= 10.0f;

@@ -116,46 +116,38 @@ __device__ bool cholesky_smem(const float* S, float* Lm, int d, int ld, float re
   return fail;
 }
 
-// d <= 32: the same factorisation with row i of S + reg I in lane i's
-// registers (warp 0); column j's pivot and entries reach the other lanes by
-// shuffles.  Same operations in the same order as cholesky_smem, so the same
-// factor; Lm as there ([ld][ld + 1]).
+// d <= 32 and at least 32 d threads: the same factorisation with entry
+// (i, q) in a register of thread 32 i + q (warp i holds row i).  Per column j
+// the pivot and the column's entries go through shared memory (col), the
+// rest stays in registers; the same operations in the same order as
+// cholesky_smem, so the same factor.  Lm as there ([ld][ld + 1]).
 __device__ bool cholesky_reg32(const float* S, float* Lm, int d, int ld, float reg, int* flag) {
-  const int lw = ld + 1;
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    float a[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q)
-      a[q] = (lane < d && q <= lane) ? S[lane * ld + q] + (q == lane ? reg : 0.0f) : 0.0f;
-    bool bad = false;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j < d && !bad) {
-        const float piv = __shfl_sync(0xffffffffu, a[j], j);
-        bad = !(piv > 0.0f) || !isfinite(piv);
-        const float ljj = sqrtf(bad ? 1.0f : piv);
-        if (lane > j) a[j] = a[j] / ljj;
-        else if (lane == j) a[j] = ljj;
-        const float lij = a[j];
-#pragma unroll
-        for (int q = j + 1; q < 32; ++q) {
-          const float lqj = __shfl_sync(0xffffffffu, a[j], q);
-          if (lane > j && q <= lane) a[q] = fmaf(-lij, lqj, a[q]);
-        }
-      }
+  __shared__ float col[33];  // col[32]: the pivot's square root
+  const int i = threadIdx.x >> 5, q = threadIdx.x & 31;
+  const bool own = i < d && q <= i;
+  float a = own ? S[i * ld + q] + (q == i ? reg : 0.0f) : 0.0f;
+  if (threadIdx.x == 0) *flag = 0;
+  __syncthreads();
+  for (int j = 0; j < d; ++j) {
+    if (i == j && q == j) {
+      const bool bad = !(a > 0.0f) || !isfinite(a);
+      if (bad) *flag = 1;
+      a = sqrtf(bad ? 1.0f : a);
+      col[32] = a;
     }
-    if (lane < ld) {
-#pragma unroll
-      for (int q = 0; q < 32; ++q)
-        if (q < ld) Lm[lane * lw + q] = (lane < d && q <= lane) ? a[q] : 0.0f;
+    __syncthreads();
+    if (*flag) break;
+    const float ljj = col[32];
+    if (q == j && i > j && i < d) {
+      a = a / ljj;
+      col[i] = a;
     }
-    if (lane == 0) *flag = bad ? 1 : 0;
+    __syncthreads();
+    if (own && q > j) a = fmaf(-col[i], col[q], a);
   }
+  if (i < ld && q < ld) Lm[i * (ld + 1) + q] = own ? a : 0.0f;
   __syncthreads();
-  const bool fail = *flag != 0;
-  __syncthreads();
-  return fail;
+  return *flag != 0;
 }
 
 // Direction metric (Sec. 3.2): covariance of the m live points (divisor m-1)
@@ -250,7 +242,8 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
     float reg = R.cov_eps * (float)tr / (float)d;
     bool fail = true;
     for (int attempt = 0; attempt <= 6; ++attempt) {
-      fail = (d <= 32) ? cholesky_reg32(Sm, Lm, d, ld, reg, &flag_s) : cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
+      fail = (d <= 32 && (int)blockDim.x >= 32 * d) ? cholesky_reg32(Sm, Lm, d, ld, reg, &flag_s)
+                                                    : cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
       __syncthreads();
       if (!fail) break;
       reg *= 10.0f;

@@ -412,7 +412,8 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0, cudaEvent_t mark = nullptr) 
   cudaStream_t st = c->cur;
   {
     Rec r(c, NSS_K_PROLOGUE);
-    CK(nss::launch_prologue(D, r0, nr, c->prologue_smem, st), "prologue launch");
+    // with several groups a smaller block, so it fits beside another group's sweep
+    CK(nss::launch_prologue(D, r0, nr, c->n_groups > 1 ? 256 : 1024, c->prologue_smem, st), "prologue launch");
   }
   for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
     const int L = g * nss_ctx::kDirClasses + q;

@@ -150,6 +150,51 @@ __device__ bool cholesky_reg32(const float* S, float* Lm, int d, int ld, float r
   return *flag != 0;
 }
 
+// d <= 32 with fewer than 32 d threads: warp 0 alone, row i in lane i's
+// registers, column j broadcast through shared memory.  Same operations in
+// the same order as cholesky_smem.
+__device__ bool cholesky_warp32(const float* S, float* Lm, int d, int ld, float reg, int* flag) {
+  __shared__ float colv[32];
+  const int lw = ld + 1;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    float a[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      a[q] = (lane < d && q <= lane) ? S[lane * ld + q] + (q == lane ? reg : 0.0f) : 0.0f;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j < d && !bad) {
+        const float piv = __shfl_sync(0xffffffffu, a[j], j);
+        bad = !(piv > 0.0f) || !isfinite(piv);
+        const float ljj = sqrtf(bad ? 1.0f : piv);
+        if (lane > j) a[j] = a[j] / ljj;
+        else if (lane == j) a[j] = ljj;
+        colv[lane] = a[j];
+        __syncwarp();
+        const float lij = a[j];
+#pragma unroll
+        for (int q = j + 1; q < 32; ++q) {
+          const float lqj = colv[q];
+          if (lane > j && q <= lane) a[q] = fmaf(-lij, lqj, a[q]);
+        }
+        __syncwarp();
+      }
+    }
+    if (lane < ld) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (q < ld) Lm[lane * lw + q] = (lane < d && q <= lane) ? a[q] : 0.0f;
+    }
+    if (lane == 0) *flag = bad ? 1 : 0;
+  }
+  __syncthreads();
+  const bool fail = *flag != 0;
+  __syncthreads();
+  return fail;
+}
+
 // Direction metric (Sec. 3.2): covariance of the m live points (divisor m-1)
 // about a shifted mean, FP32 with 4x4 register tiles and a fixed-order
 // reduction; regularised by eps * tr/d and factorised; a failed factorisation
@@ -242,8 +287,9 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
     float reg = R.cov_eps * (float)tr / (float)d;
     bool fail = true;
     for (int attempt = 0; attempt <= 6; ++attempt) {
-      fail = (d <= 32 && (int)blockDim.x >= 32 * d) ? cholesky_reg32(Sm, Lm, d, ld, reg, &flag_s)
-                                                    : cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
+      if (d <= 32 && (int)blockDim.x >= 32 * d) fail = cholesky_reg32(Sm, Lm, d, ld, reg, &flag_s);
+      else if (d <= 32) fail = cholesky_warp32(Sm, Lm, d, ld, reg, &flag_s);
+      else fail = cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
       __syncthreads();
       if (!fail) break;
       reg *= 10.0f;
@@ -561,8 +607,8 @@ cudaError_t setup_kernel_attributes() {
   return cudaFuncSetAttribute(k_final_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s) {
-  k_prologue<<<n_runs, 1024, smem, s>>>(D, run0);
+cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, int threads, size_t smem, cudaStream_t s) {
+  k_prologue<<<n_runs, threads, smem, s>>>(D, run0);
   return cudaGetLastError();
 }
 

@@ -412,8 +412,7 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0, cudaEvent_t mark = nullptr) 
   cudaStream_t st = c->cur;
   {
     Rec r(c, NSS_K_PROLOGUE);
-    // with several groups a smaller block, so it fits beside another group's sweep
-    CK(nss::launch_prologue(D, r0, nr, c->n_groups > 1 ? 256 : 1024, c->prologue_smem, st), "prologue launch");
+    CK(nss::launch_prologue(D, r0, nr, c->prologue_smem, st), "prologue launch");
   }
   for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
     const int L = g * nss_ctx::kDirClasses + q;
@@ -1039,9 +1038,9 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     // shared memory of the prologue: sort keys + survivors/flags, or the
     // covariance reductions and the two d x d matrices
     const size_t sortb = (size_t)R.m2 * 8 + (size_t)R.m2 * 4 + (size_t)R.m * 4;
-    const int nt = R.dpad / 4, ntp = nt * (nt + 1) / 2, parts2 = std::max(1, 1024 / ntp);
+    const int nt = R.dpad / 4, ntp = nt * (nt + 1) / 2, parts2 = std::max(1, nss::kPrologueThreads / ntp);
     const size_t covb = sizeof(float) * ((size_t)parts2 * ntp * 16 + (size_t)R.dpad * (2 * R.dpad + 1));
-    const size_t meanb = sizeof(float) * 1024;
+    const size_t meanb = sizeof(float) * nss::kPrologueThreads;
     c->prologue_smem = std::max(c->prologue_smem, std::max(sortb, std::max(covb, meanb)));
     c->final_smem = std::max(c->final_smem, (size_t)R.m2 * 8);
   }

@@ -312,7 +312,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
 // ---------------------------------------------------------------------------
 // Iteration prologue: steps (i), (ii), evidence and metric for one run.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_prologue(Dev D, int run0) {
+__global__ void __launch_bounds__(kPrologueThreads) k_prologue(Dev D, int run0) {
   const int run = run0 + blockIdx.x;
   const RunDesc& R = D.desc[run];
   RunState& S = D.st[run];
@@ -607,8 +607,8 @@ cudaError_t setup_kernel_attributes() {
   return cudaFuncSetAttribute(k_final_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, int threads, size_t smem, cudaStream_t s) {
-  k_prologue<<<n_runs, threads, smem, s>>>(D, run0);
+cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s) {
+  k_prologue<<<n_runs, kPrologueThreads, smem, s>>>(D, run0);
   return cudaGetLastError();
 }
 

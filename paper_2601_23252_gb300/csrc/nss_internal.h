@@ -17,7 +17,7 @@ constexpr int kShrinkCap = 100;     // shrinkage proposals before a null move (A
 constexpr uint32_t kTagParent = 0xFFFFFFF0u;
 constexpr uint32_t kTagInit = 0xFFFFFFF1u;
 constexpr uint32_t kTagVolsim = 0xFFFFFFF2u;
-constexpr int kPrologueThreads = 256;  // small enough to sit beside a running sweep
+constexpr int kPrologueThreads = 1024;  // one block per run; fixed, so every context reduces in the same order
 constexpr int kNumCfgs = 25;        // sweep configurations: 22 grouped (G lanes x DPL dims), 3 lane-per-chain
 constexpr int kVolTile = 1024;      // dead points per volume-simulation tile
 

@@ -116,42 +116,8 @@ __device__ bool cholesky_smem(const float* S, float* Lm, int d, int ld, float re
   return fail;
 }
 
-// d <= 32 and at least 32 d threads: the same factorisation with entry
-// (i, q) in a register of thread 32 i + q (warp i holds row i).  Per column j
-// the pivot and the column's entries go through shared memory (col), the
-// rest stays in registers; the same operations in the same order as
-// cholesky_smem, so the same factor.  Lm as there ([ld][ld + 1]).
-__device__ bool cholesky_reg32(const float* S, float* Lm, int d, int ld, float reg, int* flag) {
-  __shared__ float col[33];  // col[32]: the pivot's square root
-  const int i = threadIdx.x >> 5, q = threadIdx.x & 31;
-  const bool own = i < d && q <= i;
-  float a = own ? S[i * ld + q] + (q == i ? reg : 0.0f) : 0.0f;
-  if (threadIdx.x == 0) *flag = 0;
-  __syncthreads();
-  for (int j = 0; j < d; ++j) {
-    if (i == j && q == j) {
-      const bool bad = !(a > 0.0f) || !isfinite(a);
-      if (bad) *flag = 1;
-      a = sqrtf(bad ? 1.0f : a);
-      col[32] = a;
-    }
-    __syncthreads();
-    if (*flag) break;
-    const float ljj = col[32];
-    if (q == j && i > j && i < d) {
-      a = a / ljj;
-      col[i] = a;
-    }
-    __syncthreads();
-    if (own && q > j) a = fmaf(-col[i], col[q], a);
-  }
-  if (i < ld && q < ld) Lm[i * (ld + 1) + q] = own ? a : 0.0f;
-  __syncthreads();
-  return *flag != 0;
-}
-
-// d <= 32 with fewer than 32 d threads: warp 0 alone, row i in lane i's
-// registers, column j broadcast through shared memory.  Same operations in
+// d <= 32: warp 0 alone, row i in lane i's registers, column j broadcast
+// through shared memory (no block barriers inside).  Same operations in
 // the same order as cholesky_smem.
 __device__ bool cholesky_warp32(const float* S, float* Lm, int d, int ld, float reg, int* flag) {
   __shared__ float colv[32];
@@ -287,9 +253,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
     float reg = R.cov_eps * (float)tr / (float)d;
     bool fail = true;
     for (int attempt = 0; attempt <= 6; ++attempt) {
-      if (d <= 32 && (int)blockDim.x >= 32 * d) fail = cholesky_reg32(Sm, Lm, d, ld, reg, &flag_s);
-      else if (d <= 32) fail = cholesky_warp32(Sm, Lm, d, ld, reg, &flag_s);
-      else fail = cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
+      fail = (d <= 32) ? cholesky_warp32(Sm, Lm, d, ld, reg, &flag_s) : cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
       __syncthreads();
       if (!fail) break;
       reg *= 10.0f;

@@ -291,6 +291,38 @@ nss_status nss_get_profile(nss_ctx *ctx, nss_profile *prof);
    memory; runs on the default stream and synchronises. */
 nss_status nss_logreg_logits(const float *X, int n, int d, const float *U, int nu, float *Z);
 
+/* Posterior expectations over a finished run's dead points (App. D.2 weights:
+   the normalised geometric-mean weights w_i = exp(log_w_i), sum 1), reduced in
+   FP64 on the device in a fixed order.  The gradient kinds are the Fisher
+   identity: for Z(theta) = int L(x; theta) Pi(x; theta) dx,
+     d log Z / d theta = E_post[ d/dtheta log L(x; theta) + d/dtheta log Pi(x; theta) ],
+   estimated by sum_i w_i (d/dtheta log L + d/dtheta log Pi)(x_i).
+     NSS_GRAD_LIK_SIGMA        GAUSS_ISO / GMM_ISO_EQUAL: the likelihood width sigma;
+                               1 value: sum_c r_c |x - mu_c|^2 / sigma^3 - d / sigma
+                               (r_c the component responsibilities)
+     NSS_GRAD_LIK_MU           GAUSS_ISO / GMM_ISO_EQUAL: the means; n_comp * d
+                               values: r_c (x - mu_c) / sigma^2
+     NSS_GRAD_PRIOR_LOG_PREC   GAUSS_DIAG prior: a common log-precision lambda of
+                               all coordinates (sd b_i -> b_i e^{-lambda/2}) at
+                               lambda = 0; 1 value: d/2 - sum_i ((x_i - a_i)/b_i)^2 / 2
+     NSS_GRAD_GP_NOISE_SCALE   GP_RBF_WHITE: a fixed multiplier s of the noise sd
+                               (K = a^2 k + (s sigma_n)^2 I) at s = 1; 1 value:
+                               sigma_n^2 (|K^-1 y|^2 - tr K^-1), from an FP32
+                               Cholesky and triangular inverse of K per dead point
+                               with weight above 1e-12 of the largest
+     NSS_MOMENT_MEAN           any kind: the posterior mean of x; d values
+   Requires a finished run (nss_run or nss_finalise).  out: host array of n_out
+   values (NSS_ERR_ARG if n_out differs from the kind's count or the kind does
+   not fit the run's likelihood/prior).  Synchronises the context's stream. */
+enum {
+    NSS_GRAD_LIK_SIGMA = 0,
+    NSS_GRAD_LIK_MU = 1,
+    NSS_GRAD_PRIOR_LOG_PREC = 2,
+    NSS_GRAD_GP_NOISE_SCALE = 3,
+    NSS_MOMENT_MEAN = 4
+};
+nss_status nss_posterior_expectation(nss_ctx *ctx, int run, int kind, double *out, int n_out);
+
 /* Volume simulation without allocation.  The paper has no counterpart: this
    is a library convenience for callers that must not allocate device memory
    when they need it, e.g. a service whose framework allocator owns and caches

@@ -119,6 +119,8 @@ def lib():
                                        _dp, _dp, _dp, _dp]
             L.orc_volume_trajectory.argtypes = [C.c_longlong, _ip, C.c_int, C.c_uint64, C.c_uint32,
                                                 _dp]
+            L.orc_posterior_expectation.argtypes = [C.POINTER(_Problem), C.c_int, C.c_longlong, _dp, _dp, _dp]
+            L.orc_posterior_expectation.restype = C.c_int
             L.orc_u_star.restype = C.c_double
             L.orc_phi.restype = C.c_double
             L.orc_phi.argtypes = [C.c_double]
@@ -337,6 +339,21 @@ def finalise(logL, nlive, R, seed, run_id, want_r=False):
     if want_r:
         return m.value, s.value, lw, lz
     return m.value, s.value, lw
+
+
+GRAD_LIK_SIGMA, GRAD_LIK_MU, GRAD_PRIOR_LOG_PREC, GRAD_GP_NOISE_SCALE, MOMENT_MEAN = 0, 1, 2, 3, 4
+
+
+def posterior_expectation(pb: Problem, kind, x, log_w):
+    """Weighted posterior expectation over dead points (App. D.2 weights) and
+    the Fisher-identity gradients of log Z (orc_posterior_expectation)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, pb.d)
+    lw = np.ascontiguousarray(log_w, dtype=np.float64)
+    out = np.empty(max(1, pb.d * max(1, pb.s.n_comp)))
+    n = lib().orc_posterior_expectation(C.byref(pb.s), int(kind), x.shape[0], _d(x), _d(lw), _d(out))
+    if n < 0:
+        raise ValueError(f"kind {kind} does not apply to this problem")
+    return out[:n].copy()
 
 
 def volume_trajectory(nlive, r, seed, run_id):

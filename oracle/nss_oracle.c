@@ -908,3 +908,116 @@ void orc_volume_trajectory(long long n, const int *nlive, int r, uint64_t seed, 
         logX[i] = acc;
     }
 }
+
+/* Posterior expectations over weighted dead points, with the normalised
+   weights w_i = exp(log_w_i) of App. D.2, and the Fisher identity: for
+   Z(theta) = int L(x; theta) Pi(x; theta) dx,
+     d log Z / d theta = E_post[d/dtheta log L(x; theta) + d/dtheta log Pi(x; theta)].
+   kind 0: likelihood width sigma (Gaussian / equal-weight mixture)
+           d/dsigma log L = sum_c r_c |x - mu_c|^2 / sigma^3 - d / sigma;
+   kind 1: the means, n_comp * d values: r_c (x - mu_c) / sigma^2;
+   kind 2: a common log-precision lambda of a Gaussian prior (sd b_i e^{-lambda/2})
+           at lambda = 0: d/2 - sum_i ((x_i - a_i) / b_i)^2 / 2;
+   kind 3: a noise multiplier s of the GP (K = a^2 k + (s sigma_n)^2 I) at s = 1:
+           sigma_n^2 (|K^-1 y|^2 - tr K^-1);
+   kind 4: the posterior mean of x, d values.
+   r_c = N(x; mu_c) / sum_c' N(x; mu_c').  Returns the number of values written,
+   or -1 if the kind does not apply. */
+static double orc_gp_noise_term(const orc_problem *pb, const double *th)
+{
+    int n = pb->n_data;
+    double ell = exp(th[0]), amp = exp(th[1]), sn = exp(th[2]);
+    double *K = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *z = (double *)malloc(sizeof(double) * n);
+    double *beta = (double *)malloc(sizeof(double) * n);
+    if (!K || !z || !beta) { free(K); free(z); free(beta); return NAN; }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double dt = pb->t[i] - pb->t[j];
+            K[i * n + j] = amp * amp * exp(-dt * dt / (2.0 * ell * ell)) + (i == j ? sn * sn : 0.0);
+        }
+    double out = NAN;
+    if (orc_cholesky_inplace(n, K) == 0) {
+        /* beta = K^-1 y: L z = y, then L^T beta = z */
+        for (int i = 0; i < n; ++i) {
+            double s = pb->y[i];
+            for (int j = 0; j < i; ++j) s -= K[i * n + j] * z[j];
+            z[i] = s / K[i * n + i];
+        }
+        double bb = 0.0;
+        for (int i = n - 1; i >= 0; --i) {
+            double s = z[i];
+            for (int j = i + 1; j < n; ++j) s -= K[j * n + i] * beta[j];
+            beta[i] = s / K[i * n + i];
+            bb += beta[i] * beta[i];
+        }
+        /* tr K^-1 = sum_j |L^-1 e_j|^2 */
+        double tr = 0.0;
+        for (int c = 0; c < n; ++c) {
+            for (int i = c; i < n; ++i) {
+                double s = (i == c) ? 1.0 : 0.0;
+                for (int j = c; j < i; ++j) s -= K[i * n + j] * z[j];
+                z[i] = s / K[i * n + i];
+                tr += z[i] * z[i];
+            }
+        }
+        out = sn * sn * (bb - tr);
+    }
+    free(K); free(z); free(beta);
+    return out;
+}
+
+int orc_posterior_expectation(const orc_problem *pb, int kind, long long n, const double *x,
+                              const double *log_w, double *out)
+{
+    int d = pb->d;
+    int gauss = pb->lik_kind == ORC_LIK_GAUSS || pb->lik_kind == ORC_LIK_GMM;
+    int K = pb->lik_kind == ORC_LIK_GMM ? pb->n_comp : 1;
+    int count;
+    switch (kind) {
+    case 0: count = gauss ? 1 : -1; break;
+    case 1: count = gauss ? K * d : -1; break;
+    case 2: count = pb->prior_kind == ORC_PRIOR_GAUSS ? 1 : -1; break;
+    case 3: count = pb->lik_kind == ORC_LIK_GP ? 1 : -1; break;
+    case 4: count = d; break;
+    default: count = -1;
+    }
+    if (count < 0) return -1;
+    for (int q = 0; q < count; ++q) out[q] = 0.0;
+    double s2 = pb->sigma * pb->sigma;
+    double *qd = (double *)malloc(sizeof(double) * (K > 0 ? K : 1));
+    double *r = (double *)malloc(sizeof(double) * (K > 0 ? K : 1));
+    for (long long i = 0; i < n; ++i) {
+        const double *xi = x + i * d;
+        double w = exp(log_w[i]);
+        if (kind == 4) {
+            for (int a = 0; a < d; ++a) out[a] += w * xi[a];
+        } else if (kind == 2) {
+            double s = 0.0;
+            for (int a = 0; a < d; ++a) { double u = (xi[a] - pb->a[a]) / pb->b[a]; s += u * u; }
+            out[0] += w * (0.5 * d - 0.5 * s);
+        } else if (kind == 3) {
+            if (w > 0.0) out[0] += w * orc_gp_noise_term(pb, xi);
+        } else {
+            double qmin = INFINITY;
+            for (int c = 0; c < K; ++c) {
+                double s = 0.0;
+                for (int a = 0; a < d; ++a) { double e = xi[a] - pb->mu[c * d + a]; s += e * e; }
+                qd[c] = s;
+                if (s < qmin) qmin = s;
+            }
+            double rs = 0.0;
+            for (int c = 0; c < K; ++c) { r[c] = exp(-(qd[c] - qmin) / (2.0 * s2)); rs += r[c]; }
+            if (kind == 0) {
+                double e = 0.0;
+                for (int c = 0; c < K; ++c) e += r[c] * qd[c];
+                out[0] += w * (e / rs / (s2 * pb->sigma) - d / pb->sigma);
+            } else {
+                for (int c = 0; c < K; ++c)
+                    for (int a = 0; a < d; ++a) out[c * d + a] += w * (r[c] / rs) * (xi[a] - pb->mu[c * d + a]) / s2;
+            }
+        }
+    }
+    free(qd); free(r);
+    return count;
+}

@@ -57,6 +57,7 @@ struct nss_ctx {
   int device = 0, num_sms = 1;
   std::vector<RunDesc> desc;
   std::vector<double> widths;
+  std::vector<double> sigmas;       // likelihood width of Gaussian / mixture runs
   std::vector<uint32_t> run_ids;
   RunDesc* d_desc = nullptr;
   RunState* d_state = nullptr;
@@ -959,6 +960,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   // ---- layout -------------------------------------------------------------
   c->desc.resize(n_runs);
   c->widths.resize(n_runs);
+  c->sigmas.assign(n_runs, 0.0);
   c->run_ids.resize(n_runs);
   double kappa = -1.0;
   for (int r = 0; r < n_runs; ++r) {
@@ -1002,6 +1004,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     if (lk.kind == NSS_LOGLIK_GAUSS_ISO || lk.kind == NSS_LOGLIK_GMM_ISO_EQUAL ||
         lk.kind == NSS_LOGLIK_TEST_FAULT) {
       const double s2 = lk.sigma * lk.sigma;
+      c->sigmas[r] = lk.sigma;
       R.inv2s2 = (float)(1.0 / (2.0 * s2));
       R.lognorm = (float)(-0.5 * R.d * std::log(2.0 * M_PI * s2) - std::log((double)R.n_comp));
     }
@@ -1337,6 +1340,90 @@ nss_status nss_autotune(nss_ctx* c, int iters, int* cfg_out) {
 nss_status nss_finalise(nss_ctx* c, nss_result* res) {
   if (!c) return NSS_ERR_ARG;
   return finalise_impl(c, res);
+}
+
+nss_status nss_posterior_expectation(nss_ctx* c, int run, int kind, double* out, int n_out) {
+  if (!c || run < 0 || run >= c->n_runs || !out) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  if (!c->h_state[run].finalised) return set_err(c, NSS_ERR_STATE, "posterior expectations before finalisation");
+  const RunDesc& R = c->desc[run];
+  const long long n = c->h_state[run].n_dead;
+  const bool gauss = R.lik_kind == nss::kLikGauss || R.lik_kind == nss::kLikGmm;
+  const int K = R.lik_kind == nss::kLikGmm ? R.n_comp : 1;
+  int count = -1;
+  switch (kind) {
+    case NSS_GRAD_LIK_SIGMA: count = gauss ? 1 : -1; break;
+    case NSS_GRAD_LIK_MU: count = gauss ? K * R.d : -1; break;
+    case NSS_GRAD_PRIOR_LOG_PREC: count = R.prior_kind == nss::kPriorGauss ? 1 : -1; break;
+    case NSS_GRAD_GP_NOISE_SCALE: count = R.lik_kind == nss::kLikGp ? 1 : -1; break;
+    case NSS_MOMENT_MEAN: count = R.d; break;
+    default: break;
+  }
+  if (count < 0) return set_err(c, NSS_ERR_ARG, "kind %d does not apply to run %d", kind, run);
+  if (n_out != count) return set_err(c, NSS_ERR_ARG, "kind %d gives %d values, n_out = %d", kind, count, n_out);
+  if (n <= 0) return set_err(c, NSS_ERR_STATE, "run %d has no dead points", run);
+  double *coef = nullptr, *dout = nullptr;
+  int* didx = nullptr;
+  auto release = [&]() {
+    cudaFree(coef);
+    cudaFree(dout);
+    cudaFree(didx);
+  };
+  cudaError_t e = cudaMalloc(&coef, sizeof(double) * (size_t)n * K);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double) * count);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "posterior scratch");
+  }
+  nss::PostArgs A;
+  A.x = c->fpool + R.o_dx;
+  A.lw = c->dpool + R.o_lw;
+  A.n = n;
+  A.d = R.d;
+  A.ld = R.dpad;
+  A.kind = kind;
+  A.K = K;
+  A.mu = c->fpool + R.o_mu;
+  A.pa = c->fpool + R.o_a;
+  A.pb = c->fpool + R.o_b;
+  A.sigma = c->sigmas[run];
+  if (kind == NSS_GRAD_GP_NOISE_SCALE) {
+    // dead points whose weight is above 1e-12 of the largest
+    std::vector<double> lw((size_t)n);
+    e = cudaMemcpyAsync(lw.data(), c->dpool + R.o_lw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(c, e, "weights copy");
+    }
+    c->prof.d2h_bytes += (long long)sizeof(double) * n;
+    double mx = -INFINITY;
+    for (double v : lw) mx = std::max(mx, v);
+    std::vector<int> idx;
+    for (long long i = 0; i < n; ++i)
+      if (lw[i] > mx - 27.631021115928547) idx.push_back((int)i);  // ln 1e12
+    const GPWork* gw = nullptr;
+    for (const auto& g : c->gp)
+      if (g.run == run) gw = &g;
+    e = cudaMemsetAsync(coef, 0, sizeof(double) * n, c->stream);
+    if (e == cudaSuccess && !idx.empty()) e = cudaMalloc(&didx, sizeof(int) * idx.size());
+    if (e == cudaSuccess && !idx.empty())
+      e = cudaMemcpyAsync(didx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && gw)
+      e = nss::launch_gp_noise_grad(dev_of(c), gw->args, run, didx, (int)idx.size(), R.n_data, coef, c->stream);
+    if (e == cudaSuccess) e = nss::launch_post_sum(coef, n, dout, c->stream);
+    c->prof.h2d_bytes += (long long)sizeof(int) * (long long)idx.size();
+  } else {
+    e = nss::launch_post(A, coef, dout, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "posterior expectation");
+  c->prof.d2h_bytes += (long long)sizeof(double) * count;
+  return NSS_OK;
 }
 
 nss_status nss_get_dead(nss_ctx* c, int run, float* x, float* logL, double* log_w, float* birth,

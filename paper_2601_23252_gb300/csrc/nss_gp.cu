@@ -230,13 +230,87 @@ __global__ void __launch_bounds__(kGPThreads) k_gp_sweep(Dev D, GPArgs A, int ru
   }
 }
 
+// Fisher-identity term of a fixed noise multiplier s (K = a^2 k + (s sigma_n)^2 I)
+// at s = 1 for the listed dead points: d/ds log p(y | theta) = sigma_n^2
+// (|K^-1 y|^2 - tr K^-1).  One block per point: the bordered factorisation
+// of gp_loglik leaves L and alpha = L^-1 y in shared memory; warp 0 solves
+// L^T beta = alpha (beta = K^-1 y); every warp solves L z = e_j for columns
+// j = warp, warp + 32, ... (tr K^-1 = sum_j |z_j|^2).  Sums in FP64.
+__global__ void __launch_bounds__(kGPThreads) k_gp_noise_grad(Dev D, GPArgs A, int run, const int* __restrict__ idx,
+                                                              int n_idx, double* __restrict__ coef) {
+  extern __shared__ float P[];
+  __shared__ GPShared sh;
+  __shared__ double wsum[32];
+  const RunDesc& R = D.desc[run];
+  const int b = blockIdx.x;
+  if (b >= n_idx) return;
+  const long long i = idx[b];
+  const int n = R.n_data;
+  float th[3];
+  for (int q = 0; q < 3; ++q) th[q] = D.f[R.o_dx + i * R.dpad + q];
+  const float ll = gp_loglik(A.t, A.y, n, th, P, sh);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* zbuf = P + (n + 1) * (n + 2) / 2 + wid * n;   // [32][n]
+  float* beta = P + (n + 1) * (n + 2) / 2 + 32 * n;    // [n]
+  if (!(ll > -INFINITY)) {
+    if (threadIdx.x == 0) coef[i] = 0.0;
+    return;
+  }
+  double part = 0.0;  // lane 0 of each warp: its columns' sum of squares (warp 0 also |beta|^2)
+  if (wid == 0) {
+    for (int r = n - 1; r >= 0; --r) {
+      float acc = 0.0f;
+      for (int k = r + 1 + lane; k < n; k += 32) acc = fmaf(P[pidx(k, r)], beta[k], acc);
+      acc = warp_sum_f(acc);
+      if (lane == 0) {
+        const float br = (P[pidx(n, r)] - acc) / P[pidx(r, r)];
+        beta[r] = br;
+        part += (double)br * (double)br;
+      }
+      __syncwarp();
+    }
+  }
+  for (int j = wid; j < n; j += 32) {
+    for (int r = j; r < n; ++r) {
+      float acc = 0.0f;
+      for (int k = j + lane; k < r; k += 32) acc = fmaf(P[pidx(r, k)], zbuf[k], acc);
+      acc = warp_sum_f(acc);
+      if (lane == 0) {
+        const float zr = ((r == j ? 1.0f : 0.0f) - acc) / P[pidx(r, r)];
+        zbuf[r] = zr;
+        part -= (double)zr * (double)zr;
+      }
+      __syncwarp();
+    }
+  }
+  if (lane == 0) wsum[wid] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 32; ++q) t += wsum[q];
+    const double s2n = exp(2.0 * (double)th[2]);
+    coef[i] = exp(D.dd[R.o_lw + i]) * s2n * t;
+  }
+}
+
 size_t gp_smem_bytes(int n) { return sizeof(float) * (size_t)((n + 1) * (n + 2) / 2); }
+size_t gp_grad_smem_bytes(int n) { return gp_smem_bytes(n) + sizeof(float) * (size_t)(33 * n); }
 
 cudaError_t setup_gp_attributes() {
   const int bytes = (int)gp_smem_bytes(kGPMaxN);
   cudaError_t e = cudaFuncSetAttribute(k_gp_init, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gp_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(k_gp_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gp_noise_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gp_grad_smem_bytes(kGPMaxN));
+}
+
+cudaError_t launch_gp_noise_grad(const Dev& D, const GPArgs& A, int run, const int* idx, int n_idx, int n,
+                                 double* coef, cudaStream_t s) {
+  if (n_idx <= 0) return cudaSuccess;
+  k_gp_noise_grad<<<n_idx, kGPThreads, gp_grad_smem_bytes(n), s>>>(D, A, run, idx, n_idx, coef);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gp_init(const Dev& D, const GPArgs& A, int run, int m, int n, cudaStream_t s) {

@@ -40,6 +40,26 @@ cudaError_t setup_gp_attributes();
 cudaError_t launch_gp_init(const Dev& D, const GPArgs& A, int run, int m, int n, cudaStream_t s);
 cudaError_t launch_gp_sweep(const Dev& D, const GPArgs& A, int run, int k, int n, cudaStream_t s);
 
+// Posterior expectations over a finished run's dead points (nss_post.cu).
+enum { kPostLikSigma = 0, kPostLikMu = 1, kPostPriorLogPrec = 2, kPostGpNoise = 3, kPostMean = 4 };
+struct PostArgs {
+  const float* x;      // dead points [n][ld]
+  const double* lw;    // normalised log weights [n]
+  long long n;
+  int d, ld, kind, K;
+  const float* mu;     // [K][ld] (likelihood kinds)
+  const float* pa;     // prior a (mean) [d]
+  const float* pb;     // prior b (sd) [d]
+  double sigma;
+};
+// pass 1 + 2; coef: [n] or [n][K] FP64 scratch; out: device, 1 / d / K*d values
+cudaError_t launch_post(const PostArgs& A, double* coef, double* out, cudaStream_t s);
+cudaError_t launch_post_sum(const double* coef, long long n, double* out, cudaStream_t s);
+// GP noise-scale term sigma_n^2 (|K^-1 y|^2 - tr K^-1) times the weight, for
+// the dead points idx[0..n_idx) of run `run`, into coef[idx[j]] (others untouched)
+cudaError_t launch_gp_noise_grad(const Dev& D, const GPArgs& A, int run, const int* idx, int n_idx, int n,
+                                 double* coef, cudaStream_t s);
+
 // one-time function attributes (dynamic shared memory above 48 KB)
 cudaError_t setup_kernel_attributes();
 cudaError_t setup_logits_attributes();

@@ -16,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnss_gb300.so")
 
 NSS_OK, NSS_DONE = 0, 1
+# posterior expectation kinds (include/nss.h)
+GRAD_LIK_SIGMA, GRAD_LIK_MU, GRAD_PRIOR_LOG_PREC, GRAD_GP_NOISE_SCALE, MOMENT_MEAN = 0, 1, 2, 3, 4
 STATUS = {0: "ok", 1: "done", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
           -4: "dead-point store full", -5: "iteration cap reached", -6: "non-finite evidence",
           -7: "call out of order"}
@@ -102,6 +104,7 @@ def lib():
     L.nss_cfg_dims.argtypes = [C.c_int]
     L.nss_get_dead.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_size_t, P(C.c_size_t)]
+    L.nss_posterior_expectation.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]
     L.nss_export_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, P(State)]
     L.nss_import_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, P(State)]
     L.nss_step_trace.argtypes = [C.c_void_p, C.c_int, P(Trace)]
@@ -322,6 +325,19 @@ class Sampler:
         self._check(lib().nss_get_dead(self._h, run, _ptr(out.get("x")), _ptr(out.get("logL")),
                                        _ptr(out.get("log_w")), _ptr(out.get("birth")),
                                        _ptr(out.get("nlive")), n, C.byref(nn)), "nss_get_dead")
+        return out
+
+    def posterior(self, kind, run=0):
+        """Posterior expectation of a finished run computed on the device
+        (nss_posterior_expectation): the Fisher-identity gradient of log Z for
+        the GRAD_* kinds, the posterior mean for MOMENT_MEAN.  numpy FP64."""
+        wl = self.workloads[run]
+        k = wl.mu.shape[0] if (wl.mu is not None and wl.lik == "gmm") else 1
+        count = {GRAD_LIK_SIGMA: 1, GRAD_LIK_MU: k * wl.d, GRAD_PRIOR_LOG_PREC: 1,
+                 GRAD_GP_NOISE_SCALE: 1, MOMENT_MEAN: wl.d}[kind]
+        out = np.empty(count, np.float64)
+        self._check(lib().nss_posterior_expectation(self._h, run, int(kind), _ptr(out), count),
+                    "nss_posterior_expectation")
         return out
 
     def export_state(self, run=0):

@@ -1,0 +1,142 @@
+"""Device posterior expectations and Fisher-identity gradients of log Z:
+(i) the kernel equals the checker's estimator applied to the GPU's own dead
+points and weights; (ii) the gradient agrees with the closed form over seeds;
+(iii) the torch.autograd.Function; (iv) the prior log-precision gradient of a
+logistic regression against finite differences of log Z."""
+import numpy as np
+import pytest
+import torch
+from scipy.special import ndtr
+
+import oracle as O
+from paper_2601_23252_gb300 import autograd as NA
+from paper_2601_23252_gb300 import native
+from paper_2601_23252_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _phi(z):
+    return np.exp(-0.5 * z * z) / np.sqrt(2 * np.pi)
+
+
+def _gauss_box(seed, mu=(0.3, 0.7), sigma=0.3):
+    mu = np.asarray(mu, float)
+    d = mu.size
+    return W.Workload("gauss_box", d, "box", np.zeros(d), np.ones(d), "gauss", 300, 150, 5 * d,
+                      sigma=sigma, mu=mu[None, :], seed=seed)
+
+
+def _f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def _checker_on_gpu_points(wl, s, kind, run=0):
+    """The checker's estimator on the dead points and weights the GPU produced,
+    with the problem's constants as the device holds them (FP32)."""
+    dd = s.dead(run)
+    kw = wl.oracle_kwargs()
+    if "mu" in kw:
+        kw["mu"] = _f32(kw["mu"])
+    if wl.lik == "gp":
+        kw["t"], kw["y"] = _f32(kw["t"]), _f32(kw["y"])
+    pb = O.Problem((wl.prior, _f32(wl.a), _f32(wl.b)), wl.lik, **kw)
+    return O.posterior_expectation(pb, kind, dd["x"].astype(np.float64), dd["log_w"])
+
+
+@pytest.mark.parametrize("case", ["gauss_box", "gmm", "gauss_prior"])
+def test_kernel_equals_checker_formula(gpu_lib, case):
+    if case == "gauss_box":
+        wl = _gauss_box(3)
+        kinds = [native.GRAD_LIK_SIGMA, native.GRAD_LIK_MU, native.MOMENT_MEAN]
+    elif case == "gmm":
+        wl = W.gmm_d32(seed=2, n_live=300, k=150).with_(p=32)
+        kinds = [native.GRAD_LIK_SIGMA, native.GRAD_LIK_MU, native.MOMENT_MEAN]
+    else:
+        wl = W.gauss20_paper(seed=4, n_live=256, k=128).with_(p=20)
+        kinds = [native.GRAD_PRIOR_LOG_PREC, native.GRAD_LIK_SIGMA, native.MOMENT_MEAN]
+    with native.Sampler(wl) as s:
+        s.run()
+        for kind in kinds:
+            g = s.posterior(kind)
+            ref = _checker_on_gpu_points(wl, s, kind)
+            scale = max(1.0, np.abs(ref).max())
+            print(f"\n{case} kind {kind}: gpu {g[:3]} checker {ref[:3]}")
+            assert np.allclose(g, ref, rtol=1e-9, atol=1e-9 * scale)
+
+
+def test_gp_noise_scale_kernel_equals_checker_formula(gpu_lib):
+    wl = W.gp_d3(seed=1, n=48).with_(n_live=200, k=100)
+    with native.Sampler(wl) as s:
+        s.run()
+        g = s.posterior(native.GRAD_GP_NOISE_SCALE)[0]
+        ref = _checker_on_gpu_points(wl, s, native.GRAD_GP_NOISE_SCALE)[0]
+    print(f"\ngp noise scale: gpu {g:.6f} checker {ref:.6f}")
+    # FP32 Cholesky and triangular inverse per point against FP64
+    assert g == pytest.approx(ref, rel=2e-3, abs=2e-3)
+
+
+def test_sigma_and_mu_gradients_against_closed_form(gpu_lib):
+    mu, s = np.array([0.3, 0.7]), 0.3
+    a, b = -mu / s, (1 - mu) / s
+    Zi = ndtr(b) - ndtr(a)
+    t_sig = np.sum((-_phi(b) * b + _phi(a) * a) / s / Zi)
+    t_mu = (_phi(a) - _phi(b)) / (s * Zi)
+    wls = [_gauss_box(sd).with_(run_id=sd) for sd in range(16)]
+    with native.Sampler(wls) as smp:
+        smp.run()
+        gs = np.array([smp.posterior(native.GRAD_LIK_SIGMA, r)[0] for r in range(16)])
+        gm = np.array([smp.posterior(native.GRAD_LIK_MU, r) for r in range(16)])
+    se_s = gs.std(ddof=1) / 4.0
+    se_m = gm.std(0, ddof=1) / 4.0
+    print(f"\nd lnZ/dsigma {gs.mean():.4f} +- {se_s:.4f} (closed form {t_sig:.4f}); "
+          f"d lnZ/dmu {gm.mean(0)} +- {se_m} (closed form {t_mu})")
+    assert abs(gs.mean() - t_sig) <= 4 * se_s + 0.02
+    assert np.all(np.abs(gm.mean(0) - t_mu) <= 4 * se_m + 0.02)
+
+
+def test_autograd_function(gpu_lib):
+    base = _gauss_box(5)
+    theta = torch.tensor(0.3, dtype=torch.float64, requires_grad=True)
+    z = NA.logz(theta, lambda v: base.with_(sigma=float(v)), native.GRAD_LIK_SIGMA)
+    z.backward()
+    with native.Sampler(base) as s:
+        r = s.run()[0]
+        g = s.posterior(native.GRAD_LIK_SIGMA)[0]
+    assert z.item() == r["logZ"]
+    assert theta.grad.item() == g
+    # vector parameter: the mean
+    m = torch.tensor([0.3, 0.7], dtype=torch.float64, requires_grad=True)
+    z2 = NA.logz(m, lambda v: base.with_(mu=np.asarray(v)[None, :]), native.GRAD_LIK_MU)
+    (2.0 * z2).backward()
+    with native.Sampler(base) as s:
+        s.run()
+        gm = s.posterior(native.GRAD_LIK_MU)
+    assert np.array_equal(m.grad.numpy(), 2.0 * gm)
+
+
+def test_logistic_prior_log_precision_against_finite_differences(gpu_lib):
+    """d lnZ/d lambda (prior sd b e^{-lambda/2}) at lambda = 0 from the Fisher
+    kernel against central differences of lnZ at +-h, the same seeds on both
+    sides (common random numbers)."""
+    h = 0.25
+    seeds = range(8)
+    base = [W.logreg_d100(seed=sd, n_rows=400, d=6, n_live=200, k=100).with_(run_id=sd) for sd in seeds]
+    d = base[0].d
+
+    def at(lam):
+        return [w.with_(b=np.full(d, np.exp(-lam / 2))) for w in base]
+
+    with native.Sampler(at(0.0)) as s:
+        res = s.run()
+        g = np.array([s.posterior(native.GRAD_PRIOR_LOG_PREC, r)[0] for r in range(len(base))])
+    with native.Sampler(at(h)) as s:
+        zp = np.array([r["logZ"] for r in s.run()])
+    with native.Sampler(at(-h)) as s:
+        zm = np.array([r["logZ"] for r in s.run()])
+    fd = (zp - zm) / (2 * h)
+    diff = g - fd
+    se = diff.std(ddof=1) / np.sqrt(diff.size)
+    print(f"\nFisher {g.mean():.4f}, finite differences {fd.mean():.4f}, paired se {se:.4f}, "
+          f"logZ err {np.mean([r['logZ_err'] for r in res]):.3f}")
+    assert abs(diff.mean()) <= 4 * se + 0.05

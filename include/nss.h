@@ -323,6 +323,18 @@ enum {
 };
 nss_status nss_posterior_expectation(nss_ctx *ctx, int run, int kind, double *out, int n_out);
 
+/* Reweighting a finished run to inverse temperature beta (Eq. eq:marginal,
+   Z(beta) = sum_i L_i^beta dX_i, from the same dead points; App. D.2):
+     out[0] = log Z(beta), the mean over the R simulated volume trajectories,
+     out[1] = its standard deviation (ddof 1),
+     out[2] = the Kish effective sample size (sum w)^2 / sum w^2 of the
+              geometric-mean weights at beta.
+   beta = 1 reproduces nss_run's logZ and logZ_err.  Runs the volume
+   simulation of nss_volume_sim_static on beta * logL (same limits: at most
+   524288 dead points, else NSS_ERR_ARG; it shares that entry point's scratch,
+   so it must not overlap such a call).  Synchronises the context's stream. */
+nss_status nss_reweight(nss_ctx *ctx, int run, double beta, double *out);
+
 /* Volume simulation without allocation.  The paper has no counterpart: this
    is a library convenience for callers that must not allocate device memory
    when they need it, e.g. a service whose framework allocator owns and caches

@@ -1426,6 +1426,53 @@ nss_status nss_posterior_expectation(nss_ctx* c, int run, int kind, double* out,
   return NSS_OK;
 }
 
+nss_status nss_reweight(nss_ctx* c, int run, double beta, double* out) {
+  if (!c || run < 0 || run >= c->n_runs || !out || !std::isfinite(beta)) return NSS_ERR_ARG;
+  if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
+  nss_status st = sync_state(c);
+  if (st != NSS_OK) return st;
+  if (!c->h_state[run].finalised) return set_err(c, NSS_ERR_STATE, "reweighting before finalisation");
+  const RunDesc& R = c->desc[run];
+  const long long n = c->h_state[run].n_dead;
+  if (n < 1) return set_err(c, NSS_ERR_STATE, "run %d has no dead points", run);
+  float* lb = nullptr;
+  double *lw = nullptr, *aux = nullptr;
+  auto release = [&]() {
+    cudaFree(lb);
+    cudaFree(lw);
+    cudaFree(aux);
+  };
+  cudaError_t e = cudaMalloc(&lb, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&lw, sizeof(double) * n * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&aux, sizeof(double) * 4);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "reweighting scratch");
+  }
+  if ((e = nss::launch_scale_logL(c->fpool + R.o_dlogL, (float)beta, n, lb, c->stream)) != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "reweighting");
+  }
+  const uint64_t seed = ((uint64_t)R.key1 << 32) | R.key0;
+  nss_status sv = nss_volume_sim_static(lb, c->ipool + R.o_dn, n, c->R, seed, 0u, lw, aux, c->stream);
+  if (sv != NSS_OK) {
+    release();
+    return set_err(c, sv, "reweighting: %lld dead points, %d trajectories", n, c->R);
+  }
+  e = nss::launch_sq_weights(lw, n, lw + n, c->stream);
+  if (e == cudaSuccess) e = nss::launch_post_sum(lw + n, n, aux + 2, c->stream);
+  double h[3] = {0.0, 0.0, 0.0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, aux, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "reweighting");
+  c->prof.d2h_bytes += (long long)sizeof(double) * 3;
+  out[0] = h[0];
+  out[1] = h[1];
+  out[2] = 1.0 / h[2];
+  return NSS_OK;
+}
+
 nss_status nss_get_dead(nss_ctx* c, int run, float* x, float* logL, double* log_w, float* birth,
                         int* nlive, size_t cap, size_t* n_out) {
   if (!c || run < 0 || run >= c->n_runs) return NSS_ERR_ARG;

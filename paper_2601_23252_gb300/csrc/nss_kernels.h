@@ -55,6 +55,8 @@ struct PostArgs {
 // pass 1 + 2; coef: [n] or [n][K] FP64 scratch; out: device, 1 / d / K*d values
 cudaError_t launch_post(const PostArgs& A, double* coef, double* out, cudaStream_t s);
 cudaError_t launch_post_sum(const double* coef, long long n, double* out, cudaStream_t s);
+cudaError_t launch_scale_logL(const float* logL, float beta, long long n, float* out, cudaStream_t s);
+cudaError_t launch_sq_weights(const double* lw, long long n, double* out, cudaStream_t s);
 // GP noise-scale term sigma_n^2 (|K^-1 y|^2 - tr K^-1) times the weight, for
 // the dead points idx[0..n_idx) of run `run`, into coef[idx[j]] (others untouched)
 cudaError_t launch_gp_noise_grad(const Dev& D, const GPArgs& A, int run, const int* idx, int n_idx, int n,

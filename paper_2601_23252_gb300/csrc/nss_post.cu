@@ -100,7 +100,27 @@ __global__ void k_post_vec(PostArgs A, const double* __restrict__ coef, double* 
   }
 }
 
+__global__ void k_scale_logL(const float* __restrict__ logL, float beta, long long n, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = beta * logL[i];
+}
+
+__global__ void k_sq_weights(const double* __restrict__ lw, long long n, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = exp(2.0 * lw[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_scale_logL(const float* logL, float beta, long long n, float* out, cudaStream_t s) {
+  k_scale_logL<<<256, 256, 0, s>>>(logL, beta, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sq_weights(const double* lw, long long n, double* out, cudaStream_t s) {
+  k_sq_weights<<<256, 256, 0, s>>>(lw, n, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_post(const PostArgs& A, double* coef, double* out, cudaStream_t s) {
   if (A.n <= 0) return cudaErrorInvalidValue;

@@ -105,6 +105,7 @@ def lib():
     L.nss_get_dead.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_size_t, P(C.c_size_t)]
     L.nss_posterior_expectation.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]
+    L.nss_reweight.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p]
     L.nss_export_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, P(State)]
     L.nss_import_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, P(State)]
     L.nss_step_trace.argtypes = [C.c_void_p, C.c_int, P(Trace)]
@@ -339,6 +340,14 @@ class Sampler:
         self._check(lib().nss_posterior_expectation(self._h, run, int(kind), _ptr(out), count),
                     "nss_posterior_expectation")
         return out
+
+    def reweight(self, beta, run=0):
+        """log Z at inverse temperature beta from the same dead points, its
+        spread over the simulated volumes, and the Kish ESS of the weights
+        (nss_reweight)."""
+        out = np.empty(3, np.float64)
+        self._check(lib().nss_reweight(self._h, run, float(beta), _ptr(out)), "nss_reweight")
+        return {"logZ": out[0], "logZ_err": out[1], "ess": out[2]}
 
     def export_state(self, run=0):
         wl = self.workloads[run]

@@ -140,3 +140,30 @@ def test_logistic_prior_log_precision_against_finite_differences(gpu_lib):
     print(f"\nFisher {g.mean():.4f}, finite differences {fd.mean():.4f}, paired se {se:.4f}, "
           f"logZ err {np.mean([r['logZ_err'] for r in res]):.3f}")
     assert abs(diff.mean()) <= 4 * se + 0.05
+
+
+def test_reweighting_to_other_temperatures(gpu_lib):
+    """Z(beta) = sum_i L_i^beta dX_i from the same dead points: beta = 1
+    reproduces the run; beta = 0.5 against the closed form of the tempered
+    box Gaussian; the Kish ESS at beta = 1 from the run's own weights."""
+    mu, s = np.array([0.3, 0.7]), 0.3
+    wls = [_gauss_box(sd).with_(run_id=sd) for sd in range(8)]
+    beta = 0.5
+    d = 2
+    a, b = -mu * np.sqrt(beta) / s, (1 - mu) * np.sqrt(beta) / s
+    t_half = (-0.5 * d * beta * np.log(2 * np.pi * s * s) + 0.5 * d * np.log(2 * np.pi * s * s / beta)
+              + np.sum(np.log(ndtr(b) - ndtr(a))))
+    dev = []
+    with native.Sampler(wls) as smp:
+        res = smp.run()
+        for r in range(len(wls)):
+            one = smp.reweight(1.0, r)
+            assert one["logZ"] == pytest.approx(res[r]["logZ"], abs=1e-6)
+            assert one["logZ_err"] == pytest.approx(res[r]["logZ_err"], abs=1e-6)
+            lw = smp.dead(r)["log_w"]
+            assert one["ess"] == pytest.approx(1.0 / np.sum(np.exp(2 * lw)), rel=1e-6)
+            h = smp.reweight(beta, r)
+            dev.append((h["logZ"] - t_half) / h["logZ_err"])
+    dev = np.array(dev)
+    print(f"\nbeta = 0.5: closed form {t_half:.4f}, dev/err {np.round(dev, 2)}")
+    assert np.all(np.abs(dev) < 4.0)

@@ -77,6 +77,27 @@ def test_batch64_closed_form(gpu_lib):
     wls = W.batch64(seed=0)
     with native.Sampler(wls) as s:
         res = s.run()
+        # d lnZ/dsigma per run (Fisher identity, device kernel) and its spread
+        # over the weighted dead points: sum_i w_i g_i, se^2 ~ sum_i w_i^2 (g_i - mean)^2
+        grads, ses = [], []
+        for r, w in enumerate(wls):
+            g = s.posterior(native.GRAD_LIK_SIGMA, r)[0]
+            dd = s.dead(r)
+            wt = np.exp(dd["log_w"])
+            q = np.sum((dd["x"].astype(np.float64) - np.float32(w.mu[0][0])) ** 2, axis=1)
+            gi = q / w.sigma ** 3 - w.d / w.sigma
+            ses.append(np.sqrt(np.sum(wt ** 2 * (gi - g) ** 2)))
+            grads.append(g)
+    grads, ses = np.array(grads), np.array(ses)
+    # closed form: lnZ(sigma) = sum_i ln[Phi((b - mu)/sigma) - Phi((a - mu)/sigma)]
+    h = 1e-6
+    tg = np.array([(box_gauss_logZ(w.mu[0], w.sigma + h, w.a, w.b) - box_gauss_logZ(w.mu[0], w.sigma - h, w.a, w.b))
+                   / (2 * h) for w in wls])
+    zg = (grads - tg) / ses
+    print(f"\nbatch64 d lnZ/dsigma: max |dev|/se {np.max(np.abs(zg)):.2f}, mean {np.mean(zg):+.3f}")
+    # the per-run spread estimate ignores the volume noise: allow a wider band
+    assert np.all(np.abs(zg) < 6.0)
+    assert abs(np.mean(zg)) < 4.0 / np.sqrt(len(wls)) + 0.3
     truth = [box_gauss_logZ(w.mu[0], w.sigma, w.a, w.b) for w in wls]
     lz = np.array([r["logZ"] for r in res]); err = np.array([r["logZ_err"] for r in res])
     dev = lz - np.array(truth)

@@ -1034,6 +1034,10 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     R.o_dead = c->ni; c->ni += align16(R.k);
     R.o_parent = c->ni; c->ni += align16(R.k);
     R.o_stats = c->ni; c->ni += align16(6LL * R.k);
+    {
+      const bool own = lk.kind != NSS_LOGLIK_LOGREG && lk.kind != NSS_LOGLIK_GP_RBF_WHITE;
+      R.o_wd = c->ni; c->ni += own ? align16((long long)R.k * R.p * nss::kStepWords) : 16;
+    }
     // FP64 pool
     R.o_cum = c->nd; c->nd += align16(R.m + 1);
     R.o_lnd = c->nd; c->nd += align16(R.m);

@@ -7,7 +7,8 @@
 //   z_i ~ N(0, 1) from Box-Muller pair i/2 of words [0, 2 ceil(d/2)),
 //   d~ = L z (L lower triangular), v = d~ / |z| (unit Mahalanobis length)
 //   or d~ / |d~| (unit Euclidean length),
-// and writes v to V[chain][step][0, dpad).  The 32 threads of a warp are 32
+// and writes v to V[chain][step][0, dpad), with the step's first scalar
+// words (step_words) beside it.  The 32 threads of a warp are 32
 // chains of one run at one step, so every read of L (staged in shared memory
 // per block) is a broadcast.  Rows of d~ are formed from the last to the first so that d~_r
 // can overwrite z_r (row r reads z_c for c <= r only): z and d~ share one
@@ -22,6 +23,32 @@ namespace {
 
 constexpr int kDirThreads = 128;
 constexpr int kDirStepsPerBlock = 16;  // steps of one item per block, 4 per warp
+
+// Words nz .. nz + 11 of step s's counter stream (nz = 2 ceil(d/2)): the
+// bracket offset U, the prior slice height, the reserved word and the first
+// nine shrinkage proposals, which the sweep reads instead of drawing them.
+__device__ __forceinline__ void step_words(const RunDesc& R, uint32_t iter, int j, int s, int* __restrict__ wout) {
+  const uint32_t nz = 2u * (uint32_t)((R.d + 1) >> 1);
+  const uint32_t b0 = nz >> 2, off = nz & 3u;
+  uint32_t w[16];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint4 blk = make_uint4(0u, 0u, 0u, 0u);
+    if (q < 3 || off) blk = draw_block(R, iter, (uint32_t)j, (uint32_t)s, b0 + (uint32_t)q);
+    w[4 * q] = blk.x; w[4 * q + 1] = blk.y; w[4 * q + 2] = blk.z; w[4 * q + 3] = blk.w;
+  }
+  int4* o = reinterpret_cast<int4*>(wout + ((long long)j * R.p + s) * kStepWords);
+  // off is 0 or 2 (nz is even)
+  if (off == 0) {
+    o[0] = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+    o[1] = make_int4((int)w[4], (int)w[5], (int)w[6], (int)w[7]);
+    o[2] = make_int4((int)w[8], (int)w[9], (int)w[10], (int)w[11]);
+  } else {
+    o[0] = make_int4((int)w[2], (int)w[3], (int)w[4], (int)w[5]);
+    o[1] = make_int4((int)w[6], (int)w[7], (int)w[8], (int)w[9]);
+    o[2] = make_int4((int)w[10], (int)w[11], (int)w[12], (int)w[13]);
+  }
+}
 
 template <int DMAX>
 __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __restrict__ Ls, float* zsh,
@@ -139,7 +166,10 @@ __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* _
   const uint32_t iter = (uint32_t)S.iter;
   float* zsh = kShared ? dsm + ld * ld + threadIdx.x * (DMAX + 1) : nullptr;
   const int s1 = min(R.p, s0 + kDirStepsPerBlock);
-  for (int s = s0 + wid; s < s1; s += kDirThreads / 32) one_direction<DMAX>(R, dsm, zsh, iter, j, s, D.f + R.o_V);
+  for (int s = s0 + wid; s < s1; s += kDirThreads / 32) {
+    one_direction<DMAX>(R, dsm, zsh, iter, j, s, D.f + R.o_V);
+    step_words(R, iter, j, s, D.i + R.o_wd);
+  }
 }
 
 template <int DMAX>

@@ -59,18 +59,36 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   // the steps' directions, drawn ahead (nss_dirgen.cu); the load of step
   // s + 1's is issued while step s runs
   const float* vrow = f + R.o_V + (long long)j * R.p * ld;
+  // the steps' first scalar words (U, slice height, shrinkage proposals
+  // 0..8), drawn ahead beside the directions; lane gl's first-round proposal
+  // is word 3 + gl
+  const int* wrow = D.i + R.o_wd + (long long)j * R.p * kStepWords;
+  const bool wlane = 3 + gl < kStepWords;
   float vn[DPL];
 #pragma unroll
   for (int i = 0; i < DPL; ++i) vn[i] = 0.0f;
   if (has) ldg_lane<DPL>(vrow, gl, ld, vn);
+  uint32_t nU = (uint32_t)__ldg(wrow), nH = nonflat ? (uint32_t)__ldg(wrow + 1) : 0u;
+  uint32_t nS = wlane ? (uint32_t)__ldg(wrow + 3 + gl) : 0u;
   for (int s = 0; s < R.p; ++s) {
     float v[DPL];
 #pragma unroll
     for (int i = 0; i < DPL; ++i) v[i] = vn[i];
-    if (has && s + 1 < R.p) ldg_lane<DPL>(vrow + (long long)(s + 1) * ld, gl, ld, vn);
-    // the scalar words (U, slice height, shrinkage proposals) from blocks nz/4 + gl
-    StepWords<G> W;
-    W.draw(R, iter, (uint32_t)j, (uint32_t)s, gl, nz >> 2);
+    const uint32_t wU = nU, wH = nH, wS = nS;
+    if (s + 1 < R.p) {
+      const int* wn = wrow + (long long)(s + 1) * kStepWords;
+      if (has) ldg_lane<DPL>(vrow + (long long)(s + 1) * ld, gl, ld, vn);
+      nU = (uint32_t)__ldg(wn);
+      if (nonflat) nH = (uint32_t)__ldg(wn + 1);
+      if (wlane) nS = (uint32_t)__ldg(wn + 3 + gl);
+    }
+    // word nz + r of the step: drawn ahead for r < kStepWords, else now
+    const int* ws = wrow + (long long)s * kStepWords;
+    auto step_word = [&](uint32_t r) -> uint32_t {
+      if (r < (uint32_t)kStepWords) return (uint32_t)__ldg(ws + r);
+      const uint32_t wi = nz + r;
+      return pick(draw_block(R, iter, (uint32_t)j, (uint32_t)s, wi >> 2), wi & 3u);
+    };
 
     // coefficients of the step's line, reduced over the group
     float Cv = 0.0f;
@@ -140,7 +158,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       P0 = gsum<G>(P0, mask);
       P1 = gsum<G>(P1, mask);
       P2 = gsum<G>(P2, mask);
-      const float uh = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz + 1u, mask));
+      const float uh = u24(wH);
       height = fmaf(-0.5f, P0, R.prior_const) + logf(uh);
     }
     float x0 = 0.0f, v0 = 0.0f;  // coordinate 0 for the fault likelihood
@@ -193,7 +211,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     // H = G/2 consecutive ends of each per round.  The first failing end of
     // a side is where the one-at-a-time procedure stops, and the counters are
     // those of that procedure.
-    const float U = u24(W.word(R, iter, (uint32_t)j, (uint32_t)s, nz, mask));
+    const float U = u24(wU);
     const float tl0 = -w * U;
     float ends[2] = {tl0, tl0 + w};
     if constexpr (G >= 2) {
@@ -271,7 +289,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     for (int b0 = 0; b0 < kShrinkCap; b0 += G) {
       const int idx = b0 + gl;
       const bool valid = idx < kShrinkCap;
-      const float u = u24(W.lane_word(R, iter, (uint32_t)j, (uint32_t)s, nz + 3u + (uint32_t)idx, mask));
+      const float u = u24((b0 == 0 && wlane) ? wS : step_word(3u + (uint32_t)idx));
       float lo = tl, hi = tr, t = 0.0f;
 #pragma unroll
       for (int i = 0; i < G; ++i) {

@@ -110,9 +110,12 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
       }
     }
     // step words beyond the normals: U, height, shrinkage proposals
+    // words nz .. nz + 11 drawn ahead beside the directions; later ones now
+    const int* ws = D.i + R.o_wd + ((long long)j * R.p + s) * kStepWords;
     uint32_t cblk = 0xFFFFFFFFu;
     uint4 cw = make_uint4(0u, 0u, 0u, 0u);
     auto word = [&](uint32_t wi) {
+      if (wi - nz < (uint32_t)kStepWords) return (uint32_t)__ldg(ws + (wi - nz));
       if ((wi >> 2) != cblk) {
         cblk = wi >> 2;
         cw = draw_block(R, iter, (uint32_t)j, (uint32_t)s, cblk);

@@ -44,6 +44,27 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
   return (2.0 * (double)x + 1.0) * 0x1p-53;
 }
 
+// The same uniform rounded to FP32 ((float)u53(a, b)), without FP64
+// arithmetic: the 53-bit odd integer 2x + 1 converted with round-to-nearest,
+// then an exact scaling by 2^-53.
+__device__ __forceinline__ float u53f(uint32_t a, uint32_t b) {
+  const unsigned long long x = ((unsigned long long)(a >> 6) << 26) | (unsigned long long)(b >> 6);
+  return __ull2float_rn(2ull * x + 1ull) * 0x1p-53f;
+}
+
+// Volume-simulation term of death i on trajectory r (App. D.2):
+// log(u_{r,i}) / n_i in FP32, u from counter (r, i/2, TAG_VOLSIM, 0); `blk`
+// caches the Philox block of the pair (i even, i odd) under key id `bi`.
+__device__ __forceinline__ float vol_term_f(uint32_t k0, uint32_t k1, int r, long long i, int n, uint4& blk,
+                                            long long& bi) {
+  if ((i >> 1) != bi) {
+    bi = i >> 1;
+    blk = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)bi, kTagVolsim, 0u), k0, k1);
+  }
+  const float u = (i & 1) ? u53f(blk.z, blk.w) : u53f(blk.x, blk.y);
+  return logf(u) / (float)n;
+}
+
 // Box-Muller: r = sqrt(-2 ln u1), angle 2 pi u2.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
   const float r = sqrtf(-2.0f * logf(u24(a)));

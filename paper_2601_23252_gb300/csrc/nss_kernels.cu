@@ -422,12 +422,6 @@ struct VolArgs {
   double* tacc;        // [R][n_tiles] running log-sum-exp sum
 };
 
-__device__ __forceinline__ float vol_term(const RunDesc& R, int r, long long i, int n) {
-  const uint4 b = draw_block(R, (uint32_t)r, (uint32_t)(i >> 1), kTagVolsim, 0u);
-  const double u = (i & 1) ? u53(b.z, b.w) : u53(b.x, b.y);
-  return logf((float)u) / (float)n;
-}
-
 __global__ void k_vol_tilesum(Dev D, VolArgs A) {
   const int tile = blockIdx.x, r = threadIdx.x;
   if (r >= A.R) return;
@@ -437,7 +431,9 @@ __global__ void k_vol_tilesum(Dev D, VolArgs A) {
   const long long i0 = t.y, i1 = min((long long)t.y + kVolTile, n);
   double s = 0.0;
   const int* nl = D.i + R.o_dn;
-  for (long long i = i0; i < i1; ++i) s += (double)vol_term(R, r, i, nl[i]);
+  uint4 blk;
+  long long bi = -1;
+  for (long long i = i0; i < i1; ++i) s += (double)vol_term_f(R.key0, R.key1, r, i, nl[i], blk, bi);
   A.tsum[(size_t)r * A.n_tiles + tile] = s;
 }
 
@@ -470,37 +466,55 @@ __global__ void k_vol_weights(Dev D, VolArgs A) {
   const float* lL = D.f + R.o_dlogL;
   double* lw = D.dd + R.o_lw;
   const bool act = r < A.R;
-  double prev = act ? A.toff[(size_t)r * A.n_tiles + tile] : 0.0;  // log X_{i-1}
-  double cur = act ? prev + (double)vol_term(R, r, i0, nl[i0]) : 0.0;
+  uint4 blk;
+  long long bi = -1;
+  // log X_{i-1} in FP64; the terms t_i = log(u_i)/n_i in FP32.  The trapezoid
+  // weight (X_{i-1} - X_{i+1}) / 2 has log X_{i-1} + log(1 - e^{t_i + t_{i+1}})
+  // - ln 2 (t_{N+1} = -inf: X_{N+1} = 0)
+  double prev = act ? A.toff[(size_t)r * A.n_tiles + tile] : 0.0;
+  float tcur = act ? vol_term_f(R.key0, R.key1, r, i0, nl[i0], blk, bi) : 0.0f;
   double M = -INFINITY, Sacc = 0.0;
-  const double ln2 = 0.69314718055994530942;
+  const float ln2f = 0.693147182f;
   for (long long c0 = i0; c0 < i1; c0 += 32) {
     const int cn = (int)min((long long)32, i1 - c0);
     if (act) {
       for (int q = 0; q < cn; ++q) {
         const long long i = c0 + q;
-        double nxt = -INFINITY;
-        if (i + 1 < n) nxt = cur + (double)vol_term(R, r, i + 1, nl[i + 1]);
-        const double ldx = prev + (double)logf(-expm1f((float)(nxt - prev))) - ln2;
+        const float tnxt = (i + 1 < n) ? vol_term_f(R.key0, R.key1, r, i + 1, nl[i + 1], blk, bi) : -INFINITY;
+        const double ldx = prev + (double)(logf(-expm1f(tcur + tnxt)) - ln2f);
         const double v = (double)lL[i] + ldx;
         if (v == -INFINITY) {
           // a point outside every constraint set carries no weight
-        } else if (v > M) {
-          Sacc = Sacc * (double)expf((float)(M - v)) + 1.0;
-          M = v;
         } else {
-          Sacc += (double)expf((float)(v - M));
+          const float dv = (float)(v - M);
+          if (dv > 0.0f) {
+            Sacc = Sacc * (double)expf(-dv) + 1.0;
+            M = v;
+          } else {
+            Sacc += (double)expf(dv);
+          }
         }
         sh[r * 32 + q] = ldx;
-        prev = cur;
-        cur = nxt;
+        prev += (double)tcur;
+        tcur = tnxt;
       }
     }
     __syncthreads();
-    if (threadIdx.x < cn) {
+    // mean over the trajectories: one partial sum per warp and dead point,
+    // then the partials combined in warp order
+    {
+      const int pt = threadIdx.x & 31, part = threadIdx.x >> 5, P = blockDim.x >> 5;
       double s = 0.0;
-      for (int q = 0; q < A.R; ++q) s += sh[q * 32 + threadIdx.x];
-      lw[c0 + threadIdx.x] = (double)lL[c0 + threadIdx.x] + s / (double)A.R;
+      if (pt < cn)
+        for (int q = part; q < A.R; q += P) s += sh[q * 32 + pt];
+      __syncthreads();
+      sh[part * 32 + pt] = s;
+      __syncthreads();
+      if (threadIdx.x < cn) {
+        double tot = 0.0;
+        for (int q = 0; q < P; ++q) tot += sh[q * 32 + threadIdx.x];
+        lw[c0 + threadIdx.x] = (double)lL[c0 + threadIdx.x] + tot / (double)A.R;
+      }
     }
     __syncthreads();
   }

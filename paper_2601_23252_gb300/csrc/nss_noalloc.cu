@@ -41,18 +41,14 @@ struct StaticVol {
   double *tsum, *toff, *tmax, *tacc, *misc;
 };
 
-__device__ __forceinline__ float svol_term(const StaticVol& V, int r, long long i) {
-  const uint4 b = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)(i >> 1), kTagVolsim, 0u), V.k0, V.k1);
-  const double u = (i & 1) ? u53(b.z, b.w) : u53(b.x, b.y);
-  return logf((float)u) / (float)V.nlive[i];
-}
-
 __global__ void k_svol_tilesum(StaticVol V) {
   const int tile = blockIdx.x, r = threadIdx.x;
   if (r >= V.R) return;
   const long long i0 = (long long)tile * kVolTile, i1 = min(i0 + kVolTile, V.n);
   double s = 0.0;
-  for (long long i = i0; i < i1; ++i) s += (double)svol_term(V, r, i);
+  uint4 blk;
+  long long bi = -1;
+  for (long long i = i0; i < i1; ++i) s += (double)vol_term_f(V.k0, V.k1, r, i, V.nlive[i], blk, bi);
   V.tsum[(size_t)r * V.nt + tile] = s;
 }
 
@@ -73,36 +69,50 @@ __global__ void k_svol_weights(StaticVol V, double* __restrict__ lw) {
   const long long n = V.n;
   const long long i0 = (long long)tile * kVolTile, i1 = min(i0 + kVolTile, n);
   const bool act = r < V.R;
-  double prev = act ? V.toff[(size_t)r * V.nt + tile] : 0.0;
-  double cur = act ? prev + (double)svol_term(V, r, i0) : 0.0;
+  uint4 blk;
+  long long bi = -1;
+  double prev = act ? V.toff[(size_t)r * V.nt + tile] : 0.0;  // log X_{i-1}
+  float tcur = act ? vol_term_f(V.k0, V.k1, r, i0, V.nlive[i0], blk, bi) : 0.0f;
   double M = -INFINITY, Sacc = 0.0;
-  const double ln2 = 0.69314718055994530942;
+  const float ln2f = 0.693147182f;
   for (long long c0 = i0; c0 < i1; c0 += 32) {
     const int cn = (int)min((long long)32, i1 - c0);
     if (act) {
       for (int q = 0; q < cn; ++q) {
         const long long i = c0 + q;
-        double nxt = -INFINITY;
-        if (i + 1 < n) nxt = cur + (double)svol_term(V, r, i + 1);
-        const double ldx = prev + (double)logf(-expm1f((float)(nxt - prev))) - ln2;
+        const float tnxt = (i + 1 < n) ? vol_term_f(V.k0, V.k1, r, i + 1, V.nlive[i + 1], blk, bi) : -INFINITY;
+        const double ldx = prev + (double)(logf(-expm1f(tcur + tnxt)) - ln2f);
         const double v = (double)V.logL[i] + ldx;
-        if (v == -INFINITY) {
-        } else if (v > M) {
-          Sacc = Sacc * (double)expf((float)(M - v)) + 1.0;
-          M = v;
-        } else {
-          Sacc += (double)expf((float)(v - M));
+        if (v != -INFINITY) {
+          const float dv = (float)(v - M);
+          if (dv > 0.0f) {
+            Sacc = Sacc * (double)expf(-dv) + 1.0;
+            M = v;
+          } else {
+            Sacc += (double)expf(dv);
+          }
         }
         sh[r * 32 + q] = ldx;
-        prev = cur;
-        cur = nxt;
+        prev += (double)tcur;
+        tcur = tnxt;
       }
     }
     __syncthreads();
-    if (threadIdx.x < cn) {
+    // mean over the trajectories: one partial sum per warp and dead point,
+    // then the partials combined in warp order
+    {
+      const int pt = threadIdx.x & 31, part = threadIdx.x >> 5, P = blockDim.x >> 5;
       double s = 0.0;
-      for (int q = 0; q < V.R; ++q) s += sh[q * 32 + threadIdx.x];
-      lw[c0 + threadIdx.x] = (double)V.logL[c0 + threadIdx.x] + s / (double)V.R;
+      if (pt < cn)
+        for (int q = part; q < V.R; q += P) s += sh[q * 32 + pt];
+      __syncthreads();
+      sh[part * 32 + pt] = s;
+      __syncthreads();
+      if (threadIdx.x < cn) {
+        double tot = 0.0;
+        for (int q = 0; q < P; ++q) tot += sh[q * 32 + threadIdx.x];
+        lw[c0 + threadIdx.x] = (double)V.logL[c0 + threadIdx.x] + tot / (double)V.R;
+      }
     }
     __syncthreads();
   }

@@ -79,7 +79,7 @@ struct nss_ctx {
   int n_groups = 1;
   int g_r0[kMaxGroups + 1] = {};
   cudaStream_t gstream[kMaxGroups] = {};
-  cudaEvent_t fork_ev = nullptr, stagger_ev = nullptr, join_ev[kMaxGroups] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kMaxGroups] = {};
   cudaStream_t cur = nullptr;  // stream of the launches being enqueued
   std::vector<WorkItem> init_items[nss::kNumCfgs], sweep_items[kMaxGroups * kLists];
   WorkItem* d_init[nss::kNumCfgs] = {};
@@ -317,7 +317,6 @@ void free_ctx(nss_ctx* c) {
     if (c->join_ev[g]) cudaEventDestroy(c->join_ev[g]);
   }
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-  if (c->stagger_ev) cudaEventDestroy(c->stagger_ev);
   cudaFree(c->d_queue);
   cudaFree(c->d_vol);
   cudaFree(c->d_tiles);
@@ -405,9 +404,8 @@ nss_status sync_state(nss_ctx* c) {
   return NSS_OK;
 }
 
-// One outer iteration of the runs of group g, enqueued on c->cur; `mark`,
-// when given, is recorded once the iteration's directions are drawn.
-nss_status enqueue_iteration(nss_ctx* c, int g = 0, cudaEvent_t mark = nullptr) {
+// One outer iteration of the runs of group g, enqueued on c->cur.
+nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
   nss::Dev D = dev_of(c);
   const int r0 = c->g_r0[g], nr = c->g_r0[g + 1] - r0;
   cudaStream_t st = c->cur;
@@ -422,7 +420,6 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0, cudaEvent_t mark = nullptr) 
     CK(nss::launch_dirgen(8 << q, D, c->d_dir[L], (int)c->dir_items[L].size(), c->max_p, st),
        "direction launch");
   }
-  if (mark) CK(cudaEventRecord(mark, st), "stagger event");
   for (int q = 0; q < nss_ctx::kLists; ++q) {
     const int L = g * nss_ctx::kLists + q;
     if (c->sweep_items[L].empty()) continue;
@@ -474,15 +471,12 @@ nss_status enqueue_iterations(nss_ctx* c, int n) {
     }
     return NSS_OK;
   }
-  // group 1 starts once group 0 has drawn its first directions, so that
-  // one group's prologue and direction draws run beside the other's sweep
   CK(cudaEventRecord(c->fork_ev, c->stream), "fork");
   for (int g = 0; g < c->n_groups; ++g) CK(cudaStreamWaitEvent(c->gstream[g], c->fork_ev, 0), "fork");
   for (int i = 0; i < n; ++i)
     for (int g = 0; g < c->n_groups; ++g) {
       c->cur = c->gstream[g];
-      if (i == 0 && g == 1) CK(cudaStreamWaitEvent(c->gstream[1], c->stagger_ev, 0), "stagger");
-      nss_status st = enqueue_iteration(c, g, (i == 0 && g == 0) ? c->stagger_ev : nullptr);
+      nss_status st = enqueue_iteration(c, g);
       if (st != NSS_OK) {
         c->cur = c->stream;
         return st;
@@ -1148,7 +1142,6 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
       c->g_r0[1] = cut;
       c->n_groups = 2;
       CKC(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming), "event creation");
-      CKC(cudaEventCreateWithFlags(&c->stagger_ev, cudaEventDisableTiming), "event creation");
       for (int g = 0; g < 2; ++g) {
         CKC(cudaStreamCreateWithFlags(&c->gstream[g], cudaStreamNonBlocking), "stream creation");
         CKC(cudaEventCreateWithFlags(&c->join_ev[g], cudaEventDisableTiming), "event creation");

@@ -52,8 +52,20 @@ struct nss_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<LRWork> lr;
-  cudaGraphExec_t iter_graph = nullptr;
-  long long graph_launches = 0;
+  // captured chunks of outer iterations (one graph per chunk length and
+  // profiling flag); with profiling on, the graph carries its own event
+  // record nodes, read back after each replay
+  struct ChunkGraph {
+    int n = 0;
+    bool prof = false;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<EvRec> evs;
+    long long launches = 0;
+  };
+  std::vector<ChunkGraph> graphs;
+  std::vector<int> replayed;          // graphs replayed since the last harvest
+  bool capturing = false;
+  std::vector<EvRec> cap_evs;
   int device = 0, num_sms = 1;
   std::vector<RunDesc> desc;
   std::vector<double> widths;
@@ -343,7 +355,13 @@ void free_ctx(nss_ctx* c) {
     cudaFree(g.t);
     cudaFree(g.y);
   }
-  if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& e : g.evs) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -370,19 +388,35 @@ struct Rec {
     c->prof.launches[kind]++;
     if (c->profiling) {
       a = take_event(c);
-      cudaEventRecord(a, c->cur);
+      if (c->capturing) cudaEventRecordWithFlags(a, c->cur, cudaEventRecordExternal);
+      else cudaEventRecord(a, c->cur);
     }
   }
   ~Rec() {
     if (a) {
       cudaEvent_t b = take_event(c);
-      cudaEventRecord(b, c->cur);
-      c->pending.push_back({a, b, kind, cfg});
+      if (c->capturing) {
+        cudaEventRecordWithFlags(b, c->cur, cudaEventRecordExternal);
+        c->cap_evs.push_back({a, b, kind, cfg});
+      } else {
+        cudaEventRecord(b, c->cur);
+        c->pending.push_back({a, b, kind, cfg});
+      }
     }
   }
 };
 
 void harvest(nss_ctx* c) {  // after a stream synchronisation
+  for (int gi : c->replayed) {
+    for (auto& e : c->graphs[gi].evs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+        c->prof.ms[e.kind] += ms;
+        if (e.cfg >= 0) c->cfg_ms[e.cfg] += ms;
+      }
+    }
+  }
+  c->replayed.clear();
   for (auto& e : c->pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
@@ -490,44 +524,74 @@ nss_status enqueue_iterations(nss_ctx* c, int n) {
   return NSS_OK;
 }
 
-// One outer iteration: replayed from a captured CUDA graph when the context
-// has logistic runs (hundreds of launches per iteration) and profiling is
-// off; enqueued launch by launch otherwise.
-nss_status run_iteration(nss_ctx* c, int n = 1) {
-  if (c->lr.empty() || c->profiling) return enqueue_iterations(c, n);
-  c->cur = c->stream;
-  for (int i = 1; i < n; ++i) {
-    nss_status st = run_iteration(c, 1);
-    if (st != NSS_OK) return st;
+void drop_graphs(nss_ctx* c) {  // the captured chunks refer to the work lists
+  if (!c->graphs.empty()) cudaStreamSynchronize(c->stream);
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& e : g.evs) {
+      c->ev_pool.push_back(e.a);
+      c->ev_pool.push_back(e.b);
+    }
   }
-  if (!c->iter_graph) {
+  c->graphs.clear();
+  c->replayed.clear();
+}
+
+// n outer iterations, replayed from a captured CUDA graph of the whole chunk
+// (every group's launches, forks and joins; a run that is done skips its
+// kernels on the device).  Captured on first use for each chunk length and
+// profiling flag.  The autotuner enqueues launch by launch instead.
+nss_status run_iteration(nss_ctx* c, int n = 1) {
+  int gi = -1;
+  for (int q = 0; q < (int)c->graphs.size(); ++q)
+    if (c->graphs[q].n == n && c->graphs[q].prof == c->profiling) gi = q;
+  if (gi < 0) {
+    nss_ctx::ChunkGraph g;
+    g.n = n;
+    g.prof = c->profiling;
     const long long l0 = c->launches, t0 = c->prof.total_launches;
+    long long k0[8];
+    std::memcpy(k0, c->prof.launches, sizeof k0);
+    c->cap_evs.clear();
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
-    nss_status st = enqueue_iteration(c, 0);
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (st != NSS_OK) return st;
+    c->capturing = true;
+    nss_status st = enqueue_iterations(c, n);
+    c->capturing = false;
+    cudaGraph_t cg = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &cg);
+    if (st != NSS_OK) {
+      if (cg) cudaGraphDestroy(cg);
+      return st;
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
-    e = cudaGraphInstantiate(&c->iter_graph, g, 0);
-    cudaGraphDestroy(g);
+    e = cudaGraphInstantiate(&g.exec, cg, 0);
+    cudaGraphDestroy(cg);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-    c->graph_launches = c->launches - l0;
+    g.launches = c->launches - l0;
+    g.evs.swap(c->cap_evs);
     c->launches = l0;
     c->prof.total_launches = t0;
+    std::memcpy(c->prof.launches, k0, sizeof k0);
+    c->graphs.push_back(std::move(g));
+    gi = (int)c->graphs.size() - 1;
   }
-  CK(cudaGraphLaunch(c->iter_graph, c->stream), "graph launch");
-  c->launches += c->graph_launches;
-  c->prof.total_launches += c->graph_launches;
+  // one replay per harvest keeps every launch's event pair readable
+  if (c->profiling && std::find(c->replayed.begin(), c->replayed.end(), gi) != c->replayed.end()) {
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    harvest(c);
+  }
+  CK(cudaGraphLaunch(c->graphs[gi].exec, c->stream), "graph launch");
+  c->launches += c->graphs[gi].launches;
+  c->prof.total_launches += c->graphs[gi].launches;
+  for (const auto& e : c->graphs[gi].evs) c->prof.launches[e.kind]++;
+  if (c->profiling) c->replayed.push_back(gi);
   return NSS_OK;
 }
 
 // Work lists of the init and sweep kernels: 32/G slots or chains of one run
 // per warp, grouped by sweep configuration, costliest runs first.
 nss_status build_work(nss_ctx* c) {
-  if (c->iter_graph) {  // the captured iteration refers to the old work lists
-    cudaGraphExecDestroy(c->iter_graph);
-    c->iter_graph = nullptr;
-  }
+  drop_graphs(c);
   for (int q = 0; q < nss::kNumCfgs; ++q) {
     c->init_items[q].clear();
     cudaFree(c->d_init[q]);

@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NSS_ABI_VERSION 2
+#define NSS_ABI_VERSION 3
 
 typedef struct nss_ctx nss_ctx;
 
@@ -137,7 +137,21 @@ typedef struct {
     double cov_eps;            /* metric regularisation eps * tr(Sigma)/d        */
     void *cuda_stream;         /* cudaStream_t; NULL = default stream            */
     int sweep_cfg;             /* sweep configuration id, -1 = default           */
+    int kernel;                /* NSS_KERNEL_HRSS (the paper's NSS) or
+                                  NSS_KERNEL_RW (constrained random walk)       */
+    double rw_scale;           /* RW proposal x + rw_scale * L z; 0 = 2.38/sqrt(d) */
 } nss_options;
+
+/* Replacement kernels.  HRSS: hit-and-run slice sampling (Sec. 3.2).  RW:
+   the constrained Gaussian random-walk baseline (Sec. 3.1 "Vectorised
+   execution"; App. "Slice sampling vs random walk"): each of the p steps
+   proposes y = x + s L z with L the live-set Cholesky factor (the proposal
+   covariance matched to the live set) and z ~ N(0, I) from the step's normal
+   words; y replaces x when it lies in the prior support, logL(y) > logL* and,
+   for a Gaussian prior, ln u < ln Pi(y) - ln Pi(x) (Metropolis, u the step's
+   word 2 ceil(d/2)); otherwise the chain stays (a rejected step counts as a
+   null move).  Gaussian, mixture and flat likelihoods only. */
+enum { NSS_KERNEL_HRSS = 0, NSS_KERNEL_RW = 1 };
 
 /* Fills the paper's defaults: w = 1, MAHAL, tol = 1e-3, max_iter = 100000,
    n_sim = 100, cov_eps = 1e-6, seed 0, run_id 0, default stream,

@@ -42,6 +42,7 @@ class _Opts(C.Structure):
         ("n_live", C.c_int), ("k", C.c_int), ("p", C.c_int), ("w", C.c_double),
         ("dir_norm", C.c_int), ("cov_eps", C.c_double), ("tol", C.c_double),
         ("max_iter", C.c_int), ("seed", C.c_uint64), ("run_id", C.c_uint32),
+        ("kernel", C.c_int), ("rw_scale", C.c_double),
     ]
 
 
@@ -119,6 +120,8 @@ def lib():
                                        _dp, _dp, _dp, _dp]
             L.orc_volume_trajectory.argtypes = [C.c_longlong, _ip, C.c_int, C.c_uint64, C.c_uint32,
                                                 _dp]
+            L.orc_rw_step.argtypes = [C.POINTER(_Problem), _dp, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
+                                      C.c_uint32, C.c_uint32, C.c_uint32, _dp, _dp, C.POINTER(_Counts)]
             L.orc_posterior_expectation.argtypes = [C.POINTER(_Problem), C.c_int, C.c_longlong, _dp, _dp, _dp]
             L.orc_posterior_expectation.restype = C.c_int
             L.orc_u_star.restype = C.c_double
@@ -196,12 +199,16 @@ class Problem:
         return bool(lib().orc_in_support(C.byref(self.s), _d(x)))
 
 
+KERNEL_HRSS, KERNEL_RW = 0, 1
+
+
 def make_opts(n_live, k, p, seed=0, run_id=0, w=1.0, dir_norm=0, cov_eps=1e-6, tol=1e-3,
-              max_iter=100000):
+              max_iter=100000, kernel=KERNEL_HRSS, rw_scale=0.0):
     o = _Opts()
     o.n_live, o.k, o.p, o.w, o.dir_norm = n_live, k, p, float(w), int(dir_norm)
     o.cov_eps, o.tol, o.max_iter = float(cov_eps), float(tol), int(max_iter)
     o.seed, o.run_id = int(seed), int(run_id)
+    o.kernel, o.rw_scale = int(kernel), float(rw_scale)
     return o
 
 
@@ -280,6 +287,18 @@ def hrss_step(pb: Problem, L, w, dir_norm, logLstar, seed, run_id, it, chain, st
     lib().orc_hrss_step(C.byref(pb.s), _d(L), float(w), int(dir_norm), float(logLstar), int(seed),
                         int(run_id), int(it), int(chain), int(step), _d(x), C.byref(lx),
                         C.byref(cnt))
+    return x, lx.value, {f: getattr(cnt, f) for f, _ in _Counts._fields_}
+
+
+def rw_step(pb: Problem, L, scale, logLstar, seed, run_id, it, chain, step, x, logLx):
+    """One constrained random-walk step from x (modified copy returned)."""
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    x = np.array(x, dtype=np.float64)
+    lx = C.c_double(logLx)
+    cnt = _Counts()
+    cnt.margin = cnt.pmargin = cnt.bmargin = np.inf
+    lib().orc_rw_step(C.byref(pb.s), _d(L), float(scale), float(logLstar), int(seed), int(run_id), int(it),
+                      int(chain), int(step), _d(x), C.byref(lx), C.byref(cnt))
     return x, lx.value, {f: getattr(cnt, f) for f, _ in _Counts._fields_}
 
 

@@ -86,6 +86,8 @@ typedef struct {
     int max_iter;
     uint64_t seed;
     uint32_t run_id;
+    int kernel;          /* 0: HRSS (Sec. 3.2); 1: constrained random walk     */
+    double rw_scale;     /* random-walk proposal x + s L z; 0 = 2.38 / sqrt(d) */
 } orc_opts;
 
 typedef struct {
@@ -594,6 +596,46 @@ void orc_hrss_step(const orc_problem *pb, const double *L, double w, int dir_nor
     free(z); free(v); free(y);
 }
 
+/* Constrained Gaussian random walk (the baseline replacement kernel of
+   Sec. 3.1 and App. "Slice sampling vs random walk"): one proposal
+   y = x + s L z per step, z ~ N(0, I) from the step's normal words, L the
+   live-set Cholesky factor (proposal covariance s^2 L L^T, matched to the
+   live set).  y replaces x when it is in the prior support, above logL*,
+   and, for a Gaussian prior, passes the Metropolis test
+   ln u < log Pi(y) - log Pi(x) with u the step's word 2 ceil(d/2);
+   otherwise the chain stays (a null move). */
+void orc_rw_step(const orc_problem *pb, const double *L, double scale, double logLstar,
+                 uint64_t seed, uint32_t run_id, uint32_t iter, uint32_t chain, uint32_t step,
+                 double *x, double *logLx, orc_counts *cnt)
+{
+    int d = pb->d;
+    uint32_t key[2];
+    orc_key(seed, run_id, key);
+    uint32_t nz = 2u * (uint32_t)((d + 1) / 2);
+    double *z = (double *)malloc(sizeof(double) * d);
+    double *y = (double *)malloc(sizeof(double) * d);
+    orc_normals(key, iter, chain, step, d, z);
+    for (int a = 0; a < d; ++a) {
+        double s = 0.0;
+        for (int b = 0; b <= a; ++b) s += L[a * d + b] * z[b];
+        y[a] = x[a] + scale * s;
+    }
+    orc_slice sl;
+    sl.pb = pb; sl.logLstar = logLstar; sl.cnt = cnt; sl.y = y;
+    sl.nonflat = pb->prior_kind != ORC_PRIOR_BOX;
+    sl.height = 0.0;
+    if (sl.nonflat) sl.height = orc_log_prior(pb, x) + log(orc_u24(orc_word(key, iter, chain, step, nz)));
+    double lly;
+    if (orc_in_slice(&sl, y, &lly)) {
+        memcpy(x, y, sizeof(double) * d);
+        *logLx = lly;
+        cnt->accepts++;
+    } else {
+        cnt->nulls++;
+    }
+    free(z); free(y);
+}
+
 /* ------------------------------------------------------------------------ */
 /* One outer iteration (Sec. 3.1 (i)-(iv); Algorithm 1).  The live set is    */
 /* x [m][d], logL [m], birth [m]; the dead points of this iteration are      */
@@ -646,9 +688,15 @@ int orc_step(const orc_problem *pb, const orc_opts *op, uint32_t iter,
         double *xj = nx + (size_t)j * d;
         memcpy(xj, x + (size_t)parent[j] * d, sizeof(double) * d);
         double lj = logL[parent[j]];
-        for (int s = 0; s < op->p; ++s)
-            orc_hrss_step(pb, L, op->w, op->dir_norm, logLstar, op->seed, op->run_id,
-                          iter, (uint32_t)j, (uint32_t)s, xj, &lj, &cnt);
+        double rws = op->rw_scale > 0.0 ? op->rw_scale : 2.38 / sqrt((double)d);
+        for (int s = 0; s < op->p; ++s) {
+            if (op->kernel == 1)
+                orc_rw_step(pb, L, rws, logLstar, op->seed, op->run_id, iter, (uint32_t)j, (uint32_t)s,
+                            xj, &lj, &cnt);
+            else
+                orc_hrss_step(pb, L, op->w, op->dir_norm, logLstar, op->seed, op->run_id,
+                              iter, (uint32_t)j, (uint32_t)s, xj, &lj, &cnt);
+        }
         nl[j] = lj;
         if (evals_total) *evals_total += cnt.evals;
         if (tr) {

@@ -305,6 +305,12 @@ nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m
   if (o.n_sim < 2 || o.n_sim > 1024) return set_err(c, NSS_ERR_ARG, "run %d: n_sim outside [2,1024]", run);
   if (!(o.cov_eps >= 0)) return set_err(c, NSS_ERR_ARG, "run %d: cov_eps < 0", run);
   if (o.dead_capacity < 0) return set_err(c, NSS_ERR_ARG, "run %d: dead_capacity < 0", run);
+  if (o.kernel != NSS_KERNEL_HRSS && o.kernel != NSS_KERNEL_RW) return set_err(c, NSS_ERR_ARG, "run %d: unknown kernel", run);
+  if (o.kernel == NSS_KERNEL_RW) {
+    if (!(o.rw_scale >= 0) || !std::isfinite(o.rw_scale)) return set_err(c, NSS_ERR_ARG, "run %d: rw_scale < 0", run);
+    if (lk.kind == NSS_LOGLIK_LOGREG || lk.kind == NSS_LOGLIK_GP_RBF_WHITE)
+      return set_err(c, NSS_ERR_ARG, "run %d: the random-walk kernel takes Gaussian, mixture or flat likelihoods", run);
+  }
   if (o.sweep_cfg >= 0) {
     bool fits = false;
     for (int q : candidate_cfgs(pr.d)) fits |= (q == o.sweep_cfg);
@@ -899,6 +905,8 @@ void nss_options_default(nss_options* o) {
   o->cov_eps = 1e-6;
   o->cuda_stream = nullptr;
   o->sweep_cfg = -1;
+  o->kernel = NSS_KERNEL_HRSS;
+  o->rw_scale = 0.0;
 }
 
 int nss_abi_version(void) { return NSS_ABI_VERSION; }
@@ -1047,6 +1055,8 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     R.fault_mode = lk.fault_mode;
     R.fault_param = (float)lk.fault_param;
     R.max_iter = o.max_iter;
+    R.kernel = o.kernel;
+    R.rw_scale = (float)(o.rw_scale > 0 ? o.rw_scale : 2.38 / std::sqrt((double)R.d));
     double w = o.w;
     if (o.w_rule == NSS_W_THEORY) {
       if (kappa < 0) kappa = kappa_inf_host();

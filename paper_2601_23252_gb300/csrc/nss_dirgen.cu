@@ -100,7 +100,7 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
     }
 #pragma unroll
     for (int i = 0; i < kReg; ++i) dd = fmaf(z[i], z[i], dd);
-    const float inrm = rsqrtf(R.dir_norm == 0 ? zz : dd);
+    const float inrm = R.kernel == kKernelRw ? 1.0f : rsqrtf(R.dir_norm == 0 ? zz : dd);  // RW: L z itself
 #pragma unroll
     for (int b = 0; b < kReg / 4; ++b)
       if (4 * b < ld) out[b] = make_float4(z[4 * b] * inrm, z[4 * b + 1] * inrm, z[4 * b + 2] * inrm, z[4 * b + 3] * inrm);
@@ -135,7 +135,7 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
       z[r] = acc + t;
       dd = fmaf(z[r], z[r], dd);
     }
-    const float inrm = rsqrtf(R.dir_norm == 0 ? zz : dd);
+    const float inrm = R.kernel == kKernelRw ? 1.0f : rsqrtf(R.dir_norm == 0 ? zz : dd);  // RW: L z itself
     for (int b = 0; 4 * b < ld; ++b)
       out[b] = make_float4(z[4 * b] * inrm, z[4 * b + 1] * inrm, z[4 * b + 2] * inrm, z[4 * b + 3] * inrm);
   }

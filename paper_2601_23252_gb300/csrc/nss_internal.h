@@ -23,6 +23,7 @@ constexpr int kStepWords = 12;      // a step's scalar words drawn ahead: U, hei
 constexpr int kVolTile = 1024;      // dead points per volume-simulation tile
 
 enum PriorKind { kPriorBox = 0, kPriorGauss = 1 };
+enum KernelKind { kKernelHrss = 0, kKernelRw = 1 };
 enum LikKind { kLikGauss = 0, kLikGmm = 1, kLikLogreg = 2, kLikGp = 3, kLikFlat = 4, kLikFault = 5 };
 
 struct RunDesc {
@@ -30,6 +31,8 @@ struct RunDesc {
   int prior_kind, lik_kind, n_comp, n_data;
   int dir_norm, cfg;                // cfg: sweep configuration (G lanes x DPL dims)
   int fault_mode, max_iter;
+  int kernel;                       // kKernelHrss / kKernelRw
+  float rw_scale;                   // RW proposal scale s (x + s L z)
   float w, cov_eps, fault_param;
   float inv2s2, lognorm;            // Gaussian / mixture constants
   float prior_const;                // Gaussian prior: sum(-log b - log(2 pi)/2)

@@ -158,7 +158,9 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       P0 = gsum<G>(P0, mask);
       P1 = gsum<G>(P1, mask);
       P2 = gsum<G>(P2, mask);
-      const float uh = u24(wH);
+      // HRSS: slice height log Pi(x) + ln u (word nz + 1); RW: the Metropolis
+      // threshold log Pi(x) + ln u with u = word nz
+      const float uh = u24(R.kernel == kKernelRw ? wU : wH);
       height = fmaf(-0.5f, P0, R.prior_const) + logf(uh);
     }
     float x0 = 0.0f, v0 = 0.0f;  // coordinate 0 for the fault likelihood
@@ -203,6 +205,25 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       }
       return ll > lstar;
     };
+    if (R.kernel == kKernelRw) {
+      // constrained random walk: one proposal y = x + s (L z), the line point
+      // t = s; accepted under the same support / prior / logL* test
+      const float ts = R.rw_scale;
+      bool isn = false;
+      float ll = 0.0f;
+      const bool in = probe(ts, ll, isn);
+      ++evals;
+      if (isn) ++nanc;
+      if (in) {
+#pragma unroll
+        for (int i = 0; i < DPL; ++i) x[i] = fmaf(ts, v[i], x[i]);
+        lx = ll;
+        ++acc;
+      } else {
+        ++nul;
+      }
+      continue;
+    }
     // Stepping out: an end moves by repeated FP32 steps of +-w while the
     // slice test at it passes, at most kStepOutCap tests per side; index
     // kStepOutCap of a side is a stop that is never tested (the cap).  The

@@ -122,7 +122,8 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
       }
       return pick(cw, wi & 3u);
     };
-    if (nonflat) height = fmaf(-0.5f, P0, R.prior_const) + logf(u24(word(nz + 1u)));
+    // HRSS: slice height (word nz + 1); RW: Metropolis threshold (word nz)
+    if (nonflat) height = fmaf(-0.5f, P0, R.prior_const) + logf(u24(word(R.kernel == kKernelRw ? nz : nz + 1u)));
     auto in_slice = [&](float t, float& ll) -> bool {
       ++evals;
       if (box && !(t >= t_lo && t <= t_hi)) return false;
@@ -157,6 +158,20 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
       }
       return ll > lstar;
     };
+    if (R.kernel == kKernelRw) {
+      // constrained random walk: one proposal at the line point t = s
+      const float ts = R.rw_scale;
+      float ll = 0.0f;
+      if (in_slice(ts, ll)) {
+#pragma unroll
+        for (int i = 0; i < DMAX; ++i) x[i] = fmaf(ts, v[i], x[i]);
+        lx = ll;
+        ++acc;
+      } else {
+        ++nul;
+      }
+      continue;
+    }
     const float U = u24(word(nz));
     float tl = -w * U, tr = tl + w, lly = 0.0f;
     for (int n = 0;; ++n) {

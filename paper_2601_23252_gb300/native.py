@@ -44,7 +44,8 @@ class Options(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("run_id", C.c_uint32), ("w", C.c_double), ("w_rule", C.c_int),
                 ("dir_norm", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("dead_capacity", C.c_longlong), ("n_sim", C.c_int), ("cov_eps", C.c_double),
-                ("cuda_stream", C.c_void_p), ("sweep_cfg", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("sweep_cfg", C.c_int), ("kernel", C.c_int),
+                ("rw_scale", C.c_double)]
 
 
 class StepInfo(C.Structure):

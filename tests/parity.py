@@ -30,6 +30,10 @@ def oracle_problem(wl):
 
 
 def oracle_opts(wl, **kw):
+    o = (wl.extra or {}).get("options", {})
+    for key in ("kernel", "rw_scale"):
+        if key in o and key not in kw:
+            kw[key] = o[key]
     return O.make_opts(wl.n_live, wl.k, wl.p, seed=wl.seed, run_id=wl.run_id, w=wl.w, tol=wl.tol, **kw)
 
 

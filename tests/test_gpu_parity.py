@@ -29,6 +29,10 @@ def _wl(name, seed):
                           sigma=0.05, mu=np.full((1, d), 0.4), seed=seed)
     if name == "gauss20":
         return W.gauss20_paper(seed=seed, n_live=256, k=100).with_(p=10)
+    if name.startswith("rw_"):
+        base = _wl(name[3:], seed)
+        opts = dict((base.extra or {}).get("options", {}), kernel=1)
+        return base.with_(p=3 * base.p, extra=dict(base.extra or {}, options=opts))
     if name in ("gmm_d10_k3", "gmm_d20_k6"):
         d, K = (10, 3) if name == "gmm_d10_k3" else (20, 6)
         mu = np.random.default_rng(seed + 100).uniform(0.2, 0.8, size=(K, d))
@@ -53,12 +57,17 @@ def test_initial_live_set_matches_checker(gpu_lib, name):
 
 @pytest.mark.parametrize("name,seed,warm", [
     ("gauss_d2", 1, 1), ("gauss_d2", 2, 6), ("gauss_d5_odd", 4, 3), ("gmm_d32_small", 5, 4),
-    ("gmm_d32", 0, 3), ("gmm_d32", 7, 25), ("gauss20", 2, 5), ("gmm_d10_k3", 3, 4), ("gmm_d20_k6", 6, 4)])
+    ("gmm_d32", 0, 3), ("gmm_d32", 7, 25), ("gauss20", 2, 5), ("gmm_d10_k3", 3, 4), ("gmm_d20_k6", 6, 4),
+    ("rw_gauss_d5_odd", 4, 3), ("rw_gmm_d32_small", 5, 4), ("rw_gauss20", 2, 5)])
 def test_one_step_parity(gpu_lib, name, seed, warm):
     wl = _wl(name, seed)
     rep = compare_step(wl, warm)
     g, t = rep["gpu"], rep["orc"]
     key = wl.name if wl.name in ("gauss_d2", "gmm_d32", "gauss20") else "gmm_d32"
+    if name.startswith("rw_"):
+        # a random-walk step is one proposal: no bracket, no shrinkage
+        assert np.all(g["expansions"] == 0) and np.all(g["shrinks"] == 0)
+        assert np.array_equal(g["evals"], np.full(wl.k, wl.p))
     # (i) selection and threshold: bit-exact
     assert np.array_equal(g["dead_idx"], t["dead_idx"])
     assert g["logLstar"] == np.float32(t["logLstar"])

@@ -190,3 +190,20 @@ def test_export_import_resume_is_bit_identical(gpu_lib):
         got = b.export_state()
     assert np.array_equal(ref["x"], got["x"]) and np.array_equal(ref["logL"], got["logL"])
     assert ref["logZ"] == got["logZ"] and ref["logX"] == got["logX"]
+
+
+def test_random_walk_runs_against_closed_form(gpu_lib):
+    """The constrained random-walk kernel (kernel = 1) on gauss_d2 with p = 40:
+    evidence within its error of the closed form over 8 seeds; every step
+    costs exactly one evaluation."""
+    wls = [W.gauss_d2(seed=s).with_(run_id=s, p=40, extra={"options": {"kernel": 1}}) for s in range(8)]
+    truth = box_gauss_logZ(wls[0].mu[0], wls[0].sigma, wls[0].a, wls[0].b)
+    with native.Sampler(wls) as smp:
+        res = smp.run()
+    dev = np.array([(r["logZ"] - truth) / r["logZ_err"] for r in res])
+    print(f"\nrandom walk gauss_d2: dev/err {np.round(dev, 2)}, evals per dead point "
+          f"{np.mean([r['evals'] / r['n_dead'] for r in res]):.1f}")
+    assert np.all(np.abs(dev) < 4.0)
+    assert abs(dev.mean()) < 3.0 / np.sqrt(len(wls)) + 0.3
+    for r in res:
+        assert r["spec_evals"] == 0

@@ -212,6 +212,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       bool isn = false;
       float ll = 0.0f;
       const bool in = probe(ts, ll, isn);
+      if (gl != 0) --ran;  // the group's lanes test the same point: one test
       ++evals;
       if (isn) ++nanc;
       if (in) {

@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NSS_ABI_VERSION 3
+#define NSS_ABI_VERSION 4
 
 typedef struct nss_ctx nss_ctx;
 
@@ -91,6 +91,11 @@ typedef struct {
  *   TEST_FAULT      isotropic Gaussian whose value is replaced by NaN
  *                   (fault_mode 1) or +inf (fault_mode 2) where x_0 <
  *                   fault_param; NaN is read as -inf and counted.
+ *   RASTRIGIN       the Gaussian-Rastrigin mixture of App. F.3 (unnormalised):
+ *                   L = alpha exp(-|x|^2/2)
+ *                       + (1 - alpha) exp(-A d + A sum_i cos(2 pi x_i)), A = 10;
+ *                   0 <= alpha <= 1 in `alpha`.  Its slice tests evaluate the
+ *                   cosine sum per test (it is not affine along a line).
  * All pointers are host pointers, copied at create. */
 enum {
     NSS_LOGLIK_GAUSS_ISO = 0,
@@ -98,7 +103,8 @@ enum {
     NSS_LOGLIK_LOGREG = 2,
     NSS_LOGLIK_GP_RBF_WHITE = 3,
     NSS_LOGLIK_FLAT = 4,
-    NSS_LOGLIK_TEST_FAULT = 5
+    NSS_LOGLIK_TEST_FAULT = 5,
+    NSS_LOGLIK_RASTRIGIN = 6
 };
 typedef struct {
     int kind;
@@ -112,6 +118,7 @@ typedef struct {
     const double *gp_y;
     int fault_mode;
     double fault_param;
+    double alpha;              /* RASTRIGIN mixture weight                      */
 } nss_loglik;
 
 /* Direction normalisation: MAHAL v = L z / |z| (unit Mahalanobis length, the

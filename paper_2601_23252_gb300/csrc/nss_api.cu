@@ -282,6 +282,9 @@ nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m
       break;
     case NSS_LOGLIK_FLAT:
       break;
+    case NSS_LOGLIK_RASTRIGIN:
+      if (!(lk.alpha >= 0.0 && lk.alpha <= 1.0)) return set_err(c, NSS_ERR_ARG, "run %d: Rastrigin alpha outside [0,1]", run);
+      break;
     case NSS_LOGLIK_LOGREG:
       if (!lk.X || !lk.y || lk.n_data < 1 || lk.n_data > 20 * 512)
         return set_err(c, NSS_ERR_ARG, "run %d: logistic regression needs X, y and 1 <= n_data <= 10240", run);
@@ -1056,6 +1059,13 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     R.fault_param = (float)lk.fault_param;
     R.max_iter = o.max_iter;
     R.kernel = o.kernel;
+    if (lk.kind == NSS_LOGLIK_RASTRIGIN) {
+      // the Gaussian part exp(-|x|^2/2) through the line coefficients (mean 0, sigma 1)
+      R.inv2s2 = 0.5f;
+      R.lognorm = 0.0f;
+      R.ras_la = lk.alpha > 0.0 ? (float)std::log(lk.alpha) : -INFINITY;
+      R.ras_l1a = lk.alpha < 1.0 ? (float)std::log1p(-lk.alpha) : -INFINITY;
+    }
     R.rw_scale = (float)(o.rw_scale > 0 ? o.rw_scale : 2.38 / std::sqrt((double)R.d));
     double w = o.w;
     if (o.w_rule == NSS_W_THEORY) {

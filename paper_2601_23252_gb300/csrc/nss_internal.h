@@ -24,7 +24,7 @@ constexpr int kVolTile = 1024;      // dead points per volume-simulation tile
 
 enum PriorKind { kPriorBox = 0, kPriorGauss = 1 };
 enum KernelKind { kKernelHrss = 0, kKernelRw = 1 };
-enum LikKind { kLikGauss = 0, kLikGmm = 1, kLikLogreg = 2, kLikGp = 3, kLikFlat = 4, kLikFault = 5 };
+enum LikKind { kLikGauss = 0, kLikGmm = 1, kLikLogreg = 2, kLikGp = 3, kLikFlat = 4, kLikFault = 5, kLikRastrigin = 6 };
 
 struct RunDesc {
   int d, dpad, m, k, p, m2;         // m2: power of two >= m for the sort
@@ -32,6 +32,7 @@ struct RunDesc {
   int dir_norm, cfg;                // cfg: sweep configuration (G lanes x DPL dims)
   int fault_mode, max_iter;
   int kernel;                       // kKernelHrss / kKernelRw
+  float ras_la, ras_l1a;            // Rastrigin mixture: ln alpha, ln(1 - alpha)
   float rw_scale;                   // RW proposal scale s (x + s L z)
   float w, cov_eps, fault_param;
   float inv2s2, lognorm;            // Gaussian / mixture constants

@@ -42,6 +42,21 @@ struct Lik {
                                         int gl, bool has, unsigned mask) const {
     const int lk = R.lik_kind;
     if (lk == kLikFlat) return 0.0f;
+    if (lk == kLikRastrigin) {
+      // App. F.3: alpha exp(-|y|^2/2) + (1 - alpha) exp(-A d + A sum cos(2 pi y_i)), A = 10
+      float q = 0.0f, cs = 0.0f;
+#pragma unroll
+      for (int i = 0; i < DPL; ++i)
+        if (has && gl * DPL + i < R.d) {
+          q = fmaf(y[i], y[i], q);
+          cs += cospif(2.0f * y[i]);
+        }
+      q = gsum<G>(q, mask);
+      cs = gsum<G>(cs, mask);
+      const float a1 = R.ras_la - 0.5f * q, a2 = R.ras_l1a + fmaf(10.0f, cs, -10.0f * (float)R.d);
+      const float hi = fmaxf(a1, a2), lo = fminf(a1, a2);
+      return (hi == -INFINITY) ? -INFINITY : hi + log1pf(expf(lo - hi));
+    }
     if (lk == kLikGauss || lk == kLikFault) {
       const float q = gsum<G>(has ? sqdist(y, mu4[0]) : 0.0f, mask);
       float ll = fmaf(-q, R.inv2s2, R.lognorm);

@@ -43,7 +43,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   const float lstar = Sw->logLstar;
   const bool box = R.prior_kind == kPriorBox, nonflat = !box;
   const int lk = R.lik_kind;
-  const int K = (lk == kLikGmm) ? R.n_comp : ((lk == kLikGauss || lk == kLikFault) ? 1 : 0);
+  const int K = (lk == kLikGmm) ? R.n_comp : ((lk == kLikGauss || lk == kLikFault || lk == kLikRastrigin) ? 1 : 0);
   bool own[DPL];
 #pragma unroll
   for (int i = 0; i < DPL; ++i) own[i] = gl * DPL + i < d;
@@ -205,6 +205,93 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       }
       return ll > lstar;
     };
+    if (lk == kLikRastrigin) {
+      // The Rastrigin mixture (App. F.3) is not affine along the line: every
+      // test sums cos(2 pi y_i) over the group's dimensions (the Gaussian part
+      // comes from the line coefficients), so the tests run one at a time.
+      auto test = [&](float t, float& ll, bool& isn) -> bool {
+        if (gl == 0) ++ran;
+        if (box && !(t >= t_lo && t <= t_hi)) return false;
+        if (nonflat) {
+          const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
+          if (!(lp > height)) return false;
+        }
+        float cs = 0.0f;
+#pragma unroll
+        for (int i = 0; i < DPL; ++i)
+          if (own[i]) cs += cospif(2.0f * fmaf(t, v[i], x[i]));
+        cs = gsum<G>(cs, mask);
+        const float lf = -0.5f * fmaf(t, fmaf(t, Cv, 2.0f * Ec[0]), Dc[0]);
+        const float lg = fmaf(10.0f, cs, -10.0f * (float)d);
+        const float a1 = R.ras_la + lf, a2 = R.ras_l1a + lg;
+        const float hi = fmaxf(a1, a2), lo = fminf(a1, a2);
+        ll = (hi == -INFINITY) ? -INFINITY : hi + log1pf(expf(lo - hi));
+        if (isnan(ll)) {
+          ll = -INFINITY;
+          isn = true;
+        }
+        return ll > lstar;
+      };
+      if (R.kernel == kKernelRw) {
+        bool isn = false;
+        float ll = 0.0f;
+        const bool in = test(R.rw_scale, ll, isn);
+        ++evals;
+        if (isn) ++nanc;
+        if (in) {
+#pragma unroll
+          for (int i = 0; i < DPL; ++i) x[i] = fmaf(R.rw_scale, v[i], x[i]);
+          lx = ll;
+          ++acc;
+        } else {
+          ++nul;
+        }
+        continue;
+      }
+      const float tl0 = -w * u24(wU);
+      float ends[2] = {tl0, tl0 + w};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float delta = q ? w : -w;
+        float t = ends[q];
+        int n = 0;
+        for (; n < kStepOutCap; ++n) {
+          bool isn = false;
+          float ll = 0.0f;
+          const bool in = test(t, ll, isn);
+          if (isn) ++nanc;
+          if (!in) break;
+          t += delta;
+        }
+        ends[q] = t;
+        evals += min(n + 1, kStepOutCap);
+        exps += n;
+        if (n == kStepOutCap) ++capo;
+      }
+      float tl = ends[0], tr = ends[1];
+      bool ok = false;
+      for (int r = 0; r < kShrinkCap; ++r) {
+        const float t = fmaf(u24(step_word(3u + (uint32_t)r)), tr - tl, tl);
+        ++shr;
+        ++evals;
+        bool isn = false;
+        float ll = 0.0f;
+        const bool in = test(t, ll, isn);
+        if (isn) ++nanc;
+        if (in) {
+#pragma unroll
+          for (int i = 0; i < DPL; ++i) x[i] = fmaf(t, v[i], x[i]);
+          lx = ll;
+          ok = true;
+          break;
+        }
+        if (t < 0.0f) tl = t;
+        else tr = t;
+      }
+      if (ok) ++acc;
+      else ++nul;
+      continue;
+    }
     if (R.kernel == kKernelRw) {
       // constrained random walk: one proposal y = x + s (L z), the line point
       // t = s; accepted under the same support / prior / logL* test

@@ -28,7 +28,7 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
   const float lstar = Sw->logLstar;
   const bool box = R.prior_kind == kPriorBox, nonflat = !box;
   const int lk = R.lik_kind;
-  const int K = (lk == kLikGmm) ? R.n_comp : ((lk == kLikGauss || lk == kLikFault) ? 1 : 0);
+  const int K = (lk == kLikGmm) ? R.n_comp : ((lk == kLikGauss || lk == kLikFault || lk == kLikRastrigin) ? 1 : 0);
   float x[DMAX];
   {
     const float4* xp = reinterpret_cast<const float4*>(f + R.o_x + (long long)parent * ld);
@@ -151,6 +151,17 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
         }
         if (lk == kLikFault && fmaf(t, v[0], x[0]) < R.fault_param)
           ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
+        if (lk == kLikRastrigin) {
+          // App. F.3 mixture: the Gaussian part above (mean 0, sigma 1), the
+          // cosine sum over the lane's dimensions
+          float cs = 0.0f;
+#pragma unroll
+          for (int i = 0; i < DMAX; ++i)
+            if (i < d) cs += cospif(2.0f * fmaf(t, v[i], x[i]));
+          const float a1 = R.ras_la + ll, a2 = R.ras_l1a + fmaf(10.0f, cs, -10.0f * (float)d);
+          const float hi = fmaxf(a1, a2), lo = fminf(a1, a2);
+          ll = (hi == -INFINITY) ? -INFINITY : hi + log1pf(expf(lo - hi));
+        }
       }
       if (isnan(ll)) {
         ll = -INFINITY;

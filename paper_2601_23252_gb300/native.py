@@ -22,7 +22,7 @@ STATUS = {0: "ok", 1: "done", -1: "invalid argument", -2: "CUDA error", -3: "out
           -4: "dead-point store full", -5: "iteration cap reached", -6: "non-finite evidence",
           -7: "call out of order"}
 PRIOR = {"box": 0, "gauss": 1}
-LOGLIK = {"gauss": 0, "gmm": 1, "logreg": 2, "gp": 3, "flat": 4, "fault": 5}
+LOGLIK = {"gauss": 0, "gmm": 1, "logreg": 2, "gp": 3, "flat": 4, "fault": 5, "rastrigin": 6}
 K_NAMES = ["init", "prologue", "sweep", "terminate", "final_sort", "volsim", "weights", "other"]
 
 _dp = C.POINTER(C.c_double)
@@ -37,7 +37,7 @@ class Prior(C.Structure):
 class Loglik(C.Structure):
     _fields_ = [("kind", C.c_int), ("n_comp", C.c_int), ("n_data", C.c_int), ("sigma", C.c_double),
                 ("mu", _dp), ("X", _fp), ("y", _fp), ("gp_t", _dp), ("gp_y", _dp),
-                ("fault_mode", C.c_int), ("fault_param", C.c_double)]
+                ("fault_mode", C.c_int), ("fault_param", C.c_double), ("alpha", C.c_double)]
 
 
 class Options(C.Structure):
@@ -170,6 +170,8 @@ class _Spec:
             y = np.ascontiguousarray(wl.y, dtype=np.float64)
             self.keep += [t, y]
             lk.gp_t, lk.gp_y, lk.n_data = t.ctypes.data_as(_dp), y.ctypes.data_as(_dp), t.size
+        if wl.lik == "rastrigin":
+            lk.alpha = float(wl.extra.get("alpha", 0.5))
         if wl.lik == "fault":
             lk.fault_mode = int(wl.extra.get("fault_mode", 1))
             lk.fault_param = float(wl.extra.get("fault_param", 0.0))

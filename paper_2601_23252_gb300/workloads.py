@@ -68,6 +68,8 @@ class Workload:
             kw["X"], kw["y"] = self.X.astype(np.float64), self.y.astype(np.float64)
         if self.lik == "gp":
             kw["t"], kw["y"] = self.t, self.y
+        if self.lik == "rastrigin":
+            kw["alpha"] = float(self.extra.get("alpha", 0.5))
         return kw
 
 
@@ -115,6 +117,14 @@ def gp_d3(seed: int = 0, run_id: int = 0, n: int = 256) -> Workload:
     b = np.log(np.array([10.0, 10.0, 1.0]))
     return Workload("gp_d3", 3, "box", a, b, "gp", 500, 250, 15, t=t, y=y, seed=seed,
                     run_id=run_id)
+
+
+def rastrigin_mix(d: int, alpha: float = 0.5, seed: int = 0, run_id: int = 0, n_live: int = 500,
+                  k: int = 250) -> Workload:
+    """Gaussian-Rastrigin mixture of App. F.3 on the box [-5.14, 5.14]^d, p = 3d."""
+    r = 5.14
+    return Workload("rastrigin", d, "box", np.full(d, -r), np.full(d, r), "rastrigin", n_live, k, 3 * d,
+                    seed=seed, run_id=run_id, extra={"alpha": float(alpha)})
 
 
 def batch64(seed: int = 0, n_runs: int = 64) -> list[Workload]:

@@ -29,6 +29,8 @@ def _wl(name, seed):
                           sigma=0.05, mu=np.full((1, d), 0.4), seed=seed)
     if name == "gauss20":
         return W.gauss20_paper(seed=seed, n_live=256, k=100).with_(p=10)
+    if name == "rastrigin_d5":
+        return W.rastrigin_mix(5, alpha=0.5, seed=seed, n_live=200, k=100).with_(p=15)
     if name.startswith("rw_"):
         base = _wl(name[3:], seed)
         opts = dict((base.extra or {}).get("options", {}), kernel=1)
@@ -58,12 +60,15 @@ def test_initial_live_set_matches_checker(gpu_lib, name):
 @pytest.mark.parametrize("name,seed,warm", [
     ("gauss_d2", 1, 1), ("gauss_d2", 2, 6), ("gauss_d5_odd", 4, 3), ("gmm_d32_small", 5, 4),
     ("gmm_d32", 0, 3), ("gmm_d32", 7, 25), ("gauss20", 2, 5), ("gmm_d10_k3", 3, 4), ("gmm_d20_k6", 6, 4),
-    ("rw_gauss_d5_odd", 4, 3), ("rw_gmm_d32_small", 5, 4), ("rw_gauss20", 2, 5)])
+    ("rw_gauss_d5_odd", 4, 3), ("rw_gmm_d32_small", 5, 4), ("rw_gauss20", 2, 5),
+    ("rastrigin_d5", 3, 4), ("rw_rastrigin_d5", 3, 4)])
 def test_one_step_parity(gpu_lib, name, seed, warm):
     wl = _wl(name, seed)
     rep = compare_step(wl, warm)
     g, t = rep["gpu"], rep["orc"]
     key = wl.name if wl.name in ("gauss_d2", "gmm_d32", "gauss20") else "gmm_d32"
+    if name == "rastrigin_d5":
+        return W.rastrigin_mix(5, alpha=0.5, seed=seed, n_live=200, k=100).with_(p=15)
     if name.startswith("rw_"):
         # a random-walk step is one proposal: no bracket, no shrinkage
         assert np.all(g["expansions"] == 0) and np.all(g["shrinks"] == 0)
@@ -115,7 +120,7 @@ def test_one_step_parity(gpu_lib, name, seed, warm):
     assert np.array_equal(gs["x"][keep], rep["x32"][keep])
 
 
-@pytest.mark.parametrize("name", ["gauss_d2", "gauss_d5_odd", "gauss20", "gmm_d32", "gmm_d20_k6"])
+@pytest.mark.parametrize("name", ["gauss_d2", "gauss_d5_odd", "gauss20", "gmm_d32", "gmm_d20_k6", "rastrigin_d5"])
 def test_one_step_parity_every_sweep_configuration(gpu_lib, name):
     """Every (lanes per chain, dims per lane) configuration that fits d gives
     the same selection and parents and counters matching the checker; d = 5

@@ -6,7 +6,7 @@ import pytest
 from scipy import special, stats
 
 import oracle as O
-from closed_forms import box_gauss_logZ, box_gmm_logZ
+from closed_forms import box_gauss_logZ, box_gmm_logZ, rastrigin_logZ
 from paper_2601_23252_gb300 import native
 from paper_2601_23252_gb300 import workloads as W
 from conftest import golden_path
@@ -207,3 +207,17 @@ def test_random_walk_runs_against_closed_form(gpu_lib):
     assert abs(dev.mean()) < 3.0 / np.sqrt(len(wls)) + 0.3
     for r in res:
         assert r["spec_evals"] == 0
+
+
+@pytest.mark.parametrize("d", [2, 5])
+def test_rastrigin_mixture_against_quadrature(gpu_lib, d):
+    """App. F.3 test likelihood (Gaussian + Rastrigin mixture, alpha = 0.5,
+    box [-5.14, 5.14]^d): evidence against the semi-analytic quadrature."""
+    wls = [W.rastrigin_mix(d, alpha=0.5, seed=s, run_id=s) for s in range(6)]
+    truth = rastrigin_logZ(0.5, d)
+    with native.Sampler(wls) as smp:
+        res = smp.run()
+    dev = np.array([(r["logZ"] - truth) / r["logZ_err"] for r in res])
+    print(f"\nrastrigin d={d}: truth {truth:.4f}, logZ {np.mean([r['logZ'] for r in res]):.4f}, dev/err {np.round(dev, 2)}")
+    assert np.all(np.abs(dev) < 4.0)
+    assert abs(dev.mean()) < 3.0 / np.sqrt(len(wls)) + 0.4

@@ -67,8 +67,6 @@ def test_one_step_parity(gpu_lib, name, seed, warm):
     rep = compare_step(wl, warm)
     g, t = rep["gpu"], rep["orc"]
     key = wl.name if wl.name in ("gauss_d2", "gmm_d32", "gauss20") else "gmm_d32"
-    if name == "rastrigin_d5":
-        return W.rastrigin_mix(5, alpha=0.5, seed=seed, n_live=200, k=100).with_(p=15)
     if name.startswith("rw_"):
         # a random-walk step is one proposal: no bracket, no shrinkage
         assert np.all(g["expansions"] == 0) and np.all(g["shrinks"] == 0)

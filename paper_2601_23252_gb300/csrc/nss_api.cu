@@ -495,9 +495,7 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
       c->launches += 5 + 3LL * R.p;
     }
   }
-  bool any_term = false;  // runs whose termination test is not in their sweep
-  for (int r = r0; r < r0 + nr; ++r) any_term |= !c->desc[r].term_in_sweep;
-  if (any_term) {
+  {
     Rec r(c, NSS_K_TERMINATE);
     CK(nss::launch_terminate(D, r0, nr, st), "terminate launch");
   }
@@ -1061,7 +1059,6 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
     R.fault_param = (float)lk.fault_param;
     R.max_iter = o.max_iter;
     R.kernel = o.kernel;
-    R.term_in_sweep = (lk.kind != NSS_LOGLIK_LOGREG && lk.kind != NSS_LOGLIK_GP_RBF_WHITE) ? 1 : 0;
     if (lk.kind == NSS_LOGLIK_RASTRIGIN) {
       // the Gaussian part exp(-|x|^2/2) through the line coefficients (mean 0, sigma 1)
       R.inv2s2 = 0.5f;

@@ -243,49 +243,4 @@ __device__ __forceinline__ double logaddexp_d(double a, double b) {
   return m + log1p(exp(-fabs(a - b)));
 }
 
-// Termination test after an iteration (App. B.3, live-fraction reading):
-// Z_live = X mean(L_live), stop when Z_live / (Z + Z_live) < tol; counts the
-// iteration.  Run by one whole warp; the live logL are read past L1 (other
-// blocks wrote them in this kernel).
-__device__ __forceinline__ void warp_terminate(const RunDesc& R, RunState& S, const float* logL) {
-  const int lane = threadIdx.x & 31;
-  double mx = -INFINITY;
-  for (int i = lane; i < R.m; i += 32) mx = fmax(mx, (double)__ldcg(logL + i));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  double s = 0.0;
-  if (mx > -INFINITY)
-    for (int i = lane; i < R.m; i += 32) s += (double)expf((float)((double)__ldcg(logL + i) - mx));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) {
-    const double lzl = (mx > -INFINITY) ? S.logX + mx + log(s) - log((double)R.m) : -INFINITY;
-    const double tot = logaddexp_d(S.logZ, lzl);
-    const bool stop = (lzl - tot) < log(R.tol);
-    S.iter += 1;
-    S.stepped = 1;
-    if (stop) S.done = 1;
-    else if (S.iter >= R.max_iter) { S.done = 1; S.status = -5; }
-    if (!isfinite(S.logZ) && S.logZ != -INFINITY) { S.done = 1; S.status = -6; }
-  }
-}
-
-// After a warp has written its chains of a run: count them; the warp that
-// completes the run's k chains takes the termination test.
-__device__ __forceinline__ void chains_finished(const RunDesc& R, RunState* S, int n_chains, const float* logL) {
-  const int lane = threadIdx.x & 31;
-  int last = 0;
-  __syncwarp();
-  if (lane == 0) {
-    __threadfence();
-    const int old = atomicAdd(&S->chains_done, n_chains);
-    last = (old + n_chains == R.k);
-  }
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (last && R.term_in_sweep) {
-    __threadfence();
-    warp_terminate(R, *S, logL);
-  }
-}
-
 }  // namespace nss

@@ -32,7 +32,6 @@ struct RunDesc {
   int dir_norm, cfg;                // cfg: sweep configuration (G lanes x DPL dims)
   int fault_mode, max_iter;
   int kernel;                       // kKernelHrss / kKernelRw
-  int term_in_sweep;                // the sweep's last warp of the run takes the termination test
   float ras_la, ras_l1a;            // Rastrigin mixture: ln alpha, ln(1 - alpha)
   float rw_scale;                   // RW proposal scale s (x + s L z)
   float w, cov_eps, fault_param;
@@ -65,7 +64,7 @@ struct RunState {
   float logLstar;
   int stepped;                      // at least one iteration since create/import
   int finalised;
-  int chains_done;                  // chains of the iteration's sweep finished (reset by the prologue)
+  int pad_;
   double logZ_mean, logZ_std, lw_norm;
 };
 

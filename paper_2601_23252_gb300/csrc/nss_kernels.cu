@@ -297,7 +297,6 @@ __global__ void __launch_bounds__(kPrologueThreads) k_prologue(Dev D, int run0) 
   int* dead = D.i + R.o_dead;
   for (int j = threadIdx.x; j < k; j += blockDim.x) dead[j] = (int)(keys[j] & 0xffffffffu);
   if (threadIdx.x == 0) {
-    S.chains_done = 0;
     S.logLstar = logL[(int)(keys[k - 1] & 0xffffffffu)];
     cap_fail = (S.n_dead + k > R.dead_cap);
   }
@@ -351,7 +350,7 @@ __global__ void __launch_bounds__(256) k_terminate(Dev D, int run0) {
   const int run = run0 + blockIdx.x;
   const RunDesc& R = D.desc[run];
   RunState& S = D.st[run];
-  if (S.done || R.term_in_sweep) return;  // the sweep's last warp took the test
+  if (S.done) return;
   __shared__ double red[32];
   const float* logL = D.f + R.o_logL;
   double mx = -INFINITY;

@@ -486,8 +486,7 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(
     if (S->done) continue;
     const int j = wi.c0 + grp;
     if (j < wi.c1) sweep_chain<G, DPL, KC>(D, D.desc[wi.run], S, j, gl, mask);
-    const RunDesc& R = D.desc[wi.run];
-    chains_finished(R, S, wi.c1 - wi.c0, D.f + R.o_logL);
+    __syncwarp();
   }
 }
 

@@ -250,8 +250,7 @@ __global__ void __launch_bounds__(kLaneThreads, (DMAX >= 32 ? 8 : 16)) k_sweep_l
     if (S->done) continue;
     const int j = wi.c0 + lane;
     if (j < wi.c1) lane_chain<DMAX, KC>(D, D.desc[wi.run], S, j);
-    const RunDesc& R = D.desc[wi.run];
-    chains_finished(R, S, wi.c1 - wi.c0, D.f + R.o_logL);
+    __syncwarp();
   }
 }
 

@@ -92,9 +92,6 @@ struct nss_ctx {
   int g_r0[kMaxGroups + 1] = {};
   cudaStream_t gstream[kMaxGroups] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[kMaxGroups] = {};
-  // the metric of each group on a second stream, beside the selection
-  cudaStream_t mstream[kMaxGroups] = {};
-  cudaEvent_t m_fork[kMaxGroups] = {}, m_join[kMaxGroups] = {};
   cudaStream_t cur = nullptr;  // stream of the launches being enqueued
   std::vector<WorkItem> init_items[nss::kNumCfgs], sweep_items[kMaxGroups * kLists];
   WorkItem* d_init[nss::kNumCfgs] = {};
@@ -339,9 +336,6 @@ void free_ctx(nss_ctx* c) {
   for (int g = 0; g < nss_ctx::kMaxGroups; ++g) {
     if (c->gstream[g]) cudaStreamDestroy(c->gstream[g]);
     if (c->join_ev[g]) cudaEventDestroy(c->join_ev[g]);
-    if (c->mstream[g]) cudaStreamDestroy(c->mstream[g]);
-    if (c->m_fork[g]) cudaEventDestroy(c->m_fork[g]);
-    if (c->m_join[g]) cudaEventDestroy(c->m_join[g]);
   }
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   cudaFree(c->d_queue);
@@ -458,23 +452,10 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
   nss::Dev D = dev_of(c);
   const int r0 = c->g_r0[g], nr = c->g_r0[g + 1] - r0;
   cudaStream_t st = c->cur;
-  const bool split = c->mstream[g] != nullptr;
-  if (split) {  // metric on the side stream, selection on this one
-    CK(cudaEventRecord(c->m_fork[g], st), "metric fork");
-    CK(cudaStreamWaitEvent(c->mstream[g], c->m_fork[g], 0), "metric fork");
-    c->cur = c->mstream[g];
-    {
-      Rec r(c, NSS_K_PROLOGUE);
-      CK(nss::launch_metric(D, r0, nr, c->prologue_smem, c->mstream[g]), "metric launch");
-    }
-    CK(cudaEventRecord(c->m_join[g], c->mstream[g]), "metric join");
-    c->cur = st;
-  }
   {
     Rec r(c, NSS_K_PROLOGUE);
-    CK(nss::launch_prologue(D, r0, nr, c->prologue_smem, !split, st), "prologue launch");
+    CK(nss::launch_prologue(D, r0, nr, c->prologue_smem, st), "prologue launch");
   }
-  if (split) CK(cudaStreamWaitEvent(st, c->m_join[g], 0), "metric join");
   for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
     const int L = g * nss_ctx::kDirClasses + q;
     if (c->dir_items[L].empty()) continue;
@@ -1251,16 +1232,6 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
       }
     }
     c->g_r0[c->n_groups] = n_runs;
-  }
-  // second streams for the metric kernels (generic batches)
-  for (int g = 0; g < c->n_groups && c->lr.empty() && c->gp.empty(); ++g) {
-    bool generic = true;
-    for (int r = c->g_r0[g]; r < c->g_r0[g + 1]; ++r)
-      generic &= c->desc[r].lik_kind != nss::kLikLogreg && c->desc[r].lik_kind != nss::kLikGp;
-    if (!generic) continue;
-    CKC(cudaStreamCreateWithFlags(&c->mstream[g], cudaStreamNonBlocking), "stream creation");
-    CKC(cudaEventCreateWithFlags(&c->m_fork[g], cudaEventDisableTiming), "event creation");
-    CKC(cudaEventCreateWithFlags(&c->m_join[g], cudaEventDisableTiming), "event creation");
   }
   {
     nss_status sw = build_work(c);

@@ -276,7 +276,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
 // ---------------------------------------------------------------------------
 // Iteration prologue: steps (i), (ii), evidence and metric for one run.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPrologueThreads) k_prologue(Dev D, int run0, int with_metric) {
+__global__ void __launch_bounds__(kPrologueThreads) k_prologue(Dev D, int run0) {
   const int run = run0 + blockIdx.x;
   const RunDesc& R = D.desc[run];
   RunState& S = D.st[run];
@@ -338,19 +338,7 @@ __global__ void __launch_bounds__(kPrologueThreads) k_prologue(Dev D, int run0, 
   evidence_update(R, S, D.f + R.o_dlogL + S.n_dead, D.dd + R.o_cum, D.dd + R.o_lnd, k, red_d);
   if (threadIdx.x == 0) S.n_dead += k;
   __syncthreads();
-  // direction metric from the live set at the start of the iteration (here
-  // when the metric has no kernel of its own on a second stream)
-  if (with_metric) live_metric(D, R, S, smem);
-}
-
-// Direction metric of the live set at the start of the iteration, by itself:
-// it reads only the live positions, so it runs beside the selection.
-__global__ void __launch_bounds__(kPrologueThreads) k_metric(Dev D, int run0) {
-  const int run = run0 + blockIdx.x;
-  const RunDesc& R = D.desc[run];
-  RunState& S = D.st[run];
-  if (S.done) return;
-  extern __shared__ __align__(16) char smem[];
+  // direction metric from the live set at the start of the iteration
   live_metric(D, R, S, smem);
 }
 
@@ -594,18 +582,11 @@ __global__ void k_vol_norm(Dev D, int run) {
 cudaError_t setup_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_metric, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_final_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, bool with_metric, cudaStream_t s) {
-  k_prologue<<<n_runs, kPrologueThreads, smem, s>>>(D, run0, with_metric ? 1 : 0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_metric(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s) {
-  k_metric<<<n_runs, kPrologueThreads, smem, s>>>(D, run0);
+cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s) {
+  k_prologue<<<n_runs, kPrologueThreads, smem, s>>>(D, run0);
   return cudaGetLastError();
 }
 

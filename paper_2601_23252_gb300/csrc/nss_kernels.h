@@ -80,8 +80,7 @@ cudaError_t launch_lr_replace(const Dev& D, const LRArgs& A, int run, int k, cud
 
 cudaError_t launch_init(int cfg, const Dev& D, const WorkItem* items, int n, cudaStream_t s);
 // runs [run0, run0 + n_runs)
-cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, bool with_metric, cudaStream_t s);
-cudaError_t launch_metric(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s);
+cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s);
 // the sweep of configuration cfg for runs of mixture bound kc = sweep_kc(.)
 cudaError_t launch_sweep(int cfg, int kc, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
                          cudaStream_t s);

@@ -42,7 +42,9 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   const uint32_t iter = (uint32_t)Sw->iter;
   const float lstar = Sw->logLstar;
   const bool box = R.prior_kind == kPriorBox, nonflat = !box;
-  const int lk = R.lik_kind;
+  // runs with a mixture bound above 1 are mixture runs (sweep_kc), so their
+  // instantiations compile the mixture likelihood alone
+  const int lk = KC > 1 ? kLikGmm : R.lik_kind;
   const int K = (lk == kLikGmm) ? R.n_comp : ((lk == kLikGauss || lk == kLikFault || lk == kLikRastrigin) ? 1 : 0);
   bool own[DPL];
 #pragma unroll
@@ -54,7 +56,12 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   float lx = f[R.o_logL + parent];
   const float w = R.w;
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
-  int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
+  // Per-chain counters.  Logical evaluations and null moves are not kept:
+  // every step ends in an acceptance or a null move, so nul = p - acc, and
+  // a side that stops after n expansions took min(n + 1, cap) tests, so an
+  // HRSS chain's evals = exps + 2 p - capo + shr (a random-walk chain takes
+  // one test per step: evals = p).
+  int acc = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
   int ran = 0;  // slice tests this lane ran (logical or speculative)
   // the steps' directions, drawn ahead (nss_dirgen.cu); the load of step
   // s + 1's is issued while step s runs
@@ -121,14 +128,24 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
         Dc[c] = c < K ? dq : INFINITY;
       }
     }
-    float t_lo = -INFINITY, t_hi = INFINITY;
-    float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f, height = 0.0f;
+    // support and prior terms of the slice test; a run has either a box
+    // prior (q0, q1 = t_lo, t_hi) or a Gaussian one (q0..q2 = P0..P2, q3 =
+    // the slice height), so the two share registers
+    float q0, q1, q2 = 0.0f, q3 = 0.0f;
+    // the prior's per-dimension a (lower bound / mean) and b (upper bound / sd)
+    float pa[DPL], pb[DPL];
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) pa[i] = pb[i] = 0.0f;
+    if (has) {
+      ldg_lane<DPL>(f + R.o_a, gl, ld, pa);
+      ldg_lane<DPL>(f + R.o_b, gl, ld, pb);
+    }
     if (box) {
+      float t_lo = -INFINITY, t_hi = INFINITY;
 #pragma unroll
       for (int i = 0; i < DPL; ++i) {
         if (own[i]) {
-          const int dim = gl * DPL + i;
-          const float ai = f[R.o_a + dim] - x[i], bi = f[R.o_b + dim] - x[i];
+          const float ai = pa[i] - x[i], bi = pb[i] - x[i];
           const float rv = __frcp_rn(v[i]);
           if (v[i] > 0.0f) {
             t_lo = fmaxf(t_lo, ai * rv);
@@ -141,15 +158,15 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
           }
         }
       }
-      t_lo = gmax<G>(t_lo, mask);
-      t_hi = -gmax<G>(-t_hi, mask);
+      q0 = gmax<G>(t_lo, mask);
+      q1 = -gmax<G>(-t_hi, mask);
     } else {
+      float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f;
 #pragma unroll
       for (int i = 0; i < DPL; ++i) {
         if (own[i]) {
-          const int dim = gl * DPL + i;
-          const float ib = 1.0f / f[R.o_b + dim];
-          const float u = (x[i] - f[R.o_a + dim]) * ib, q = v[i] * ib;
+          const float ib = 1.0f / pb[i];
+          const float u = (x[i] - pa[i]) * ib, q = v[i] * ib;
           P0 = fmaf(u, u, P0);
           P1 = fmaf(u, q, P1);
           P2 = fmaf(q, q, P2);
@@ -161,7 +178,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       // HRSS: slice height log Pi(x) + ln u (word nz + 1); RW: the Metropolis
       // threshold log Pi(x) + ln u with u = word nz
       const float uh = u24(R.kernel == kKernelRw ? wU : wH);
-      height = fmaf(-0.5f, P0, R.prior_const) + logf(uh);
+      q3 = fmaf(-0.5f, P0, R.prior_const) + logf(uh);
+      q0 = P0;
+      q1 = P1;
+      q2 = P2;
     }
     float x0 = 0.0f, v0 = 0.0f;  // coordinate 0 for the fault likelihood
     if (lk == kLikFault) {
@@ -173,10 +193,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     // and is flagged; nothing is counted here.
     auto probe = [&](float t, float& ll, bool& isn) -> bool {
       ++ran;
-      if (box && !(t >= t_lo && t <= t_hi)) return false;
+      if (box && !(t >= q0 && t <= q1)) return false;
       if (nonflat) {
-        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
-        if (!(lp > height)) return false;
+        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, q2, 2.0f * q1), q0), R.prior_const);
+        if (!(lp > q3)) return false;
       }
       if (lk == kLikFlat) {
         ll = 0.0f;
@@ -211,10 +231,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       // comes from the line coefficients), so the tests run one at a time.
       auto test = [&](float t, float& ll, bool& isn) -> bool {
         if (gl == 0) ++ran;
-        if (box && !(t >= t_lo && t <= t_hi)) return false;
+        if (box && !(t >= q0 && t <= q1)) return false;
         if (nonflat) {
-          const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
-          if (!(lp > height)) return false;
+          const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, q2, 2.0f * q1), q0), R.prior_const);
+          if (!(lp > q3)) return false;
         }
         float cs = 0.0f;
 #pragma unroll
@@ -236,15 +256,12 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
         bool isn = false;
         float ll = 0.0f;
         const bool in = test(R.rw_scale, ll, isn);
-        ++evals;
         if (isn) ++nanc;
         if (in) {
 #pragma unroll
           for (int i = 0; i < DPL; ++i) x[i] = fmaf(R.rw_scale, v[i], x[i]);
           lx = ll;
           ++acc;
-        } else {
-          ++nul;
         }
         continue;
       }
@@ -264,7 +281,6 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
           t += delta;
         }
         ends[q] = t;
-        evals += min(n + 1, kStepOutCap);
         exps += n;
         if (n == kStepOutCap) ++capo;
       }
@@ -273,7 +289,6 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       for (int r = 0; r < kShrinkCap; ++r) {
         const float t = fmaf(u24(step_word(3u + (uint32_t)r)), tr - tl, tl);
         ++shr;
-        ++evals;
         bool isn = false;
         float ll = 0.0f;
         const bool in = test(t, ll, isn);
@@ -289,7 +304,6 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
         else tr = t;
       }
       if (ok) ++acc;
-      else ++nul;
       continue;
     }
     if (R.kernel == kKernelRw) {
@@ -300,15 +314,12 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       float ll = 0.0f;
       const bool in = probe(ts, ll, isn);
       if (gl != 0) --ran;  // the group's lanes test the same point: one test
-      ++evals;
       if (isn) ++nanc;
       if (in) {
 #pragma unroll
         for (int i = 0; i < DPL; ++i) x[i] = fmaf(ts, v[i], x[i]);
         lx = ll;
         ++acc;
-      } else {
-        ++nul;
       }
       continue;
     }
@@ -361,7 +372,6 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        evals += min(stop[q] + 1, kStepOutCap);
         exps += stop[q];
         if (stop[q] == kStepOutCap) ++capo;
       }
@@ -381,7 +391,6 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
           t += delta;
         }
         ends[q] = t;
-        evals += min(n + 1, kStepOutCap);
         exps += n;
         if (n == kStepOutCap) ++capo;
       }
@@ -416,7 +425,6 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       if (inb) {
         const int f = __ffs(inb) - 1;
         shr += f + 1;
-        evals += f + 1;
         nanc += __popc(nanb & ((1u << f) - 1u));
         tacc = __shfl_sync(mask, t, f, G);
         llacc = __shfl_sync(mask, ll, f, G);
@@ -425,7 +433,6 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       }
       const int nvalid = min(G, kShrinkCap - b0);
       shr += nvalid;
-      evals += nvalid;
       nanc += __popc(nanb);
       tl = lo;
       tr = hi;
@@ -436,7 +443,6 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       lx = llacc;
     }
     if (ok) ++acc;
-    else ++nul;
   }
   // group-parallel rounds test ends and proposals past the first decisive
   // one; those extra tests are counted apart from the logical evaluations
@@ -446,6 +452,8 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     for (int o = G / 2; o > 0; o >>= 1) tot += __shfl_xor_sync(mask, tot, o, G);
     ran = tot;
   }
+  const int nul = R.p - acc;
+  const int evals = (R.kernel == kKernelRw) ? R.p : exps + 2 * R.p - capo + shr;
   // (iv) replace dead slot j, born at logL*
   const int slot = D.i[R.o_dead + j];
   if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, ld, x);

@@ -29,25 +29,27 @@ constexpr int kDirStepsPerBlock = 16;  // steps of one item per block, 4 per war
 // nine shrinkage proposals, which the sweep reads instead of drawing them.
 __device__ __forceinline__ void step_words(const RunDesc& R, uint32_t iter, int j, int s, int* __restrict__ wout) {
   const uint32_t nz = 2u * (uint32_t)((R.d + 1) >> 1);
-  const uint32_t b0 = nz >> 2, off = nz & 3u;
-  uint32_t w[16];
+  const int b0 = (int)(nz >> 2), off = (int)(nz & 3u);  // off is 0 or 2 (nz is even)
+  int* o = wout + ((long long)j * R.p + s) * kStepWords;
+  // one Philox block per pass (a rolled loop keeps the kernel's code small)
+#pragma unroll 1
+  for (int q = 0; q < 3 + (off != 0); ++q) {
+    const uint4 blk = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)(b0 + q));
+    const uint32_t w[4] = {blk.x, blk.y, blk.z, blk.w};
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint4 blk = make_uint4(0u, 0u, 0u, 0u);
-    if (q < 3 || off) blk = draw_block(R, iter, (uint32_t)j, (uint32_t)s, b0 + (uint32_t)q);
-    w[4 * q] = blk.x; w[4 * q + 1] = blk.y; w[4 * q + 2] = blk.z; w[4 * q + 3] = blk.w;
+    for (int e = 0; e < 4; ++e) {
+      const int idx = 4 * q + e - off;
+      if (idx >= 0 && idx < kStepWords) o[idx] = (int)w[e];
+    }
   }
-  int4* o = reinterpret_cast<int4*>(wout + ((long long)j * R.p + s) * kStepWords);
-  // off is 0 or 2 (nz is even)
-  if (off == 0) {
-    o[0] = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
-    o[1] = make_int4((int)w[4], (int)w[5], (int)w[6], (int)w[7]);
-    o[2] = make_int4((int)w[8], (int)w[9], (int)w[10], (int)w[11]);
-  } else {
-    o[0] = make_int4((int)w[2], (int)w[3], (int)w[4], (int)w[5]);
-    o[1] = make_int4((int)w[6], (int)w[7], (int)w[8], (int)w[9]);
-    o[2] = make_int4((int)w[10], (int)w[11], (int)w[12], (int)w[13]);
-  }
+}
+
+// floats per thread of the normals' staging rows: d <= 32 stages float4
+// rows (stride DMAX + 4: a quarter-warp's 16-byte accesses hit distinct
+// banks), d > 32 keeps z and d~ there (odd stride)
+template <int DMAX>
+__host__ __device__ constexpr int dirgen_zrow() {
+  return DMAX > 32 ? DMAX + 1 : DMAX + 4;
 }
 
 template <int DMAX>
@@ -59,16 +61,23 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
   float4* out = reinterpret_cast<float4*>(vout + ((long long)j * R.p + s) * ld);
   float zz = 0.0f, dd = 0.0f;
   if constexpr (!kShared) {
+    // the normals, one Philox block (two Box-Muller pairs) per pass of a
+    // rolled loop through this thread's row of shared memory, then into
+    // registers
+    float4* zs4 = reinterpret_cast<float4*>(zsh);
+#pragma unroll 1
+    for (int q = 0; 4 * q < d; ++q) {
+      float a0, a1, a2, a3;
+      const uint4 w = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
+      box_muller(w.x, w.y, a0, a1);
+      box_muller(w.z, w.w, a2, a3);
+      zs4[q] = make_float4(a0, a1, a2, a3);
+    }
     float z[kReg];
 #pragma unroll
     for (int q = 0; q < kReg / 4; ++q) {
-      if (4 * q < d) {
-        const uint4 w = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
-        box_muller(w.x, w.y, z[4 * q], z[4 * q + 1]);
-        box_muller(w.z, w.w, z[4 * q + 2], z[4 * q + 3]);
-      } else {
-        z[4 * q] = z[4 * q + 1] = z[4 * q + 2] = z[4 * q + 3] = 0.0f;
-      }
+      const float4 t = (4 * q < d) ? zs4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      z[4 * q] = t.x; z[4 * q + 1] = t.y; z[4 * q + 2] = t.z; z[4 * q + 3] = t.w;
     }
 #pragma unroll
     for (int i = 0; i < kReg; ++i) {
@@ -147,7 +156,7 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
 template <int DMAX>
 __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* __restrict__ items, int n_items) {
   constexpr bool kShared = DMAX > 32;
-  extern __shared__ __align__(16) float dsm[];  // L [ld][ld], then (kShared) z [kDirThreads][DMAX + 1]
+  extern __shared__ __align__(16) float dsm[];  // L [ld][ld], then z [kDirThreads][zrow]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int it = blockIdx.x;
   if (it >= n_items) return;
@@ -164,7 +173,7 @@ __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* _
   const int j = wi.c0 + lane;
   if (j >= wi.c1) return;
   const uint32_t iter = (uint32_t)S.iter;
-  float* zsh = kShared ? dsm + ld * ld + threadIdx.x * (DMAX + 1) : nullptr;
+  float* zsh = dsm + DMAX * DMAX + threadIdx.x * dirgen_zrow<DMAX>();
   const int s1 = min(R.p, s0 + kDirStepsPerBlock);
   for (int s = s0 + wid; s < s1; s += kDirThreads / 32) {
     one_direction<DMAX>(R, dsm, zsh, iter, j, s, D.f + R.o_V);
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* _
 
 template <int DMAX>
 size_t dirgen_smem() {
-  return sizeof(float) * ((size_t)DMAX * DMAX + (DMAX > 32 ? (size_t)kDirThreads * (DMAX + 1) : 0));
+  return sizeof(float) * ((size_t)DMAX * DMAX + (size_t)kDirThreads * dirgen_zrow<DMAX>());
 }
 
 }  // namespace

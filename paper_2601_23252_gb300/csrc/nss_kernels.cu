@@ -453,10 +453,20 @@ __global__ void k_vol_scan(Dev D, VolArgs A, int n_runs) {
   }
 }
 
-// per tile: log w_i^(r) = logL_i + log dX_i^(r) (trapezoid), the running
-// log-sum-exp of each trajectory, and the mean over r of log dX_i.
+// per tile: log w_i^(r) = logL_i + log dX_i^(r) (trapezoid), the tile's part
+// of each trajectory's log-sum-exp, and the mean over r of log dX_i.
+//
+// Within a tile everything is relative to two references, so the per-term
+// work stays in FP32: log X at the tile start (FP64, from the scan) and the
+// tile's largest logL.  rel_i = log dX_i - log X(start) sums the terms from
+// the tile start (compensated FP32 sum) and the trapezoid factor; since
+// log X only decreases and the factor is below 1/2, every log w_i is at most
+// M = max logL + log X(start), and the tile's sum is sum exp(log w_i - M)
+// with FP32 exponents accumulated in FP64.
 __global__ void k_vol_weights(Dev D, VolArgs A) {
-  extern __shared__ double sh[];  // [R][32]
+  extern __shared__ float shf[];  // [R][32] rel_i of the current chunk
+  __shared__ double red[32];
+  __shared__ double part_s[32 * 32];
   const int tile = blockIdx.x, r = threadIdx.x;
   const int2 t = A.tiles[tile];
   const RunDesc& R = D.desc[t.x];
@@ -466,14 +476,17 @@ __global__ void k_vol_weights(Dev D, VolArgs A) {
   const float* lL = D.f + R.o_dlogL;
   double* lw = D.dd + R.o_lw;
   const bool act = r < A.R;
+  // the tile's largest logL, and the mean over r of log X at the tile start
+  float lm = -INFINITY;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) lm = fmaxf(lm, lL[i]);
+  lm = (float)block_max_d((double)lm, red);
+  const double start = act ? A.toff[(size_t)r * A.n_tiles + tile] : 0.0;
+  const double start_mean = block_sum_d(start, red) / (double)A.R;
   uint4 blk;
   long long bi = -1;
-  // log X_{i-1} in FP64; the terms t_i = log(u_i)/n_i in FP32.  The trapezoid
-  // weight (X_{i-1} - X_{i+1}) / 2 has log X_{i-1} + log(1 - e^{t_i + t_{i+1}})
-  // - ln 2 (t_{N+1} = -inf: X_{N+1} = 0)
-  double prev = act ? A.toff[(size_t)r * A.n_tiles + tile] : 0.0;
+  float off = 0.0f, comp = 0.0f;  // log X_{i-1} - log X(start), compensated
   float tcur = act ? vol_term_f(R.key0, R.key1, r, i0, nl[i0], blk, bi) : 0.0f;
-  double M = -INFINITY, Sacc = 0.0;
+  double Sacc = 0.0;
   const float ln2f = 0.693147182f;
   for (long long c0 = i0; c0 < i1; c0 += 32) {
     const int cn = (int)min((long long)32, i1 - c0);
@@ -481,21 +494,15 @@ __global__ void k_vol_weights(Dev D, VolArgs A) {
       for (int q = 0; q < cn; ++q) {
         const long long i = c0 + q;
         const float tnxt = (i + 1 < n) ? vol_term_f(R.key0, R.key1, r, i + 1, nl[i + 1], blk, bi) : -INFINITY;
-        const double ldx = prev + (double)(logf(-expm1f(tcur + tnxt)) - ln2f);
-        const double v = (double)lL[i] + ldx;
-        if (v == -INFINITY) {
-          // a point outside every constraint set carries no weight
-        } else {
-          const float dv = (float)(v - M);
-          if (dv > 0.0f) {
-            Sacc = Sacc * (double)expf(-dv) + 1.0;
-            M = v;
-          } else {
-            Sacc += (double)expf(dv);
-          }
-        }
-        sh[r * 32 + q] = ldx;
-        prev += (double)tcur;
+        // (X_{i-1} - X_{i+1}) / 2 = X_{i-1} (1 - e^{t_i + t_{i+1}}) / 2  (t_{N+1} = -inf: X_{N+1} = 0)
+        const float rel = off + (logf(-expm1f(tcur + tnxt)) - ln2f);
+        const float li = lL[i];
+        // a point outside every constraint set carries no weight
+        if (li > -INFINITY) Sacc += (double)expf((li - lm) + rel);
+        shf[r * 32 + q] = rel;
+        const float y = tcur - comp, tt = off + y;
+        comp = (tt - off) - y;
+        off = tt;
         tcur = tnxt;
       }
     }
@@ -504,22 +511,21 @@ __global__ void k_vol_weights(Dev D, VolArgs A) {
     // then the partials combined in warp order
     {
       const int pt = threadIdx.x & 31, part = threadIdx.x >> 5, P = blockDim.x >> 5;
-      double s = 0.0;
+      double sp = 0.0;
       if (pt < cn)
-        for (int q = part; q < A.R; q += P) s += sh[q * 32 + pt];
-      __syncthreads();
-      sh[part * 32 + pt] = s;
+        for (int q = part; q < A.R; q += P) sp += (double)shf[q * 32 + pt];
+      part_s[part * 32 + pt] = sp;
       __syncthreads();
       if (threadIdx.x < cn) {
         double tot = 0.0;
-        for (int q = 0; q < P; ++q) tot += sh[q * 32 + threadIdx.x];
-        lw[c0 + threadIdx.x] = (double)lL[c0 + threadIdx.x] + tot / (double)A.R;
+        for (int q = 0; q < P; ++q) tot += part_s[q * 32 + threadIdx.x];
+        lw[c0 + threadIdx.x] = (double)lL[c0 + threadIdx.x] + (start_mean + tot / (double)A.R);
       }
     }
     __syncthreads();
   }
   if (act) {
-    A.tmax[(size_t)r * A.n_tiles + tile] = M;
+    A.tmax[(size_t)r * A.n_tiles + tile] = (lm > -INFINITY && Sacc > 0.0) ? (double)lm + start : -INFINITY;
     A.tacc[(size_t)r * A.n_tiles + tile] = Sacc;
   }
 }
@@ -582,6 +588,9 @@ __global__ void k_vol_norm(Dev D, int run) {
 cudaError_t setup_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
+  // up to 1024 trajectories: [1024][32] FP32 offsets
+  e = cudaFuncSetAttribute(k_vol_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 * 32 * (int)sizeof(float));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_final_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
@@ -616,7 +625,7 @@ cudaError_t launch_volsim(const Dev& D, const VolLaunch& V, int n_runs, cudaStre
   if (e != cudaSuccess) return e;
   k_vol_scan<<<n_runs, bt, 0, s>>>(D, A, n_runs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_vol_weights<<<V.n_tiles, bt, (size_t)bt * 32 * sizeof(double), s>>>(D, A);
+  k_vol_weights<<<V.n_tiles, bt, (size_t)bt * 32 * sizeof(float), s>>>(D, A);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_vol_final<<<n_runs, 256, 0, s>>>(D, A, n_runs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -63,17 +63,25 @@ __global__ void k_svol_scan(StaticVol V) {
   }
 }
 
+// the same tile-relative scheme as k_vol_weights (nss_kernels.cu)
 __global__ void k_svol_weights(StaticVol V, double* __restrict__ lw) {
-  extern __shared__ double sh[];  // [blockDim][32]
+  extern __shared__ float shf[];  // [blockDim][32]
+  __shared__ double red[32];
+  __shared__ double part_s[32 * 32];
   const int tile = blockIdx.x, r = threadIdx.x;
   const long long n = V.n;
   const long long i0 = (long long)tile * kVolTile, i1 = min(i0 + kVolTile, n);
   const bool act = r < V.R;
+  float lm = -INFINITY;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) lm = fmaxf(lm, V.logL[i]);
+  lm = (float)block_max_d((double)lm, red);
+  const double start = act ? V.toff[(size_t)r * V.nt + tile] : 0.0;
+  const double start_mean = block_sum_d(start, red) / (double)V.R;
   uint4 blk;
   long long bi = -1;
-  double prev = act ? V.toff[(size_t)r * V.nt + tile] : 0.0;  // log X_{i-1}
+  float off = 0.0f, comp = 0.0f;
   float tcur = act ? vol_term_f(V.k0, V.k1, r, i0, V.nlive[i0], blk, bi) : 0.0f;
-  double M = -INFINITY, Sacc = 0.0;
+  double Sacc = 0.0;
   const float ln2f = 0.693147182f;
   for (long long c0 = i0; c0 < i1; c0 += 32) {
     const int cn = (int)min((long long)32, i1 - c0);
@@ -81,43 +89,34 @@ __global__ void k_svol_weights(StaticVol V, double* __restrict__ lw) {
       for (int q = 0; q < cn; ++q) {
         const long long i = c0 + q;
         const float tnxt = (i + 1 < n) ? vol_term_f(V.k0, V.k1, r, i + 1, V.nlive[i + 1], blk, bi) : -INFINITY;
-        const double ldx = prev + (double)(logf(-expm1f(tcur + tnxt)) - ln2f);
-        const double v = (double)V.logL[i] + ldx;
-        if (v != -INFINITY) {
-          const float dv = (float)(v - M);
-          if (dv > 0.0f) {
-            Sacc = Sacc * (double)expf(-dv) + 1.0;
-            M = v;
-          } else {
-            Sacc += (double)expf(dv);
-          }
-        }
-        sh[r * 32 + q] = ldx;
-        prev += (double)tcur;
+        const float rel = off + (logf(-expm1f(tcur + tnxt)) - ln2f);
+        const float li = V.logL[i];
+        if (li > -INFINITY) Sacc += (double)expf((li - lm) + rel);
+        shf[r * 32 + q] = rel;
+        const float y = tcur - comp, tt = off + y;
+        comp = (tt - off) - y;
+        off = tt;
         tcur = tnxt;
       }
     }
     __syncthreads();
-    // mean over the trajectories: one partial sum per warp and dead point,
-    // then the partials combined in warp order
     {
       const int pt = threadIdx.x & 31, part = threadIdx.x >> 5, P = blockDim.x >> 5;
-      double s = 0.0;
+      double sp = 0.0;
       if (pt < cn)
-        for (int q = part; q < V.R; q += P) s += sh[q * 32 + pt];
-      __syncthreads();
-      sh[part * 32 + pt] = s;
+        for (int q = part; q < V.R; q += P) sp += (double)shf[q * 32 + pt];
+      part_s[part * 32 + pt] = sp;
       __syncthreads();
       if (threadIdx.x < cn) {
         double tot = 0.0;
-        for (int q = 0; q < P; ++q) tot += sh[q * 32 + threadIdx.x];
-        lw[c0 + threadIdx.x] = (double)V.logL[c0 + threadIdx.x] + tot / (double)V.R;
+        for (int q = 0; q < P; ++q) tot += part_s[q * 32 + threadIdx.x];
+        lw[c0 + threadIdx.x] = (double)V.logL[c0 + threadIdx.x] + (start_mean + tot / (double)V.R);
       }
     }
     __syncthreads();
   }
   if (act) {
-    V.tmax[(size_t)r * V.nt + tile] = M;
+    V.tmax[(size_t)r * V.nt + tile] = (lm > -INFINITY && Sacc > 0.0) ? (double)lm + start : -INFINITY;
     V.tacc[(size_t)r * V.nt + tile] = Sacc;
   }
 }
@@ -211,7 +210,7 @@ extern "C" nss_status nss_volume_sim_static(const float* logL, const int* nlive,
   const int bt = (n_sim + 31) / 32 * 32;
   k_svol_tilesum<<<V.nt, bt, 0, s>>>(V);
   k_svol_scan<<<1, bt, 0, s>>>(V);
-  k_svol_weights<<<V.nt, bt, (size_t)bt * 32 * sizeof(double), s>>>(V, log_w);
+  k_svol_weights<<<V.nt, bt, (size_t)bt * 32 * sizeof(float), s>>>(V, log_w);
   k_svol_final<<<1, 256, 0, s>>>(V, log_w, logZ_stats);
   k_svol_norm<<<64, 256, 0, s>>>(V, log_w);
   e = cudaGetLastError();

@@ -34,7 +34,15 @@ namespace nss {
 // The moved point x + t v is formed coordinate by coordinate on acceptance.
 // ---------------------------------------------------------------------------
 template <int G, int DPL, int KC>
-__device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j, int gl, unsigned mask) {
+__device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j, int gl, unsigned mask, bool live) {
+  // Every lane of the warp runs here (a group without a chain of its own
+  // repeats the warp's first chain and writes nothing), and all groups take
+  // the same number of steps, so the per-step reductions and the grouped
+  // slice-test rounds run on the whole warp (full-mask shuffles and votes,
+  // warp-uniform round loops); `mask` (the group's lanes) serves the paths
+  // whose groups run their tests one at a time.
+  constexpr unsigned kAll = 0xffffffffu;
+  const int gshift = (int)(threadIdx.x & 31) & ~(G - 1);  // first lane of the group
   const float* __restrict__ f = D.f;
   const int d = R.d, ld = R.dpad;
   const bool has = gl * DPL < ld;
@@ -101,7 +109,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     float Cv = 0.0f;
 #pragma unroll
     for (int i = 0; i < DPL; ++i) Cv = fmaf(v[i], v[i], Cv);
-    Cv = gsum<G>(Cv, mask);
+    Cv = gsum<G>(Cv, kAll);
     float Dc[KC], Ec[KC];
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
@@ -123,8 +131,8 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
           dq = fmaf(e, e, dq);
           de = fmaf(e, v[i], de);
         }
-        dq = gsum<G>(dq, mask);
-        Ec[c] = gsum<G>(de, mask);
+        dq = gsum<G>(dq, kAll);
+        Ec[c] = gsum<G>(de, kAll);
         Dc[c] = c < K ? dq : INFINITY;
       }
     }
@@ -158,8 +166,8 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
           }
         }
       }
-      q0 = gmax<G>(t_lo, mask);
-      q1 = -gmax<G>(-t_hi, mask);
+      q0 = gmax<G>(t_lo, kAll);
+      q1 = -gmax<G>(-t_hi, kAll);
     } else {
       float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f;
 #pragma unroll
@@ -172,9 +180,9 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
           P2 = fmaf(q, q, P2);
         }
       }
-      P0 = gsum<G>(P0, mask);
-      P1 = gsum<G>(P1, mask);
-      P2 = gsum<G>(P2, mask);
+      P0 = gsum<G>(P0, kAll);
+      P1 = gsum<G>(P1, kAll);
+      P2 = gsum<G>(P2, kAll);
       // HRSS: slice height log Pi(x) + ln u (word nz + 1); RW: the Metropolis
       // threshold log Pi(x) + ln u with u = word nz
       const float uh = u24(R.kernel == kKernelRw ? wU : wH);
@@ -185,18 +193,19 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     }
     float x0 = 0.0f, v0 = 0.0f;  // coordinate 0 for the fault likelihood
     if (lk == kLikFault) {
-      x0 = __shfl_sync(mask, x[0], 0, G);
-      v0 = __shfl_sync(mask, v[0], 0, G);
+      x0 = __shfl_sync(kAll, x[0], 0, G);
+      v0 = __shfl_sync(kAll, v[0], 0, G);
     }
     // one slice test at x + t v: support, prior slice height, then
     // logL > logL* (Sec. 3.1: E < E_batch).  A NaN likelihood reads as -inf
-    // and is flagged; nothing is counted here.
+    // and is flagged (only where support and prior pass); nothing is counted
+    // here.  No early exit: every lane evaluates, so a warp never splits.
     auto probe = [&](float t, float& ll, bool& isn) -> bool {
-      ++ran;
-      if (box && !(t >= q0 && t <= q1)) return false;
+      bool ok = true;
+      if (box) ok = t >= q0 && t <= q1;
       if (nonflat) {
         const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, q2, 2.0f * q1), q0), R.prior_const);
-        if (!(lp > q3)) return false;
+        ok = lp > q3;
       }
       if (lk == kLikFlat) {
         ll = 0.0f;
@@ -219,11 +228,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
         if (lk == kLikFault && fmaf(t, v0, x0) < R.fault_param)
           ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
       }
-      if (isnan(ll)) {
-        ll = -INFINITY;
-        isn = true;
-      }
-      return ll > lstar;
+      const bool nan_ll = isnan(ll);
+      ll = nan_ll ? -INFINITY : ll;
+      isn = ok && nan_ll;
+      return ok && ll > lstar;
     };
     if (lk == kLikRastrigin) {
       // The Rastrigin mixture (App. F.3) is not affine along the line: every
@@ -313,7 +321,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       bool isn = false;
       float ll = 0.0f;
       const bool in = probe(ts, ll, isn);
-      if (gl != 0) --ran;  // the group's lanes test the same point: one test
+      if (gl == 0) ++ran;  // the group's lanes test the same point: one test
       if (isn) ++nanc;
       if (in) {
 #pragma unroll
@@ -342,32 +350,34 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       const float delta = side ? w : -w;
       float base[2] = {ends[0], ends[1]};  // the end at index b0 of each side
       int stop[2] = {-1, -1};
-      for (int b0 = 0; stop[0] < 0 || stop[1] < 0; b0 += H) {
-        const bool mine_open = (side ? stop[1] : stop[0]) < 0;
+      // rounds until every group of the warp has stopped both sides; a group
+      // that has stops testing (its lanes evaluate but count nothing)
+      for (int b0 = 0; __any_sync(kAll, stop[0] < 0 || stop[1] < 0); b0 += H) {
         const int idx = b0 + hl;
+        const bool mine = (side ? stop[1] : stop[0]) < 0 && idx < kStepOutCap;
         float t = side ? base[1] : base[0];
 #pragma unroll
         for (int i = 0; i < H - 1; ++i)
           if (i < hl) t += delta;
         bool isn = false;
         float ll = 0.0f;
-        const bool in = mine_open && idx < kStepOutCap && probe(t, ll, isn);
-        const bool halt = mine_open && (idx >= kStepOutCap || !in);
-        const unsigned hb = gballot<G>(halt, mask);
-        const unsigned nb = gballot<G>(isn, mask);
+        const bool pin = probe(t, ll, isn);
+        ran += mine;
+        const bool mine_open = (side ? stop[1] : stop[0]) < 0;
+        const bool halt = mine_open && (idx >= kStepOutCap || !pin);
+        const unsigned hb = (__ballot_sync(kAll, halt) >> gshift) & (G == 32 ? 0xffffffffu : (1u << G) - 1u);
+        const unsigned nb = (__ballot_sync(kAll, mine && isn) >> gshift) & (G == 32 ? 0xffffffffu : (1u << G) - 1u);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          if (stop[q] >= 0) continue;
           const unsigned hq = (hb >> (q * H)) & kHalf, nq = (nb >> (q * H)) & kHalf;
-          if (hq) {
-            const int fq = __ffs(hq) - 1;
-            stop[q] = b0 + fq;
-            nanc += __popc(nq & ((2u << fq) - 1u));
-            ends[q] = __shfl_sync(mask, t, q * H + fq, G);
-          } else {
-            nanc += __popc(nq);
-            base[q] = __shfl_sync(mask, t, q * H + H - 1, G) + (q ? w : -w);
-          }
+          const int fq = __ffs(hq) - 1;
+          // the first halting end of side q, else its last end this round
+          const float tq = __shfl_sync(kAll, t, q * H + (hq ? fq : H - 1), G);
+          const bool open_q = stop[q] < 0;
+          nanc += open_q ? __popc(hq ? (nq & ((2u << fq) - 1u)) : nq) : 0;
+          ends[q] = (open_q && hq) ? tq : ends[q];
+          base[q] = (open_q && !hq) ? tq + (q ? w : -w) : base[q];
+          stop[q] = (open_q && hq) ? b0 + fq : stop[q];
         }
       }
 #pragma unroll
@@ -386,6 +396,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
           bool isn = false;
           float ll = 0.0f;
           const bool in = probe(t, ll, isn);
+          ++ran;
           if (isn) ++nanc;
           if (!in) break;
           t += delta;
@@ -402,16 +413,19 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     // rejections are known before any test: each round the group forms G
     // consecutive proposals (a short scan over the shared u's) and tests
     // them at once; the first inside the slice is the sequential result.
+    // Rounds run until every group of the warp has accepted or used the cap;
+    // a group that has accepted evaluates but counts and changes nothing.
     bool ok = false;
     float tacc = 0.0f, llacc = 0.0f;
-    for (int b0 = 0; b0 < kShrinkCap; b0 += G) {
+    constexpr unsigned kGroupBits = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    for (int b0 = 0; b0 < kShrinkCap && __any_sync(kAll, !ok); b0 += G) {
       const int idx = b0 + gl;
-      const bool valid = idx < kShrinkCap;
+      const bool mine = !ok && idx < kShrinkCap;
       const float u = u24((b0 == 0 && wlane) ? wS : step_word(3u + (uint32_t)idx));
       float lo = tl, hi = tr, t = 0.0f;
 #pragma unroll
       for (int i = 0; i < G; ++i) {
-        const float ui = __shfl_sync(mask, u, i, G);
+        const float ui = __shfl_sync(kAll, u, i, G);
         const float ti = fmaf(ui, hi - lo, lo);
         if (i == gl) t = ti;
         if (ti < 0.0f) lo = ti;
@@ -419,23 +433,23 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       }
       bool isn = false;
       float ll = 0.0f;
-      const bool in = valid && probe(t, ll, isn);
-      const unsigned inb = gballot<G>(in, mask);
-      const unsigned nanb = gballot<G>(isn, mask);
-      if (inb) {
-        const int f = __ffs(inb) - 1;
-        shr += f + 1;
-        nanc += __popc(nanb & ((1u << f) - 1u));
-        tacc = __shfl_sync(mask, t, f, G);
-        llacc = __shfl_sync(mask, ll, f, G);
-        ok = true;
-        break;
+      const bool pin = probe(t, ll, isn);
+      ran += mine;
+      const unsigned inb = (__ballot_sync(kAll, mine && pin) >> gshift) & kGroupBits;
+      const unsigned nanb = (__ballot_sync(kAll, mine && isn) >> gshift) & kGroupBits;
+      const int f = __ffs(inb) - 1;
+      const float tf = __shfl_sync(kAll, t, inb ? f : 0, G);
+      const float lf = __shfl_sync(kAll, ll, inb ? f : 0, G);
+      if (!ok) {
+        const int nvalid = min(G, kShrinkCap - b0);
+        shr += inb ? f + 1 : nvalid;
+        nanc += __popc(inb ? (nanb & ((1u << f) - 1u)) : nanb);
+        tacc = inb ? tf : tacc;
+        llacc = inb ? lf : llacc;
+        tl = lo;
+        tr = hi;
+        ok = inb != 0;
       }
-      const int nvalid = min(G, kShrinkCap - b0);
-      shr += nvalid;
-      nanc += __popc(nanb);
-      tl = lo;
-      tr = hi;
     }
     if (ok) {
 #pragma unroll
@@ -449,15 +463,15 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   {
     int tot = ran;
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) tot += __shfl_xor_sync(mask, tot, o, G);
+    for (int o = G / 2; o > 0; o >>= 1) tot += __shfl_xor_sync(kAll, tot, o, G);
     ran = tot;
   }
   const int nul = R.p - acc;
   const int evals = (R.kernel == kKernelRw) ? R.p : exps + 2 * R.p - capo + shr;
   // (iv) replace dead slot j, born at logL*
   const int slot = D.i[R.o_dead + j];
-  if (has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, ld, x);
-  if (gl == 0) {
+  if (live && has) store_lane<DPL>(D.f + R.o_x + (long long)slot * ld, gl, ld, x);
+  if (live && gl == 0) {
     D.f[R.o_logL + slot] = lx;
     D.f[R.o_birth + slot] = lstar;
     int* st = D.i + R.o_stats;
@@ -493,7 +507,8 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(
     RunState* S = D.st + wi.run;
     if (S->done) continue;
     const int j = wi.c0 + grp;
-    if (j < wi.c1) sweep_chain<G, DPL, KC>(D, D.desc[wi.run], S, j, gl, mask);
+    const bool live = j < wi.c1;
+    sweep_chain<G, DPL, KC>(D, D.desc[wi.run], S, live ? j : wi.c0, gl, mask, live);
     __syncwarp();
   }
 }

@@ -6,11 +6,13 @@
 // step's direction v in registers.  A warp holds 32/G chains of one run.
 // Group reductions are xor butterflies, so every lane of the group ends with
 // the bitwise-identical value and the whole group takes the same branch.
-// Chains of a warp step in lockstep per HRSS step and diverge only inside
-// the stepping-out and shrinkage rounds; a persistent grid takes warps' worth
-// of chains from an atomic ticket queue (costliest runs first), so a warp
-// that finishes early takes the next chains instead of idling.  No lane ever
-// waits on another block.
+// The warp's chains step in lockstep and never split the warp: the
+// stepping-out and shrinkage rounds loop until every group is done (a done
+// group evaluates but changes nothing), so every shuffle and vote runs on
+// the full warp.  A persistent grid takes warps' worth of chains from an
+// atomic ticket queue (costliest runs first), so a warp that finishes early
+// takes the next chains instead of idling.  No lane ever waits on another
+// block.
 //
 // KC bounds the number of mixture components (1: one isotropic Gaussian or
 // no likelihood; 4; 8).  Components K..KC-1 of a run with fewer read as

@@ -22,7 +22,7 @@ namespace nss {
 namespace {
 
 constexpr int kDirThreads = 128;
-constexpr int kDirStepsPerBlock = 16;  // steps of one item per block, 4 per warp
+constexpr int kDirStepsPerBlock = 8;  // steps of one item per block, 2 per warp
 
 // Words nz .. nz + 11 of step s's counter stream (nz = 2 ceil(d/2)): the
 // bracket offset U, the prior slice height, the reserved word and the first
@@ -151,8 +151,9 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
 }
 
 // block (item, step chunk): the run's factor L is staged in shared memory
-// once; warp w makes the directions of steps chunk*16 + w, +4, ... for the
-// item's 32 chains (one per lane)
+// once; warp w makes the directions of steps chunk*8 + w and + 4 for the
+// item's 32 chains (one per lane).  Short blocks keep the launch's last
+// partial wave short (measured: 16 steps per block left a long tail).
 template <int DMAX>
 __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* __restrict__ items, int n_items) {
   constexpr bool kShared = DMAX > 32;

@@ -154,19 +154,16 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       float t_lo = -INFINITY, t_hi = INFINITY;
 #pragma unroll
       for (int i = 0; i < DPL; ++i) {
-        if (own[i]) {
-          const float ai = pa[i] - x[i], bi = pb[i] - x[i];
-          const float rv = __frcp_rn(v[i]);
-          if (v[i] > 0.0f) {
-            t_lo = fmaxf(t_lo, ai * rv);
-            t_hi = fminf(t_hi, bi * rv);
-          } else if (v[i] < 0.0f) {
-            t_lo = fmaxf(t_lo, bi * rv);
-            t_hi = fminf(t_hi, ai * rv);
-          } else if (!(ai <= 0.0f && bi >= 0.0f)) {
-            t_lo = INFINITY;
-          }
-        }
+        // a <= x + t v <= b per dimension, by selects (no lane branches);
+        // v = 0 leaves t free if x is inside, else empties the interval
+        const float ai = pa[i] - x[i], bi = pb[i] - x[i];
+        const float rv = __fdividef(1.0f, v[i]);
+        const float ta = ai * rv, tb = bi * rv;
+        const bool pos = v[i] > 0.0f, neg = v[i] < 0.0f;
+        const float lo = pos ? ta : neg ? tb : (ai <= 0.0f && bi >= 0.0f) ? -INFINITY : INFINITY;
+        const float hi = pos ? tb : neg ? ta : INFINITY;
+        t_lo = own[i] ? fmaxf(t_lo, lo) : t_lo;
+        t_hi = own[i] ? fminf(t_hi, hi) : t_hi;
       }
       q0 = gmax<G>(t_lo, kAll);
       q1 = -gmax<G>(-t_hi, kAll);
@@ -423,7 +420,18 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     for (int b0 = 0; b0 < kShrinkCap && __any_sync(kAll, !ok); b0 += G) {
       const int idx = b0 + gl;
       const bool mine = !ok && idx < kShrinkCap;
-      const float u = u24((b0 == 0 && wlane) ? wS : step_word(3u + (uint32_t)idx));
+      uint32_t wr;
+      if (b0 == 0 && G <= kStepWords - 3) {
+        wr = wS;  // every lane's first proposal was drawn ahead
+      } else {
+        // drawn ahead below word kStepWords, else from the counter; both
+        // formed by every lane, so the warp does not split
+        const uint32_t r = 3u + (uint32_t)idx, wi = nz + r;
+        const uint32_t wp = pick(draw_block(R, iter, (uint32_t)j, (uint32_t)s, wi >> 2), wi & 3u);
+        const uint32_t wl = (uint32_t)__ldg(ws + min(r, (uint32_t)kStepWords - 1u));
+        wr = r < (uint32_t)kStepWords ? wl : wp;
+      }
+      const float u = u24(wr);
       float lo = tl, hi = tr, t = 0.0f;
 #pragma unroll
       for (int i = 0; i < G; ++i) {
@@ -439,19 +447,18 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       ran += mine;
       const unsigned inb = (__ballot_sync(kAll, mine && pin) >> gshift) & kGroupBits;
       const unsigned nanb = (__ballot_sync(kAll, mine && isn) >> gshift) & kGroupBits;
-      const int f = __ffs(inb) - 1;
-      const float tf = __shfl_sync(kAll, t, inb ? f : 0, G);
-      const float lf = __shfl_sync(kAll, ll, inb ? f : 0, G);
-      if (!ok) {
-        const int nvalid = min(G, kShrinkCap - b0);
-        shr += inb ? f + 1 : nvalid;
-        nanc += __popc(inb ? (nanb & ((1u << f) - 1u)) : nanb);
-        tacc = inb ? tf : tacc;
-        llacc = inb ? lf : llacc;
-        tl = lo;
-        tr = hi;
-        ok = inb != 0;
-      }
+      const int f = inb ? __ffs(inb) - 1 : 0;
+      const float tf = __shfl_sync(kAll, t, f, G);
+      const float lf = __shfl_sync(kAll, ll, f, G);
+      // a group still shrinking takes this round's outcome (by selects)
+      const int nvalid = min(G, kShrinkCap - b0);
+      shr += ok ? 0 : (inb ? f + 1 : nvalid);
+      nanc += ok ? 0 : __popc(inb ? (nanb & ((1u << f) - 1u)) : nanb);
+      tacc = (!ok && inb) ? tf : tacc;
+      llacc = (!ok && inb) ? lf : llacc;
+      tl = ok ? tl : lo;
+      tr = ok ? tr : hi;
+      ok = ok || inb != 0;
     }
     if (ok) {
 #pragma unroll

@@ -119,10 +119,16 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the sources the sweep kernel is compiled from (its own files and the headers
+# they include); a change elsewhere does not change the sweep's counters
+SWEEP_SOURCES = ("nss_device.cuh", "nss_internal.h", "nss_kernels.h", "nss_sweep.cu", "nss_sweep_chain.cuh",
+                 "nss_sweep_common.cuh", "nss_sweep_k1.cu", "nss_sweep_k4.cu", "nss_sweep_k8.cu")
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2601_23252_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in SWEEP_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

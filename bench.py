@@ -220,6 +220,25 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seeds(rank, nrun):
+    """Each rank runs its own replicas: seeds rank*nrun .. rank*nrun + nrun - 1."""
+    return [rank * nrun + s for s in range(nrun)]
+
+
+def aggregate(total_ms, dead, evals, world, device):
+    """Whole-job figures: the slowest rank's time, the dead points and
+    evaluations summed over ranks (no exchange inside the timed region)."""
+    import torch
+    if world == 1:
+        return float(total_ms), float(dead), float(evals)
+    t = torch.tensor([total_ms, dead, evals], dtype=torch.float64, device=device)
+    mx = t.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    sm = t.clone()
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(sm[2])
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -264,7 +283,7 @@ def run_native(args):
             torch.distributed.barrier()
 
     nrun = args.runs
-    seeds = [rank * nrun + s for s in range(nrun)]
+    seeds = rank_seeds(rank, nrun)
     wls = [W.gmm_d32(seed=s) for s in seeds]
     truth = np.array([gmm_logZ(w.mu, w.sigma) for w in wls])
     stream = torch.cuda.Stream(device=dev)
@@ -308,15 +327,7 @@ def run_native(args):
     clk = clocks.stop()
     prof = sampler.profile()
     total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms, dead, evals], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        total_ms_all, dead_all, evals_all = float(mx[0]), float(sm[1]), float(sm[2])
-    else:
-        total_ms_all, dead_all, evals_all = total_ms, float(dead), float(evals)
+    total_ms_all, dead_all, evals_all = aggregate(total_ms, dead, evals, world, dev)
     value = dead_all / (total_ms_all / 1e3)
     dlogZ = np.array([r["logZ"] for r in res]) - truth
     errs = np.array([r["logZ_err"] for r in res])

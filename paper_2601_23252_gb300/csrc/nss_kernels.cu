@@ -447,7 +447,6 @@ __global__ void k_vol_tilesum(Dev D, VolArgs A) {
 __global__ void k_vol_scan(Dev D, VolArgs A, int n_runs) {
   const int run = blockIdx.x, r = threadIdx.x;
   if (r >= A.R || run >= n_runs) return;
-  const RunDesc& R = D.desc[run];
   const long long n = D.st[run].n_dead;
   const int nt = (int)((n + kVolTile - 1) / kVolTile);
   double acc = 0.0;

@@ -22,6 +22,7 @@ namespace nss {
 
 constexpr int kGPThreads = 1024;
 constexpr int kGPMaxN = 256;
+constexpr int kGPPanel = 8;  // columns per factorisation panel
 
 __device__ __forceinline__ int pidx(int i, int j) { return (i * (i + 1)) / 2 + j; }
 
@@ -39,47 +40,122 @@ __device__ float gp_loglik(const float* __restrict__ tt, const float* __restrict
   const float ell = expf(th[0]), amp = expf(th[1]), sn = expf(th[2]);
   const float a2 = amp * amp, s2 = sn * sn, c = -0.5f / (ell * ell);
   const int N = n + 1;
-  // fill
-  const int tot = (N * (N + 1)) / 2;
-  for (int e = tid; e < tot; e += T) {
-    // row i of linear index e: i(i+1)/2 <= e
-    int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-    while ((i * (i + 1)) / 2 > e) --i;
-    while (((i + 1) * (i + 2)) / 2 <= e) ++i;
-    const int j = e - (i * (i + 1)) / 2;
-    float v;
-    if (i < n) {
-      const float dt = tt[i] - tt[j];
-      v = a2 * expf(c * dt * dt) + (i == j ? s2 : 0.0f);
-    } else {
-      v = (j < n) ? yy[j] : 0.0f;
+  // fill: warp w takes rows w, w + 32, ...; its lanes the row's entries
+  {
+    const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
+    for (int i = wid; i < N; i += nw) {
+      const int bi = (i * (i + 1)) / 2;
+      const float ti = i < n ? tt[i] : 0.0f;
+      for (int j = lane; j <= i; j += 32) {
+        float v;
+        if (i < n) {
+          const float dt = ti - tt[j];
+          v = a2 * expf(c * dt * dt) + (i == j ? s2 : 0.0f);
+        } else {
+          v = (j < n) ? yy[j] : 0.0f;
+        }
+        P[bi + j] = v;
+      }
     }
-    P[e] = v;
   }
   if (tid == 0) sh.ok = 1;
   __syncthreads();
-  // right-looking column steps; thread (kc, rr): column j+1+kc, rows kc+rr, +4, ...
-  const int kc = tid >> 2, rr = tid & 3;
+  // Right-looking factorisation in panels of kGPPanel columns, with the same
+  // operations in the same order as column-by-column steps (so the same
+  // bits): column j's pivot l = sqrt(A_jj), the entries below it scaled by
+  // 1/l, and every later entry A_ik -= L_ij L_kj applied in increasing j.
+  // Per panel: warp 0 factors the diagonal block; each row below solves its
+  // panel entries (its updates from the panel's earlier columns, then the
+  // scale); the trailing entries take the panel's columns in order.  Three
+  // block barriers per panel instead of three per column.
+  // L_i,j0.. of the rows below the block; row stride kGPPanel + 4 floats so
+  // that a quarter-warp's 16-byte loads of 8 different rows hit distinct banks
+  constexpr int kPS = kGPPanel + 4;
+  __shared__ __align__(16) float panel[(kGPMaxN + 1) * kPS];
+  __shared__ float pinv[kGPPanel];
   double ldet = 0.0;
-  for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const float d = P[pidx(j, j)];
-      const bool good = d > 0.0f && isfinite(d);
-      const float l = sqrtf(good ? d : 1.0f);
-      P[pidx(j, j)] = l;
-      sh.inv = 1.0f / l;
-      if (!good) sh.ok = 0;
+  for (int j0 = 0; j0 < n; j0 += kGPPanel) {
+    const int jb = min(kGPPanel, n - j0);
+    if (tid < 32) {
+      const int lane = tid;
+      for (int c = 0; c < jb; ++c) {
+        const int j = j0 + c;
+        if (lane == 0) {
+          const float d = P[pidx(j, j)];
+          const bool good = d > 0.0f && isfinite(d);
+          const float l = sqrtf(good ? d : 1.0f);
+          P[pidx(j, j)] = l;
+          pinv[c] = 1.0f / l;
+          if (!good) sh.ok = 0;
+          ldet += (double)logf(l);
+        }
+        __syncwarp();
+        if (!sh.ok) break;
+        // scale column j inside the block, then the block's later entries
+        if (lane > c && lane < jb) P[pidx(j0 + lane, j)] *= pinv[c];
+        __syncwarp();
+        for (int e = lane; e < kGPPanel * kGPPanel; e += 32) {
+          const int r = e / kGPPanel, q = e % kGPPanel;
+          if (q > c && q <= r && r < jb)
+            P[pidx(j0 + r, j0 + q)] = fmaf(-P[pidx(j0 + r, j)], P[pidx(j0 + q, j)], P[pidx(j0 + r, j0 + q)]);
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
     if (!sh.ok) break;
-    const float inv = sh.inv;
-    for (int i = j + 1 + tid; i < N; i += T) P[pidx(i, j)] *= inv;
-    if (tid == 0) ldet += (double)logf(P[pidx(j, j)]);
+    // rows below the block: their panel entries
+    const int r0 = j0 + jb;
+    for (int i = r0 + tid; i < N; i += T) {
+      const int bi = pidx(i, j0);
+      float li[kGPPanel];
+#pragma unroll
+      for (int c = 0; c < kGPPanel; ++c) {
+        if (c < jb) {
+          float a = P[bi + c];
+#pragma unroll
+          for (int q = 0; q < c; ++q) a = fmaf(-li[q], P[pidx(j0 + c, j0 + q)], a);
+          a *= pinv[c];
+          li[c] = a;
+          P[bi + c] = a;
+        } else {
+          li[c] = 0.0f;
+        }
+      }
+      float4* pr = reinterpret_cast<float4*>(panel + (size_t)i * kPS);
+#pragma unroll
+      for (int c4 = 0; c4 < kGPPanel / 4; ++c4)
+        pr[c4] = make_float4(li[4 * c4], li[4 * c4 + 1], li[4 * c4 + 2], li[4 * c4 + 3]);
+    }
     __syncthreads();
-    const int k = j + 1 + kc;
-    if (k < n) {
-      const float lk = P[pidx(k, j)];
-      for (int i = k + rr; i < N; i += 4) P[pidx(i, k)] = fmaf(-P[pidx(i, j)], lk, P[pidx(i, k)]);
+    // trailing entries: warp w takes rows r0 + w, r0 + w + 32, ...; lanes
+    // the columns k in [r0, min(i, n - 1)]
+    {
+      const int lane = tid & 31, wid = tid >> 5, nw = T >> 5;
+      for (int i = r0 + wid; i < N; i += nw) {
+        const float4* pi4 = reinterpret_cast<const float4*>(panel + (size_t)i * kPS);
+        float li[kGPPanel];
+#pragma unroll
+        for (int c4 = 0; c4 < kGPPanel / 4; ++c4) {
+          const float4 t4 = pi4[c4];
+          li[4 * c4] = t4.x; li[4 * c4 + 1] = t4.y; li[4 * c4 + 2] = t4.z; li[4 * c4 + 3] = t4.w;
+        }
+        const int kmax = min(i, n - 1), bi = (i * (i + 1)) / 2;
+        for (int k = r0 + lane; k <= kmax; k += 32) {
+          const float4* pk4 = reinterpret_cast<const float4*>(panel + (size_t)k * kPS);
+          float lk[kGPPanel];
+#pragma unroll
+          for (int c4 = 0; c4 < kGPPanel / 4; ++c4) {
+            const float4 t4 = pk4[c4];
+            lk[4 * c4] = t4.x; lk[4 * c4 + 1] = t4.y; lk[4 * c4 + 2] = t4.z; lk[4 * c4 + 3] = t4.w;
+          }
+          float acc = P[bi + k];
+#pragma unroll
+          for (int c = 0; c < kGPPanel; ++c)
+            if (c < jb) acc = fmaf(-li[c], lk[c], acc);
+          P[bi + k] = acc;
+        }
+      }
     }
     __syncthreads();
   }

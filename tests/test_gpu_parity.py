@@ -178,3 +178,39 @@ def test_batched_runs_equal_single_runs(gpu_lib):
             d1 = s.dead(0)
         for key in ("x", "logL", "nlive", "birth", "log_w"):
             assert np.array_equal(d1[key], dead_b[r][key]), (r, key)
+
+
+# tiny batches: a warp's last groups without a chain of their own (k not a
+# multiple of the chains per warp, down to k = 1), d below one lane's float4
+TINY = [(1, 8, 4, 3), (2, 8, 1, 2), (3, 9, 7, 4), (3, 40, 13, 3), (4, 16, 9, 5)]
+
+
+@pytest.mark.parametrize("d,m,k,p", TINY)
+def test_one_step_parity_tiny_batches(gpu_lib, d, m, k, p):
+    """m, k, p and d at their small ends, in every configuration that fits:
+    selection, parents and the logical counters as the checker, positions
+    within 1e-5, and the slots not replaced untouched."""
+    wl = W.Workload("tiny", d, "box", np.zeros(d), np.ones(d), "gauss", m, k, p, sigma=0.2,
+                    mu=np.full((1, d), 0.45), seed=11 + d + k)
+    with native.Sampler(wl) as s:
+        cands = [q for q in range(25) if _fits(s, q, d)]
+    assert cands
+    for q in cands:
+        with native.Sampler(wl) as s:
+            s.set_cfg(0, q)
+            rep = compare_step(wl, 1, sampler=s)
+        g, t = rep["gpu"], rep["orc"]
+        assert np.array_equal(g["dead_idx"], t["dead_idx"]) and np.array_equal(g["parent"], t["parent"])
+        tie = near_tie_mask(rep, "gauss_d2")
+        same = np.ones(k, bool)
+        for c in COUNTERS:
+            same &= g[c] == t[c]
+        assert np.all(same | tie), (q, np.nonzero(~(same | tie))[0])
+        ok = same & ~tie
+        if ok.any():
+            assert np.abs(g["new_x"][ok] - t["new_x"][ok]).max() <= 1e-5
+        gs = rep["gstate"]
+        assert np.array_equal(gs["x"][g["dead_idx"]], g["new_x"])
+        keep = np.setdiff1d(np.arange(m), g["dead_idx"])
+        assert np.array_equal(gs["x"][keep], rep["x32"][keep])
+        assert abs(rep["info"]["logZ"] - rep["orc_logZ"]) < 1e-6 * max(1.0, abs(rep["orc_logZ"]))

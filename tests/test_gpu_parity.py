@@ -214,3 +214,41 @@ def test_one_step_parity_tiny_batches(gpu_lib, d, m, k, p):
         keep = np.setdiff1d(np.arange(m), g["dead_idx"])
         assert np.array_equal(gs["x"][keep], rep["x32"][keep])
         assert abs(rep["info"]["logZ"] - rep["orc_logZ"]) < 1e-6 * max(1.0, abs(rep["orc_logZ"]))
+
+
+# the largest sizes the library accepts: d = 128 (directions and the factor
+# through shared memory, 128-wide groups) and m = 4096 (the block sort through
+# shared memory); a Gaussian prior at d = 64
+LARGE = [("box", 128, 300, 150, 3), ("box", 2, 4096, 2048, 3), ("gauss", 64, 256, 128, 4)]
+
+
+@pytest.mark.parametrize("prior,d,m,k,p", LARGE)
+def test_one_step_parity_maximum_sizes(gpu_lib, prior, d, m, k, p):
+    if prior == "box":
+        a, b = np.zeros(d), np.ones(d)
+        mu = np.full((1, d), 0.45)
+        sigma = 0.25 if d > 2 else 0.1
+    else:  # prior N(0, I); likelihood N(x; 0.5, 0.5^2 I)
+        a, b = np.zeros(d), np.ones(d)
+        mu = np.full((1, d), 0.5)
+        sigma = 0.5
+    wl = W.Workload("large", d, prior, a, b, "gauss", m, k, p, sigma=sigma, mu=mu, seed=5 + d)
+    rep = compare_step(wl, 2)
+    g, t = rep["gpu"], rep["orc"]
+    assert np.array_equal(g["dead_idx"], t["dead_idx"]) and np.array_equal(g["parent"], t["parent"])
+    assert g["logLstar"] == np.float32(t["logLstar"])
+    lerr = np.abs(g["L"] - t["L"]).max() / np.abs(t["L"]).max()
+    tie = near_tie_mask(rep, "gmm_d32")
+    same = np.ones(k, bool)
+    for c in COUNTERS:
+        same &= g[c] == t[c]
+    ok = same & ~tie
+    print(f"\nlarge {prior} d={d} m={m} k={k}: L rel err {lerr:.2e}, ties {tie.mean():.4f}, "
+          f"mismatch {np.mean(~same):.4f}")
+    assert lerr < 2e-5
+    assert np.all(same | tie)
+    assert ok.mean() > 0.9
+    assert np.abs(g["new_x"][ok] - t["new_x"][ok]).max() <= 1e-5 * (1.0 if prior == "box" else 10.0)
+    keep = np.setdiff1d(np.arange(m), g["dead_idx"])
+    assert np.array_equal(rep["gstate"]["x"][keep], rep["x32"][keep])
+    assert abs(rep["info"]["logZ"] - rep["orc_logZ"]) < 1e-6 * max(1.0, abs(rep["orc_logZ"]))

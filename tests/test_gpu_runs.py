@@ -218,7 +218,7 @@ def test_random_walk_runs_against_closed_form(gpu_lib):
 # p = 10d and is left out.
 RASTRIGIN_CASES = [(2, 0.0, 3), (2, 0.5, 3), (2, 1.0, 3), (4, 0.0, 3), (4, 0.5, 3), (4, 1.0, 3),
                    (10, 0.0, 3), (10, 0.1, 3), (10, 0.5, 3), (10, 1.0, 3), (30, 0.0, 10), (30, 0.5, 3),
-                   (30, 0.9, 3), (100, 0.5, 10), (100, 1.0, 10)]
+                   (30, 0.9, 3), (100, 0.1, 10), (100, 0.5, 10), (100, 1.0, 10)]
 
 
 @pytest.mark.parametrize("d,alpha,pd", RASTRIGIN_CASES)

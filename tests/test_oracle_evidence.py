@@ -177,3 +177,16 @@ def test_run_invariants_and_posterior_moments():
         var = np.sum(w * (r["x"][:, i] - mean) ** 2)
         assert abs(mean - tn.mean()) < 5 * tn.std() / np.sqrt(ess)
         assert abs(var / tn.var() - 1) < 5 * np.sqrt(2 / ess)
+
+
+@pytest.mark.parametrize("live", [[0.0, 0.0, 0.0, 0.0], [0.0, -1.0, -2.0, -3.0], [1.5, -0.5, 0.2]])
+def test_termination_is_the_live_fraction_threshold(live):
+    """Reading C11: stop when Z_live / (Z + Z_live) < tol with Z_live = X
+    times the mean live likelihood; just below the threshold stops, just
+    above does not."""
+    live = np.array(live)
+    tol, logX = 1e-3, -2.0
+    z_live = np.exp(logX) * np.mean(np.exp(live))
+    for f, want in ((0.999 * tol, True), (1.001 * tol, False)):
+        logZ = np.log(z_live * (1.0 / f - 1.0))
+        assert O.should_stop(live, logZ, logX, tol) == want

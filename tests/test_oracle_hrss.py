@@ -168,3 +168,21 @@ def test_mean_chord_matches_monte_carlo_and_asymptotics():
     # Lemma "mean chord length in ellipsoids": E[l] -> 4 R sqrt(2/(pi d))
     d = 400
     assert abs(O.mean_chord_ball(d, 1.0) / (4 * np.sqrt(2 / (np.pi * d))) - 1) < 5e-3
+
+
+@pytest.mark.parametrize("dir_norm,scale", [(0, 2.5), (1, 2.5), (0, 0.8)])
+def test_direction_normalisation_sets_the_slice_scale(dir_norm, scale):
+    """Reading C5: by default v = L z / |z|, so the bracket width w acts in
+    whitened units and on a slice of length ell the cost theorem holds with
+    ell / s (L = [[s]]); the literal v = d~ / |d~| (dir_norm 1) keeps ell."""
+    ell, w = 10.0, 2.0
+    pb = _interval_problem(ell)
+    rng = np.random.default_rng(17 + dir_norm)
+    n = 4000
+    outs = np.empty(n)
+    for i in range(n):
+        x0 = rng.uniform(0, ell)
+        _, _, c = O.hrss_step(pb, np.array([[scale]]), w, dir_norm, -np.inf, 9, 0, 0, i, 0, [x0], 0.0)
+        outs[i] = c["expansions"]
+    ell_eff = ell / scale if dir_norm == 0 else ell
+    assert abs(outs.mean() - ell_eff / w) < 4 * outs.std() / np.sqrt(n) + 1e-9

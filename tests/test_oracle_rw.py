@@ -87,3 +87,26 @@ def test_rw_cost_spread_exceeds_hrss():
     rw, hr = np.array(rw), np.array(hr)
     assert rw.std() > 2.0 * hr.std()
     assert np.percentile(rw, 95) > np.percentile(hr, 95)
+
+
+@pytest.mark.parametrize("scale", [0.3, 2.38 / np.sqrt(3)])
+def test_rw_proposal_is_scaled_metric_step(scale):
+    """Sec. 3.1 random walk: y = x + s L z with z ~ N(0, I); on an
+    unconstrained flat problem every proposal is taken, so (y - x) / s has
+    covariance L L^T (here diag(4, 1, 0.25)) and |L^-1 (y - x)|^2 / s^2 is
+    chi-square with d degrees of freedom."""
+    d = 3
+    pb = O.Problem(("box", np.full(d, -1e6), np.full(d, 1e6)), "flat")
+    L = np.diag([2.0, 1.0, 0.5])
+    Linv = np.linalg.inv(L)
+    n = 4000
+    q = np.empty(n)
+    dev = np.empty((n, d))
+    for c in range(n):
+        x0 = np.zeros(d)
+        y, _, cnt = O.rw_step(pb, L, scale, -np.inf, 21, 0, 0, c, 0, x0, 0.0)
+        assert cnt["accepts"] == 1
+        dev[c] = (y - x0) / scale
+        q[c] = np.sum((Linv @ dev[c]) ** 2)
+    assert stats.kstest(q, "chi2", args=(d,)).pvalue > 1e-3
+    assert np.allclose(np.var(dev, axis=0), np.diag(L) ** 2, rtol=0.1)

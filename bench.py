@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--ncu-case-logreg", action="store_true",
                     help="no timing: one outer iteration of the full-size logistic-regression "
                          "workload (d=100, N=10000, k=1000, p=200), for ncu captures of its kernels")
+    ap.add_argument("--ncu-case-gp", action="store_true",
+                    help="no timing: two outer iterations of the GP workload (n=256, k=250, p=15), "
+                         "for ncu captures of its sweep kernel")
     return ap.parse_args()
 
 
@@ -483,12 +486,24 @@ def run_ncu_case_logreg(args):
     return 0
 
 
+def run_ncu_case_gp(args):
+    from paper_2601_23252_gb300 import native
+    from paper_2601_23252_gb300 import workloads as W
+    wl = W.gp_d3(seed=0).with_(extra={"options": {"dead_capacity": 4 * 250 + 500}})
+    with native.Sampler(wl) as s:
+        s.step()
+        s.step()
+    return 0
+
+
 def main():
     args = parse()
     if args.ncu_case:
         return run_ncu_case(args)
     if args.ncu_case_logreg:
         return run_ncu_case_logreg(args)
+    if args.ncu_case_gp:
+        return run_ncu_case_gp(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

@@ -77,30 +77,40 @@ __device__ float gp_loglik(const float* __restrict__ tt, const float* __restrict
   for (int j0 = 0; j0 < n; j0 += kGPPanel) {
     const int jb = min(kGPPanel, n - j0);
     if (tid < 32) {
+      // the diagonal block in registers: lane r < jb holds row j0 + r;
+      // column c's entries are broadcast by shuffles
       const int lane = tid;
-      for (int c = 0; c < jb; ++c) {
-        const int j = j0 + c;
-        if (lane == 0) {
-          const float d = P[pidx(j, j)];
+      float a[kGPPanel];
+#pragma unroll
+      for (int q = 0; q < kGPPanel; ++q) a[q] = (lane < jb && q <= lane) ? P[pidx(j0 + lane, j0 + q)] : 0.0f;
+#pragma unroll
+      for (int c = 0; c < kGPPanel; ++c) {
+        if (c < jb) {
+          const float d = __shfl_sync(0xffffffffu, a[c], c);
           const bool good = d > 0.0f && isfinite(d);
           const float l = sqrtf(good ? d : 1.0f);
-          P[pidx(j, j)] = l;
-          pinv[c] = 1.0f / l;
-          if (!good) sh.ok = 0;
-          ldet += (double)logf(l);
+          const float inv = 1.0f / l;
+          if (lane == 0) {
+            pinv[c] = inv;
+            if (!good) sh.ok = 0;
+            ldet += (double)logf(l);
+          }
+          if (!good) break;  // the pivot is the same in every lane
+          if (lane == c) a[c] = l;
+          else if (lane > c && lane < jb) a[c] *= inv;
+#pragma unroll
+          for (int q = c + 1; q < kGPPanel; ++q) {
+            const float lqc = __shfl_sync(0xffffffffu, a[c], q);
+            if (q <= lane && lane < jb) a[q] = fmaf(-a[c], lqc, a[q]);
+          }
         }
-        __syncwarp();
-        if (!sh.ok) break;
-        // scale column j inside the block, then the block's later entries
-        if (lane > c && lane < jb) P[pidx(j0 + lane, j)] *= pinv[c];
-        __syncwarp();
-        for (int e = lane; e < kGPPanel * kGPPanel; e += 32) {
-          const int r = e / kGPPanel, q = e % kGPPanel;
-          if (q > c && q <= r && r < jb)
-            P[pidx(j0 + r, j0 + q)] = fmaf(-P[pidx(j0 + r, j)], P[pidx(j0 + q, j)], P[pidx(j0 + r, j0 + q)]);
-        }
-        __syncwarp();
       }
+      if (lane < jb) {
+#pragma unroll
+        for (int q = 0; q < kGPPanel; ++q)
+          if (q <= lane) P[pidx(j0 + lane, j0 + q)] = a[q];
+      }
+      __syncwarp();
     }
     __syncthreads();
     if (!sh.ok) break;

@@ -312,6 +312,15 @@ nss_status nss_get_profile(nss_ctx *ctx, nss_profile *prof);
    memory; runs on the default stream and synchronises. */
 nss_status nss_logreg_logits(const float *X, int n, int d, const float *U, int nu, float *Z);
 
+/* Self-test of the device-side bounded waits (the tensor-core kernels wait
+   on mbarriers with a poll limit, then record an error and return): a
+   one-warp kernel waits on an mbarrier that nothing completes, with at most
+   max_polls polls (1 <= max_polls <= 1<<20).  *outcome = 2 when the wait gave
+   up as designed, 1 if it completed.  Allocates and frees its own device
+   memory; runs on the default stream and synchronises.  NSS_ERR_ARG on bad
+   arguments, NSS_ERR_CUDA on a CUDA error. */
+nss_status nss_wait_selftest(unsigned max_polls, int *outcome);
+
 /* Posterior expectations over a finished run's dead points (App. D.2 weights:
    the normalised geometric-mean weights w_i = exp(log_w_i), sum 1), reduced in
    FP64 on the device in a fixed order.  The gradient kinds are the Fisher

@@ -933,6 +933,17 @@ const char* nss_last_error(const nss_ctx* c) { return c ? c->err.c_str() : "no c
 
 int nss_n_runs(const nss_ctx* c) { return c ? c->n_runs : 0; }
 
+nss_status nss_wait_selftest(unsigned max_polls, int* outcome) {
+  if (!outcome || max_polls < 1 || max_polls > (1u << 20)) return NSS_ERR_ARG;
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(int));
+  if (e == cudaSuccess) e = nss::launch_wait_selftest(d, max_polls, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(outcome, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? NSS_OK : NSS_ERR_CUDA;
+}
+
 nss_status nss_logreg_logits(const float* X, int n, int d, const float* U, int nu, float* Z) {
   if (!X || !U || !Z || d < 1 || d > 128 || n < 1 || n > (1 << 20) || nu < 1 || nu > (1 << 16)) return NSS_ERR_ARG;
   const int rows_pad = (n + 127) / 128 * 128, cols_pad = (nu + 127) / 128 * 128;

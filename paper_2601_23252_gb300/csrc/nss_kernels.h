@@ -77,6 +77,8 @@ cudaError_t launch_lr_rowll(const Dev& D, const LRArgs& A, int run, int m, int e
 cudaError_t launch_lr_dir(const Dev& D, const LRArgs& A, int run, int k, int step, cudaStream_t s);
 cudaError_t launch_lr_slice(const Dev& D, const LRArgs& A, int run, int k, int step, int emax, cudaStream_t s);
 cudaError_t launch_lr_replace(const Dev& D, const LRArgs& A, int run, int k, cudaStream_t s);
+// bounded-wait self-test: *out = 2 when the wait gave up (the expected outcome)
+cudaError_t launch_wait_selftest(int* out, uint32_t max_polls, cudaStream_t s);
 
 cudaError_t launch_init(int cfg, const Dev& D, const WorkItem* items, int n, cudaStream_t s);
 // runs [run0, run0 + n_runs)

@@ -530,4 +530,23 @@ cudaError_t launch_lr_replace(const Dev& D, const LRArgs& A, int run, int k, cud
   return cudaGetLastError();
 }
 
+// Self-test of the bounded wait: an mbarrier whose phase never completes
+// (nothing arrives on it) makes mbar_wait give up after max_polls polls; the
+// kernel reports that (2) instead of spinning, and returns.
+__global__ void k_wait_selftest(int* out, uint32_t max_polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  const bool done = tc::mbar_wait(&bar, 0, max_polls);
+  if (threadIdx.x == 0) out[0] = done ? 1 : 2;
+}
+
+cudaError_t launch_wait_selftest(int* out, uint32_t max_polls, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(out, max_polls);
+  return cudaGetLastError();
+}
+
 }  // namespace nss

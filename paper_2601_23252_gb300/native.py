@@ -114,6 +114,7 @@ def lib():
     L.nss_get_profile.argtypes = [C.c_void_p, P(Profile)]
     L.nss_n_runs.argtypes = [C.c_void_p]
     L.nss_logreg_logits.argtypes = [_fp, C.c_int, C.c_int, _fp, C.c_int, _fp]
+    L.nss_wait_selftest.argtypes = [C.c_uint, C.POINTER(C.c_int)]
     L.nss_volume_sim_static.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_uint64, C.c_uint32,
                                         C.c_void_p, C.c_void_p, C.c_void_p]
     L.nss_run_width.argtypes = [C.c_void_p, C.c_int]
@@ -193,6 +194,17 @@ def volume_sim_static(logL, nlive, n_sim, seed, run_id, log_w, logZ_stats, n=Non
                                      _ptr(log_w), _ptr(logZ_stats), stream)
     if st != NSS_OK:
         raise NSSError(st, "nss_volume_sim_static")
+
+
+def wait_selftest(max_polls=2000):
+    """Device bounded-wait self-test: 2 when a wait on an mbarrier that nothing
+    completes gave up after max_polls polls (the designed outcome), 1 if it
+    completed."""
+    out = C.c_int(0)
+    st = lib().nss_wait_selftest(int(max_polls), C.byref(out))
+    if st != NSS_OK:
+        raise NSSError(st, "nss_wait_selftest")
+    return out.value
 
 
 def logreg_logits(X, U):

@@ -72,3 +72,15 @@ def test_full_dead_store_reports_capacity(gpu_lib):
             s.step()
         assert s.n_dead() == 500
     assert e.value.status == -4
+
+
+def test_bounded_device_wait_gives_up_and_the_context_stays_usable(gpu_lib):
+    """A wait on an mbarrier that nothing completes (the tensor-core kernels'
+    wait primitive, poll-limited) gives up and reports it; the device then
+    runs a normal sampler as before."""
+    assert native.wait_selftest(2000) == 2
+    with pytest.raises(native.NSSError):
+        native.wait_selftest(0)
+    with native.Sampler(W.gauss_d2(seed=3)) as s:
+        res = s.run()[0]
+    assert np.isfinite(res["logZ"]) and res["n_dead"] > 0

@@ -156,7 +156,6 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
 // partial wave short (measured: 16 steps per block left a long tail).
 template <int DMAX>
 __global__ void __launch_bounds__(kDirThreads) k_dirgen(Dev D, const WorkItem* __restrict__ items, int n_items) {
-  constexpr bool kShared = DMAX > 32;
   extern __shared__ __align__(16) float dsm[];  // L [ld][ld], then z [kDirThreads][zrow]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int it = blockIdx.x;

@@ -70,3 +70,24 @@ def _draw(pb, slot):
     x = np.empty(pb.d)
     O.lib().orc_prior_draw(C.byref(pb.s), 5, 0, slot, O._d(x))
     return x
+
+
+def test_counter_and_key_layout_of_the_initial_draw():
+    """Reading C14: key = (seed_lo, seed_hi XOR run_id), counter (0, slot,
+    TAG_INIT, word / 4) for the prior draw.  The box draw a + (b - a) u24(w)
+    is rebuilt here from the known-answer-pinned generator, word by word, so a
+    wrong key (a dropped run id), counter or word index fails."""
+    d, m = 5, 6
+    seed, run_id = (7 << 32) | 123456789, 37
+    a, b = np.linspace(-1.0, 0.0, d), np.linspace(1.0, 3.0, d)
+    pb = O.Problem(("box", a, b), "flat")
+    x, _, _ = O.init_live(pb, O.make_opts(m, 1, 1, seed=seed, run_id=run_id))
+    key = [seed & 0xFFFFFFFF, (seed >> 32) ^ run_id]
+    tag_init = 0xFFFFFFF1
+    for slot in range(m):
+        for i in range(d):
+            w = O.philox([0, slot, tag_init, i // 4], key)[i % 4]
+            assert x[slot, i] == a[i] + (b[i] - a[i]) * O.u24(w)
+    # a different run id gives a different stream
+    x2, _, _ = O.init_live(pb, O.make_opts(m, 1, 1, seed=seed, run_id=run_id + 1))
+    assert not np.array_equal(x, x2)

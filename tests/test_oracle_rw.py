@@ -110,3 +110,23 @@ def test_rw_proposal_is_scaled_metric_step(scale):
         q[c] = np.sum((Linv @ dev[c]) ** 2)
     assert stats.kstest(q, "chi2", args=(d,)).pvalue > 1e-3
     assert np.allclose(np.var(dev, axis=0), np.diag(L) ** 2, rtol=0.1)
+
+
+def test_rw_default_scale_is_2_38_over_sqrt_d():
+    """With no scale given, the random walk proposes with s = 2.38 / sqrt(d)
+    (the optimal-scaling rule the RW baseline is run with): on an
+    unconstrained flat problem one step moves every chain by s L z, so the
+    mean of |L^-1 (y - x)|^2 over the chains is s^2 d."""
+    d, m, k = 4, 3000, 1500
+    pb = O.Problem(("box", np.full(d, -1e6), np.full(d, 1e6)), "flat")
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(m, d)) * np.array([1.0, 2.0, 0.5, 3.0])
+    logL = np.zeros(m)
+    logL[:k] = -1.0  # the first k slots die; every survivor sits at 0 > logL*
+    op = O.make_opts(m, k, 1, seed=8, kernel=O.KERNEL_RW)
+    (_, _, _, _, _), tr = O.step(pb, op, 0, x, logL, np.full(m, -np.inf), -np.inf, 0.0)
+    assert np.all(tr["accepts"] == 1)
+    dlt = tr["new_x"] - x[tr["parent"]]
+    q = np.sum(np.linalg.solve(tr["L"], dlt.T) ** 2, axis=0)
+    s2 = q.mean() / d
+    assert abs(np.sqrt(s2) - 2.38 / np.sqrt(d)) < 0.05 * 2.38 / np.sqrt(d)

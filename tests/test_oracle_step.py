@@ -53,3 +53,17 @@ def test_step_is_deterministic_given_counters():
     b = O.step(pb, op, 1, *st)
     for key in ("dead_idx", "parent", "evals", "new_x", "new_logL"):
         assert np.array_equal(a[1][key], b[1][key])
+
+
+def test_step_metric_is_the_live_set_at_the_start():
+    """Reading C4: the direction metric of an iteration is the Cholesky factor
+    of the regularised covariance of all m live points before deletion."""
+    wl = W.gmm_d32(seed=2, n_live=120, k=60).with_(p=3)
+    pb, op, st = _state(wl, 1)
+    x = st[0]
+    _, tr = O.step(pb, op, 1, *st)
+    L_start, _ = O.metric(x)
+    assert np.array_equal(tr["L"], L_start)
+    survivors = np.setdiff1d(np.arange(wl.n_live), tr["dead_idx"])
+    L_surv, _ = O.metric(x[survivors])
+    assert not np.allclose(tr["L"], L_surv)

@@ -67,3 +67,13 @@ def test_null_arguments(lib):
     assert lib.nss_run(None, None) == -1
     lib.nss_destroy.argtypes = [C.c_void_p]
     lib.nss_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: with the CUDA library absent the binding raises
+    instead of computing anything."""
+    from paper_2601_23252_gb300 import native
+    monkeypatch.setattr(native, "LIB_PATH", str(tmp_path / "absent" / "libnss_gb300.so"))
+    monkeypatch.setattr(native, "_lib", None, raising=False)
+    with pytest.raises(RuntimeError):
+        native.lib()

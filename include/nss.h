@@ -359,10 +359,11 @@ nss_status nss_posterior_expectation(nss_ctx *ctx, int run, int kind, double *ou
      out[1] = its standard deviation (ddof 1),
      out[2] = the Kish effective sample size (sum w)^2 / sum w^2 of the
               geometric-mean weights at beta.
-   beta = 1 reproduces nss_run's logZ and logZ_err.  Runs the volume
-   simulation of nss_volume_sim_static on beta * logL (same limits: at most
-   524288 dead points, else NSS_ERR_ARG; it shares that entry point's scratch,
-   so it must not overlap such a call).  Synchronises the context's stream. */
+   beta = 1 reproduces nss_run's logZ and logZ_err.  beta must be finite and
+   > 0 (else NSS_ERR_ARG); a dead point with logL = -inf keeps weight 0.  Runs
+   the context's own volume simulation (its R trajectories, any number of
+   dead points) on beta * logL with per-call scratch; the run's stored
+   weights and results are unchanged.  Synchronises the context's stream. */
 nss_status nss_reweight(nss_ctx *ctx, int run, double beta, double *out);
 
 /* Volume simulation without allocation.  The paper has no counterpart: this
@@ -382,9 +383,10 @@ nss_status nss_reweight(nss_ctx *ctx, int run, double beta, double *out);
      seed, run_id             the run's Philox key, as in nss_options
      cuda_stream              stream for the work (NULL = legacy default stream)
    Limits: 1 <= n <= 524288 dead points, 2 <= n_sim <= 128; larger sizes
-   return NSS_ERR_ARG.  The first call on a device looks up the array's device
-   address (cudaGetSymbolAddress) with that device current; make it before any
-   stream capture.  Every call shares the array and leaves its contents
+   return NSS_ERR_ARG.  Every call looks up the array's device address
+   (cudaGetSymbolAddress) on the current device; the first call on a device
+   also loads the array's module there, so make it before any stream
+   capture.  Every call shares the array and leaves its contents
    behind; calls whose work overlaps on the GPU race on it, so order them.
    Returns after enqueueing (no synchronisation). */
 nss_status nss_volume_sim_static(const float *logL, const int *nlive, long long n, int n_sim,

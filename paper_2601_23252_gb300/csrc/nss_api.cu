@@ -1519,7 +1519,7 @@ nss_status nss_posterior_expectation(nss_ctx* c, int run, int kind, double* out,
 }
 
 nss_status nss_reweight(nss_ctx* c, int run, double beta, double* out) {
-  if (!c || run < 0 || run >= c->n_runs || !out || !std::isfinite(beta)) return NSS_ERR_ARG;
+  if (!c || run < 0 || run >= c->n_runs || !out || !std::isfinite(beta) || !(beta > 0.0)) return NSS_ERR_ARG;
   if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
   nss_status st = sync_state(c);
   if (st != NSS_OK) return st;
@@ -1527,6 +1527,12 @@ nss_status nss_reweight(nss_ctx* c, int run, double beta, double* out) {
   const RunDesc& R = c->desc[run];
   const long long n = c->h_state[run].n_dead;
   if (n < 1) return set_err(c, NSS_ERR_STATE, "run %d has no dead points", run);
+  // the run's tiles alone, through the context's own volume-simulation
+  // scratch (finalisation sized it for every run's tiles)
+  std::vector<int2> tiles;
+  for (long long i = 0; i < n; i += nss::kVolTile) tiles.push_back(make_int2(run, (int)i));
+  const int nt = (int)tiles.size();
+  if (nt > c->vol_cap_tiles || !c->d_vol) return set_err(c, NSS_ERR_STATE, "volume scratch not sized for run %d", run);
   float* lb = nullptr;
   double *lw = nullptr, *aux = nullptr;
   auto release = [&]() {
@@ -1541,27 +1547,39 @@ nss_status nss_reweight(nss_ctx* c, int run, double beta, double* out) {
     release();
     return cuda_fail(c, e, "reweighting scratch");
   }
-  if ((e = nss::launch_scale_logL(c->fpool + R.o_dlogL, (float)beta, n, lb, c->stream)) != cudaSuccess) {
-    release();
-    return cuda_fail(c, e, "reweighting");
+  e = nss::launch_scale_logL(c->fpool + R.o_dlogL, (float)beta, n, lb, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(int2) * nt, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_vbase + run, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) {
+    nss::VolLaunch V;
+    V.tiles = c->d_tiles;
+    V.vbase = c->d_vbase;
+    V.n_tiles = nt;
+    V.R = c->R;
+    const size_t blk = (size_t)c->R * nt;
+    V.tsum = c->d_vol;
+    V.toff = c->d_vol + blk;
+    V.tmax = c->d_vol + 2 * blk;
+    V.tacc = c->d_vol + 3 * blk;
+    V.run = run;
+    V.logL_in = lb;
+    V.lw_out = lw;
+    V.stats_out = aux;
+    e = nss::launch_volsim(dev_of(c), V, c->n_runs, c->stream);
   }
-  const uint64_t seed = ((uint64_t)R.key1 << 32) | R.key0;
-  nss_status sv = nss_volume_sim_static(lb, c->ipool + R.o_dn, n, c->R, seed, 0u, lw, aux, c->stream);
-  if (sv != NSS_OK) {
-    release();
-    return set_err(c, sv, "reweighting: %lld dead points, %d trajectories", n, c->R);
-  }
-  e = nss::launch_sq_weights(lw, n, lw + n, c->stream);
-  if (e == cudaSuccess) e = nss::launch_post_sum(lw + n, n, aux + 2, c->stream);
-  double h[3] = {0.0, 0.0, 0.0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h, aux, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = nss::launch_sq_weights(lw, n, lw + n, c->stream);
+  if (e == cudaSuccess) e = nss::launch_post_sum(lw + n, n, aux + 3, c->stream);
+  double h[4] = {0.0, 0.0, 0.0, 0.0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, aux, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   release();
   if (e != cudaSuccess) return cuda_fail(c, e, "reweighting");
-  c->prof.d2h_bytes += (long long)sizeof(double) * 3;
+  c->prof.h2d_bytes += (long long)(sizeof(int2) * nt);
+  c->prof.d2h_bytes += (long long)sizeof(double) * 4;
   out[0] = h[0];
   out[1] = h[1];
-  out[2] = 1.0 / h[2];
+  out[2] = 1.0 / h[3];
   return NSS_OK;
 }
 

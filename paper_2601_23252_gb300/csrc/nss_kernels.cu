@@ -421,10 +421,16 @@ struct VolArgs {
   const int2* tiles;   // (run, first dead index) per tile
   const int* vbase;    // first tile of each run
   int n_tiles, R;
+  int run0;            // block b of the per-run kernels serves run run0 + b
   double* tsum;        // [R][n_tiles] sum of the tile's terms
   double* toff;        // [R][n_tiles] log X before the tile
   double* tmax;        // [R][n_tiles] running log-sum-exp max of log w
   double* tacc;        // [R][n_tiles] running log-sum-exp sum
+  // reweighting (one run): logL read from logL_in and the weights and
+  // statistics written to lw_out / stats_out instead of the run's own store
+  const float* logL_in;
+  double* lw_out;
+  double* stats_out;   // logZ mean, std, weight norm
 };
 
 __global__ void k_vol_tilesum(Dev D, VolArgs A) {
@@ -445,7 +451,7 @@ __global__ void k_vol_tilesum(Dev D, VolArgs A) {
 // exclusive scan of tile sums per (run, trajectory); tiles of a run are
 // contiguous starting at vbase[run]
 __global__ void k_vol_scan(Dev D, VolArgs A, int n_runs) {
-  const int run = blockIdx.x, r = threadIdx.x;
+  const int run = A.run0 + blockIdx.x, r = threadIdx.x;
   if (r >= A.R || run >= n_runs) return;
   const long long n = D.st[run].n_dead;
   const int nt = (int)((n + kVolTile - 1) / kVolTile);
@@ -477,8 +483,8 @@ __global__ void k_vol_weights(Dev D, VolArgs A) {
   const long long n = D.st[t.x].n_dead;
   const long long i0 = t.y, i1 = min((long long)t.y + kVolTile, n);
   const int* nl = D.i + R.o_dn;
-  const float* lL = D.f + R.o_dlogL;
-  double* lw = D.dd + R.o_lw;
+  const float* lL = A.logL_in ? A.logL_in : D.f + R.o_dlogL;
+  double* lw = A.lw_out ? A.lw_out : D.dd + R.o_lw;
   const bool act = r < A.R;
   // the tile's largest logL, and the mean over r of log X at the tile start
   float lm = -INFINITY;
@@ -536,7 +542,7 @@ __global__ void k_vol_weights(Dev D, VolArgs A) {
 
 // per run: log Z^(r), their mean and standard deviation, the weight norm
 __global__ void k_vol_final(Dev D, VolArgs A, int n_runs) {
-  const int run = blockIdx.x;
+  const int run = A.run0 + blockIdx.x;
   if (run >= n_runs) return;
   const RunDesc& R = D.desc[run];
   RunState& S = D.st[run];
@@ -562,7 +568,7 @@ __global__ void k_vol_final(Dev D, VolArgs A, int n_runs) {
   for (int r = threadIdx.x; r < A.R; r += blockDim.x) var += (lz[r] - mean) * (lz[r] - mean);
   var = block_sum_d(var, red) / (A.R > 1 ? A.R - 1 : 1);
   // normalisation of the geometric-mean weights
-  const double* lw = D.dd + R.o_lw;
+  const double* lw = A.lw_out ? A.lw_out : D.dd + R.o_lw;
   double mx = -INFINITY;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, lw[i]);
   mx = block_max_d(mx, red);
@@ -570,17 +576,23 @@ __global__ void k_vol_final(Dev D, VolArgs A, int n_runs) {
   for (long long i = threadIdx.x; i < n; i += blockDim.x) s += (double)expf((float)(lw[i] - mx));
   s = block_sum_d(s, red);
   if (threadIdx.x == 0) {
-    S.logZ_mean = mean;
-    S.logZ_std = sqrt(var);
-    S.lw_norm = mx + log(s);
+    if (A.stats_out) {
+      A.stats_out[0] = mean;
+      A.stats_out[1] = sqrt(var);
+      A.stats_out[2] = mx + log(s);
+    } else {
+      S.logZ_mean = mean;
+      S.logZ_std = sqrt(var);
+      S.lw_norm = mx + log(s);
+    }
   }
 }
 
-__global__ void k_vol_norm(Dev D, int run) {
+__global__ void k_vol_norm(Dev D, int run, double* lw_out, const double* stats_out) {
   const RunDesc& R = D.desc[run];
   const RunState& S = D.st[run];
-  double* lw = D.dd + R.o_lw;
-  const double c = S.lw_norm;
+  double* lw = lw_out ? lw_out : D.dd + R.o_lw;
+  const double c = stats_out ? stats_out[2] : S.lw_norm;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.n_dead;
        i += (long long)gridDim.x * blockDim.x)
     lw[i] -= c;
@@ -623,18 +635,25 @@ cudaError_t launch_volsim(const Dev& D, const VolLaunch& V, int n_runs, cudaStre
   A.toff = V.toff;
   A.tmax = V.tmax;
   A.tacc = V.tacc;
+  A.logL_in = V.logL_in;
+  A.lw_out = V.lw_out;
+  A.stats_out = V.stats_out;
+  // one run (reweighting) or all of them
+  const bool one = V.run >= 0;
+  A.run0 = one ? V.run : 0;
+  const int nb = one ? 1 : n_runs;
   const int bt = (V.R + 31) / 32 * 32;
   k_vol_tilesum<<<V.n_tiles, bt, 0, s>>>(D, A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_vol_scan<<<n_runs, bt, 0, s>>>(D, A, n_runs);
+  k_vol_scan<<<nb, bt, 0, s>>>(D, A, n_runs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_vol_weights<<<V.n_tiles, bt, (size_t)bt * 32 * sizeof(float), s>>>(D, A);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_vol_final<<<n_runs, 256, 0, s>>>(D, A, n_runs);
+  k_vol_final<<<nb, 256, 0, s>>>(D, A, n_runs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  for (int r = 0; r < n_runs; ++r) {
-    k_vol_norm<<<64, 256, 0, s>>>(D, r);
+  for (int r = A.run0; r < A.run0 + nb; ++r) {
+    k_vol_norm<<<64, 256, 0, s>>>(D, r, A.lw_out, A.stats_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

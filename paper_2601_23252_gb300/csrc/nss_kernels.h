@@ -13,6 +13,13 @@ struct VolLaunch {
   const int* vbase;
   int n_tiles, R;
   double *tsum, *toff, *tmax, *tacc;
+  // reweighting: run >= 0 simulates that run alone, reading logL_in and
+  // writing its log weights to lw_out and (logZ mean, std, norm) to
+  // stats_out; run = -1 serves every run from and into its own store
+  int run = -1;
+  const float* logL_in = nullptr;
+  double* lw_out = nullptr;
+  double* stats_out = nullptr;
 };
 
 // Device workspace of one logistic-regression run (line-affine logits).

@@ -15,7 +15,6 @@
 // has to start at zero.  Two calls whose kernels overlap on the GPU (for
 // example on two streams) race on it; the caller must order them.
 #include <cmath>
-#include <mutex>
 
 #include "../../include/nss.h"
 #include "nss_device.cuh"
@@ -160,23 +159,16 @@ __global__ void k_svol_norm(StaticVol V, double* __restrict__ lw) {
     lw[i] -= c;
 }
 
-// device address of the scratch array, looked up once per device
-std::mutex g_mu;
-double* g_dev_ptr[64] = {};
-
+// Device address of the scratch array for the current device, looked up on
+// every call (cheap), so a device context that was reset or re-created since
+// an earlier call never gets a stale address.  The first lookup on a device
+// loads the array's module there, so make the first call on each device
+// before any stream capture.
 cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_vol_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_vol_scratch);
-    if (e != cudaSuccess) return e;
-    g_dev_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_dev_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -190,6 +182,7 @@ extern "C" nss_status nss_volume_sim_static(const float* logL, const int* nlive,
   if (!logL || !nlive || !log_w || !logZ_stats) return NSS_ERR_ARG;
   if (n < 1 || n > kStaticMaxDead) return NSS_ERR_ARG;
   if (n_sim < 2 || n_sim > kStaticMaxSim) return NSS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double* scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) return NSS_ERR_CUDA;
@@ -206,7 +199,6 @@ extern "C" nss_status nss_volume_sim_static(const float* logL, const int* nlive,
   V.tmax = scratch + 2 * kStaticSlab;
   V.tacc = scratch + 3 * kStaticSlab;
   V.misc = scratch + 4 * kStaticSlab;
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int bt = (n_sim + 31) / 32 * 32;
   k_svol_tilesum<<<V.nt, bt, 0, s>>>(V);
   k_svol_scan<<<1, bt, 0, s>>>(V);

@@ -102,7 +102,7 @@ __global__ void k_post_vec(PostArgs A, const double* __restrict__ coef, double* 
 
 __global__ void k_scale_logL(const float* __restrict__ logL, float beta, long long n, float* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = beta * logL[i];
+    out[i] = logL[i] > -INFINITY ? beta * logL[i] : -INFINITY;  // beta > 0; -inf and NaN keep weight 0
 }
 
 __global__ void k_sq_weights(const double* __restrict__ lw, long long n, double* __restrict__ out) {

@@ -167,3 +167,24 @@ def test_reweighting_to_other_temperatures(gpu_lib):
     dev = np.array(dev)
     print(f"\nbeta = 0.5: closed form {t_half:.4f}, dev/err {np.round(dev, 2)}")
     assert np.all(np.abs(dev) < 4.0)
+
+
+def test_reweighting_with_many_trajectories_and_beta_range(gpu_lib):
+    """nss_reweight runs the context's own volume simulation: a run with 300
+    simulated trajectories (more than the fixed-scratch entry point takes)
+    reweights at beta = 1 to its own logZ and error, its stored weights stay
+    untouched, and beta outside (0, inf) is rejected."""
+    wl = _gauss_box(3).with_(extra={"options": {"n_sim": 300}})
+    with native.Sampler(wl) as smp:
+        res = smp.run()[0]
+        lw0 = smp.dead(0)["log_w"].copy()
+        one = smp.reweight(1.0, 0)
+        assert one["logZ"] == pytest.approx(res["logZ"], abs=1e-6)
+        assert one["logZ_err"] == pytest.approx(res["logZ_err"], abs=1e-6)
+        hot = smp.reweight(2.0, 0)
+        assert np.isfinite(hot["logZ"]) and hot["ess"] < one["ess"]
+        assert np.array_equal(smp.dead(0)["log_w"], lw0)
+        for bad in (0.0, -1.0, float("nan"), float("inf")):
+            with pytest.raises(native.NSSError) as e:
+                smp.reweight(bad, 0)
+            assert e.value.status == -1

@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NSS_ABI_VERSION 4
+#define NSS_ABI_VERSION 5
 
 typedef struct nss_ctx nss_ctx;
 
@@ -147,7 +147,28 @@ typedef struct {
     int kernel;                /* NSS_KERNEL_HRSS (the paper's NSS) or
                                   NSS_KERNEL_RW (constrained random walk)       */
     double rw_scale;           /* RW proposal x + rw_scale * L z; 0 = 2.38/sqrt(d) */
+    int path;                  /* NSS_PATH_BATCHED (default) or NSS_PATH_PLAIN   */
+    int run_groups;            /* batched path: 0 = automatic (two streams when
+                                  every run uses the generic sweep), 1 = one    */
 } nss_options;
+
+/* Execution paths.  BATCHED: the device-resident batched sweep (persistent
+   chain-group kernels, directions drawn ahead, outer iterations replayed
+   from CUDA graphs, many runs per launch).  PLAIN: the plain single-run FP32
+   GPU path that the batched sweep is measured against -- one kernel per
+   phase of an outer iteration (selection; dead append and evidence; metric;
+   parents; directions; one HRSS kernel launch per step; termination), the
+   run's k chains as one thread each advancing in lockstep evaluation rounds
+   (every chain evaluates one candidate per round, as one batched likelihood
+   call over the k chains does, Sec. 3.1 "Vectorised execution"), every
+   candidate's likelihood evaluated from scratch over all d coordinates, and
+   a host loop that waits for each iteration.  Its FP32 expressions follow
+   the batched sweep's in the run's sweep configuration, so both paths give
+   bit-identical dead points for the same configuration.  PLAIN requires a
+   single run (nss_create or n_runs = 1), the HRSS kernel, a Gaussian,
+   mixture or flat likelihood, k <= 1024 and a grouped sweep configuration
+   (sweep_cfg < 22; -1 picks the default one); otherwise NSS_ERR_ARG. */
+enum { NSS_PATH_BATCHED = 0, NSS_PATH_PLAIN = 1 };
 
 /* Replacement kernels.  HRSS: hit-and-run slice sampling (Sec. 3.2).  RW:
    the constrained Gaussian random-walk baseline (Sec. 3.1 "Vectorised
@@ -162,7 +183,7 @@ enum { NSS_KERNEL_HRSS = 0, NSS_KERNEL_RW = 1 };
 
 /* Fills the paper's defaults: w = 1, MAHAL, tol = 1e-3, max_iter = 100000,
    n_sim = 100, cov_eps = 1e-6, seed 0, run_id 0, default stream,
-   default sweep configuration. */
+   default sweep configuration, the batched path, automatic run groups. */
 void nss_options_default(nss_options *opt);
 
 /* Per-run state after a step. */
@@ -222,16 +243,27 @@ typedef struct {
 } nss_trace;
 
 /* Per-kernel timing collected while profiling is on (CUDA events on the
-   context's stream around every launch of that kernel). */
+   stream of every launch of that kernel, around the launch).  With two run
+   groups the groups' launches overlap in time, so the per-kind sums can
+   exceed the wall time; a context with run_groups = 1 serialises them. */
+#define NSS_PROFILE_KINDS 12
 typedef struct {
-    long long launches[8];
-    double ms[8];          /* summed event time                           */
+    long long launches[NSS_PROFILE_KINDS];
+    double ms[NSS_PROFILE_KINDS];          /* summed event time           */
     long long total_launches;
     long long h2d_bytes;   /* host-to-device bytes copied by the library   */
     long long d2h_bytes;   /* device-to-host bytes copied by the library   */
 } nss_profile;
+/* INIT prior draw; PROLOGUE selection, evidence, metric, parents (one
+   kernel, or the plain path's four); SWEEP the HRSS sweep (generic
+   likelihoods; the plain path's per-step kernel); TERMINATE; FINAL_SORT;
+   VOLSIM every volume-simulation kernel; DIRGEN the directions drawn ahead;
+   LOGITS the tensor-core logistic contraction; LR_SLICE the logistic slice
+   kernel; GP_SWEEP the GP sweep; OTHER the logistic helpers (centre,
+   parents, directions, replacement).  Kind 6 is unused. */
 enum { NSS_K_INIT = 0, NSS_K_PROLOGUE = 1, NSS_K_SWEEP = 2, NSS_K_TERMINATE = 3,
-       NSS_K_FINAL_SORT = 4, NSS_K_VOLSIM = 5, NSS_K_WEIGHTS = 6, NSS_K_OTHER = 7 };
+       NSS_K_FINAL_SORT = 4, NSS_K_VOLSIM = 5, NSS_K_WEIGHTS = 6, NSS_K_OTHER = 7,
+       NSS_K_DIRGEN = 8, NSS_K_LOGITS = 9, NSS_K_LR_SLICE = 10, NSS_K_GP_SWEEP = 11 };
 
 /* Create a single-run context: copies the problem to the device and draws
    the m initial live points from the prior (Sec. 2.1).  n_live = m >= 2,

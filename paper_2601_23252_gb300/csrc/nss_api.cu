@@ -118,6 +118,7 @@ struct nss_ctx {
   double tune_cost[nss::kNumCfgs] = {};
   int max_p = 1;   // last autotune: device ms per 1e6 evaluations
   long long launches = 0;
+  bool plain = false;   // the plain single-run path (NSS_PATH_PLAIN)
   bool broken = false;
   std::string err;
 };
@@ -314,6 +315,15 @@ nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m
     if (lk.kind == NSS_LOGLIK_LOGREG || lk.kind == NSS_LOGLIK_GP_RBF_WHITE)
       return set_err(c, NSS_ERR_ARG, "run %d: the random-walk kernel takes Gaussian, mixture or flat likelihoods", run);
   }
+  if (o.path != NSS_PATH_BATCHED && o.path != NSS_PATH_PLAIN) return set_err(c, NSS_ERR_ARG, "run %d: unknown path", run);
+  if (o.run_groups != 0 && o.run_groups != 1) return set_err(c, NSS_ERR_ARG, "run %d: run_groups must be 0 or 1", run);
+  if (o.path == NSS_PATH_PLAIN) {
+    if (o.kernel != NSS_KERNEL_HRSS) return set_err(c, NSS_ERR_ARG, "run %d: the plain path runs the HRSS kernel", run);
+    if (lk.kind != NSS_LOGLIK_GAUSS_ISO && lk.kind != NSS_LOGLIK_GMM_ISO_EQUAL && lk.kind != NSS_LOGLIK_FLAT)
+      return set_err(c, NSS_ERR_ARG, "run %d: the plain path takes Gaussian, mixture or flat likelihoods", run);
+    if (k > 1024) return set_err(c, NSS_ERR_ARG, "run %d: the plain path takes k <= 1024", run);
+    if (o.sweep_cfg >= nss::kLaneCfg0) return set_err(c, NSS_ERR_ARG, "run %d: the plain path takes a grouped sweep configuration", run);
+  }
   if (o.sweep_cfg >= 0) {
     bool fits = false;
     for (int q : candidate_cfgs(pr.d)) fits |= (q == o.sweep_cfg);
@@ -459,7 +469,7 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
   for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
     const int L = g * nss_ctx::kDirClasses + q;
     if (c->dir_items[L].empty()) continue;
-    Rec rd(c, NSS_K_OTHER);
+    Rec rd(c, NSS_K_DIRGEN);
     CK(nss::launch_dirgen(8 << q, D, c->d_dir[L], (int)c->dir_items[L].size(), c->max_p, st),
        "direction launch");
   }
@@ -474,30 +484,76 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
   if (g == 0) {  // logistic and GP runs keep one group
     for (auto& gw : c->gp) {
       const RunDesc& R = c->desc[gw.run];
-      Rec r(c, NSS_K_SWEEP);
+      Rec r(c, NSS_K_GP_SWEEP);
       CK(nss::launch_gp_sweep(D, gw.args, gw.run, R.k, R.n_data, st), "GP sweep launch");
     }
     for (auto& w : c->lr) {
       const RunDesc& R = c->desc[w.run];
       const int* done = &c->d_state[w.run].done;
-      Rec r(c, NSS_K_OTHER);
-      CK(nss::launch_lr_center(D, w.args, w.run, R.n_data, st), "logistic centre launch");
-      CK(nss::launch_lr_parents(D, w.args, w.run, R.k, st), "logistic parents launch");
-      CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.k, w.err, done,
-                            w.zref, st), "logits launch");
-      for (int s = 0; s < R.p; ++s) {
-        CK(nss::launch_lr_dir(D, w.args, w.run, R.k, s, st), "logistic direction launch");
-        CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zv, w.rows_pad, R.n_data, R.k, w.err, done,
-                              nullptr, st), "logits launch");
-        CK(nss::launch_lr_slice(D, w.args, w.run, R.k, s, w.emax, st), "logistic slice launch");
+      {
+        Rec r(c, NSS_K_OTHER);
+        CK(nss::launch_lr_center(D, w.args, w.run, R.n_data, st), "logistic centre launch");
       }
-      CK(nss::launch_lr_replace(D, w.args, w.run, R.k, st), "logistic replace launch");
-      c->launches += 5 + 3LL * R.p;
+      {
+        Rec r(c, NSS_K_OTHER);
+        CK(nss::launch_lr_parents(D, w.args, w.run, R.k, st), "logistic parents launch");
+      }
+      {
+        Rec r(c, NSS_K_LOGITS);
+        CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.k, w.err, done,
+                              w.zref, st), "logits launch");
+      }
+      for (int s = 0; s < R.p; ++s) {
+        {
+          Rec r(c, NSS_K_OTHER);
+          CK(nss::launch_lr_dir(D, w.args, w.run, R.k, s, st), "logistic direction launch");
+        }
+        {
+          Rec r(c, NSS_K_LOGITS);
+          CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zv, w.rows_pad, R.n_data, R.k, w.err,
+                                done, nullptr, st), "logits launch");
+        }
+        {
+          Rec r(c, NSS_K_LR_SLICE);
+          CK(nss::launch_lr_slice(D, w.args, w.run, R.k, s, w.emax, st), "logistic slice launch");
+        }
+      }
+      {
+        Rec r(c, NSS_K_OTHER);
+        CK(nss::launch_lr_replace(D, w.args, w.run, R.k, st), "logistic replace launch");
+      }
     }
   }
   {
     Rec r(c, NSS_K_TERMINATE);
     CK(nss::launch_terminate(D, r0, nr, st), "terminate launch");
+  }
+  return NSS_OK;
+}
+
+// One outer iteration of the plain single-run path (NSS_PATH_PLAIN): one
+// launch per phase, one HRSS launch per step, on c->stream.
+nss_status enqueue_plain_iteration(nss_ctx* c) {
+  nss::Dev D = dev_of(c);
+  const RunDesc& R = c->desc[0];
+  cudaStream_t st = c->stream;
+  for (int ph = 0; ph < 4; ++ph) {
+    Rec r(c, NSS_K_PROLOGUE);
+    CK(nss::launch_plain_phase(ph, D, 0, R.k, c->prologue_smem, st), "plain phase launch");
+  }
+  for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
+    if (c->dir_items[q].empty()) continue;
+    Rec rd(c, NSS_K_DIRGEN);
+    CK(nss::launch_dirgen(8 << q, D, c->d_dir[q], (int)c->dir_items[q].size(), c->max_p, st), "direction launch");
+  }
+  const int G = nss::cfg_g(R.cfg), DPL = nss::cfg_dpl(R.cfg);
+  for (int s = 0; s < R.p; ++s) {
+    Rec r(c, NSS_K_SWEEP, R.cfg);
+    CK(nss::launch_plain_hrss(D, 0, R.k, s, G, DPL, st), "plain HRSS launch");
+  }
+  {
+    Rec r(c, NSS_K_TERMINATE);
+    CK(nss::launch_terminate(D, 0, 1, st), "terminate launch");
   }
   return NSS_OK;
 }
@@ -559,7 +615,7 @@ nss_status run_iteration(nss_ctx* c, int n = 1) {
     g.n = n;
     g.prof = c->profiling;
     const long long l0 = c->launches, t0 = c->prof.total_launches;
-    long long k0[8];
+    long long k0[NSS_PROFILE_KINDS];
     std::memcpy(k0, c->prof.launches, sizeof k0);
     c->cap_evs.clear();
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
@@ -910,6 +966,8 @@ void nss_options_default(nss_options* o) {
   o->sweep_cfg = -1;
   o->kernel = NSS_KERNEL_HRSS;
   o->rw_scale = 0.0;
+  o->path = NSS_PATH_BATCHED;
+  o->run_groups = 0;
 }
 
 int nss_abi_version(void) { return NSS_ABI_VERSION; }
@@ -1020,10 +1078,16 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   }
   c->R = opt[0].n_sim;
   for (int r = 1; r < n_runs; ++r)
-    if (opt[r].n_sim != c->R) {
+    if (opt[r].n_sim != c->R || opt[r].path != opt[0].path || opt[r].run_groups != opt[0].run_groups) {
       delete c;
       return NSS_ERR_ARG;
     }
+  c->plain = opt[0].path == NSS_PATH_PLAIN;
+  if (c->plain && n_runs != 1) {
+    delete c;
+    std::fprintf(stderr, "nss_create: the plain path runs a single run\n");
+    return NSS_ERR_ARG;
+  }
   c->stream = static_cast<cudaStream_t>(opt[0].cuda_stream);
   if (!c->stream) {
     cudaError_t es = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
@@ -1127,6 +1191,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
       const bool own = lk.kind != NSS_LOGLIK_LOGREG && lk.kind != NSS_LOGLIK_GP_RBF_WHITE;
       R.o_wd = c->ni; c->ni += own ? align16((long long)R.k * R.p * nss::kStepWords) : 16;
     }
+    R.o_surv = c->ni; c->ni += align16(R.m);
     // FP64 pool
     R.o_cum = c->nd; c->nd += align16(R.m + 1);
     R.o_lnd = c->nd; c->nd += align16(R.m);
@@ -1217,7 +1282,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   // run groups: two streams when every run uses the generic sweep, split
   // into contiguous halves of about equal sweep cost
   {
-    bool generic = n_runs >= 2;
+    bool generic = n_runs >= 2 && !c->plain && opt[0].run_groups == 0;
     double total = 0.0;
     for (int r = 0; r < n_runs; ++r) {
       const RunDesc& R = c->desc[r];
@@ -1301,7 +1366,7 @@ nss_status nss_step(nss_ctx* c, nss_step_info* info) {
   nss_status st = sync_state(c);
   if (st != NSS_OK) return st;
   if (!all_done(c)) {
-    if ((st = run_iteration(c)) != NSS_OK) return st;
+    if ((st = c->plain ? enqueue_plain_iteration(c) : run_iteration(c)) != NSS_OK) return st;
     if ((st = sync_state(c)) != NSS_OK) return st;
   }
   fill_info(c, info);
@@ -1315,6 +1380,14 @@ nss_status nss_run(nss_ctx* c, nss_result* res) {
   if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
   nss_status st = sync_state(c);
   if (st != NSS_OK) return st;
+  if (c->plain) {
+    // the plain path's host loop waits for every iteration
+    while (!all_done(c)) {
+      if ((st = enqueue_plain_iteration(c)) != NSS_OK) return st;
+      if ((st = sync_state(c)) != NSS_OK) return st;
+    }
+    return finalise_impl(c, res);
+  }
   int chunk = 4;
   while (!all_done(c)) {
     if ((st = run_iteration(c, chunk)) != NSS_OK) return st;
@@ -1371,6 +1444,7 @@ nss_status nss_set_cfg(nss_ctx* c, int run, int cfg) {
   bool fits = false;
   for (int q : candidate_cfgs(c->desc[run].d)) fits |= (q == cfg);
   if (!fits) return set_err(c, NSS_ERR_ARG, "configuration %d does not fit d=%d", cfg, c->desc[run].d);
+  if (c->plain && cfg >= nss::kLaneCfg0) return set_err(c, NSS_ERR_ARG, "the plain path takes a grouped configuration");
   nss_status st = sync_state(c);
   if (st != NSS_OK) return st;
   c->desc[run].cfg = cfg;
@@ -1379,6 +1453,7 @@ nss_status nss_set_cfg(nss_ctx* c, int run, int cfg) {
 
 nss_status nss_autotune(nss_ctx* c, int iters, int* cfg_out) {
   if (!c || iters < 1) return NSS_ERR_ARG;
+  if (c->plain) return set_err(c, NSS_ERR_ARG, "the plain path is not autotuned");
   if (c->broken) return set_err(c, NSS_ERR_STATE, "context is unusable after an earlier CUDA error");
   nss_status st = sync_state(c);
   if (st != NSS_OK) return st;

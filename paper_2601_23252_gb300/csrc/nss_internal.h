@@ -19,7 +19,8 @@ constexpr uint32_t kTagInit = 0xFFFFFFF1u;
 constexpr uint32_t kTagVolsim = 0xFFFFFFF2u;
 constexpr int kPrologueThreads = 1024;  // one block per run; fixed, so every context reduces in the same order
 constexpr int kNumCfgs = 25;
-constexpr int kStepWords = 12;      // a step's scalar words drawn ahead: U, height, reserved, shrink 0..8        // sweep configurations: 22 grouped (G lanes x DPL dims), 3 lane-per-chain
+constexpr int kLaneCfg0 = 22;       // configurations 22..24 run one chain per lane
+constexpr int kStepWords = 12;      // a step's scalar words drawn ahead: U, height, reserved, shrink 0..8
 constexpr int kVolTile = 1024;      // dead points per volume-simulation tile
 
 enum PriorKind { kPriorBox = 0, kPriorGauss = 1 };
@@ -50,6 +51,7 @@ struct RunDesc {
   long long o_dead, o_parent;       // [k] each
   long long o_stats;                // [6][k] evals, accepts, nulls, expansions, shrinks, cap_out
   long long o_wd;                   // [k][p][kStepWords] words nz .. nz+11 of each step's counter stream
+  long long o_surv;                 // [m] survivors in slot order (plain single-run path)
   // FP64 pool offsets
   long long o_cum, o_lnd;           // [m+1]: sum_{j'<j} 1/(m-j'); [m]: log(-expm1(-1/(m-j)))
   long long o_lw;                   // [dead_cap] log posterior weights

@@ -55,24 +55,31 @@ __device__ void evidence_update(const RunDesc& R, RunState& S, const float* __re
   __syncthreads();
 }
 
-// Append the first `cnt` entries of the sorted key list to the dead store.
-__device__ void append_dead(const Dev& D, const RunDesc& R, RunState& S,
-                            const unsigned long long* keys, int cnt) {
+// Append `cnt` dead slots, worst first, to the dead store; slot_of(j) is
+// the j-th dead slot.
+template <class SlotOf>
+__device__ void append_dead_by(const Dev& D, const RunDesc& R, RunState& S, SlotOf slot_of, int cnt) {
   const long long base = S.n_dead;
   const int q4 = R.dpad >> 2;
   const float4* xs = reinterpret_cast<const float4*>(D.f + R.o_x);
   float4* xd = reinterpret_cast<float4*>(D.f + R.o_dx + base * R.dpad);
   for (int t = threadIdx.x; t < cnt * q4; t += blockDim.x) {
     const int j = t / q4, c = t - j * q4;
-    const int slot = (int)(keys[j] & 0xffffffffu);
+    const int slot = slot_of(j);
     xd[(long long)j * q4 + c] = xs[(long long)slot * q4 + c];
   }
   for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-    const int slot = (int)(keys[j] & 0xffffffffu);
+    const int slot = slot_of(j);
     D.f[R.o_dlogL + base + j] = D.f[R.o_logL + slot];
     D.f[R.o_dbirth + base + j] = D.f[R.o_birth + slot];
     D.i[R.o_dn + base + j] = R.m - j;
   }
+}
+
+// ... from the first `cnt` entries of the sorted key list
+__device__ void append_dead(const Dev& D, const RunDesc& R, RunState& S,
+                            const unsigned long long* keys, int cnt) {
+  append_dead_by(D, R, S, [keys](int j) { return (int)(keys[j] & 0xffffffffu); }, cnt);
 }
 
 // Cholesky factor of S + reg I ([ld][ld] in shared memory) into Lm
@@ -348,6 +355,89 @@ __global__ void __launch_bounds__(kPrologueThreads) k_prologue(Dev D, int run0) 
 }
 
 // ---------------------------------------------------------------------------
+// The plain single-run path: the prologue's phases as separate kernels, one
+// block of kPrologueThreads threads each, calling the same device functions
+// (so every reduction runs in the same order and the results are
+// bit-identical to k_prologue's).
+// ---------------------------------------------------------------------------
+// (i) selection: dead slots worst first, logL*, survivors in slot order
+__global__ void __launch_bounds__(kPrologueThreads) k_plain_select(Dev D, int run) {
+  const RunDesc& R = D.desc[run];
+  RunState& S = D.st[run];
+  if (S.done) return;
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int red_i[32];
+  __shared__ int cap_fail;
+  const int m = R.m, k = R.k, m2 = R.m2;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);
+  int* flag = reinterpret_cast<int*>(smem + (size_t)m2 * 8);
+  const float* logL = D.f + R.o_logL;
+  for (int i = threadIdx.x; i < m2; i += blockDim.x) keys[i] = (i < m) ? sort_key(logL[i], i) : ~0ull;
+  if (m2 <= (int)blockDim.x) bitonic_sort_reg(keys, m2);
+  else bitonic_sort(keys, m2);
+  int* dead = D.i + R.o_dead;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) dead[j] = (int)(keys[j] & 0xffffffffu);
+  if (threadIdx.x == 0) {
+    S.logLstar = logL[(int)(keys[k - 1] & 0xffffffffu)];
+    cap_fail = (S.n_dead + k > R.dead_cap);
+  }
+  __syncthreads();
+  if (cap_fail) {
+    if (threadIdx.x == 0) {
+      S.done = 1;
+      S.status = -4;
+    }
+    return;
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) flag[i] = 1;
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) flag[(int)(keys[j] & 0xffffffffu)] = 0;
+  __syncthreads();
+  int* surv = D.i + R.o_surv;
+  const int per = (m + blockDim.x - 1) / blockDim.x;
+  const int i0 = threadIdx.x * per;
+  int c = 0;
+  for (int i = i0; i < min(i0 + per, m); ++i) c += flag[i];
+  int tot;
+  int pos = block_exscan_i(c, red_i, &tot);
+  for (int i = i0; i < min(i0 + per, m); ++i)
+    if (flag[i]) surv[pos++] = i;
+}
+
+// dead-point append and the unrolled evidence update
+__global__ void __launch_bounds__(kPrologueThreads) k_plain_evidence(Dev D, int run) {
+  const RunDesc& R = D.desc[run];
+  RunState& S = D.st[run];
+  if (S.done) return;
+  __shared__ double red_d[32];
+  const int* dead = D.i + R.o_dead;
+  append_dead_by(D, R, S, [dead](int j) { return dead[j]; }, R.k);
+  __syncthreads();
+  evidence_update(R, S, D.f + R.o_dlogL + S.n_dead, D.dd + R.o_cum, D.dd + R.o_lnd, R.k, red_d);
+  if (threadIdx.x == 0) S.n_dead += R.k;
+}
+
+// direction metric of the live set at the start of the iteration
+__global__ void __launch_bounds__(kPrologueThreads) k_plain_metric(Dev D, int run) {
+  const RunDesc& R = D.desc[run];
+  RunState& S = D.st[run];
+  if (S.done) return;
+  extern __shared__ __align__(16) char smem[];
+  live_metric(D, R, S, smem);
+}
+
+// (ii) parents uniformly with replacement among the m-k survivors
+__global__ void k_plain_parents(Dev D, int run) {
+  const RunDesc& R = D.desc[run];
+  const RunState& S = D.st[run];
+  if (S.done) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= R.k) return;
+  const uint32_t w = draw_block(R, (uint32_t)S.iter, (uint32_t)j, kTagParent, 0u).x;
+  D.i[R.o_parent + j] = D.i[R.o_surv + __umulhi(w, (uint32_t)(R.m - R.k))];
+}
+
+// ---------------------------------------------------------------------------
 // Termination (App. B.3, reading: live fraction): Z_live = X mean(L_live);
 // stop when Z_live / (Z + Z_live) < tol.  Also counts the iteration.
 // ---------------------------------------------------------------------------
@@ -604,6 +694,10 @@ __global__ void k_vol_norm(Dev D, int run, double* lw_out, const double* stats_o
 cudaError_t setup_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_plain_select, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_plain_metric, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   // up to 1024 trajectories: [1024][32] FP32 offsets
   e = cudaFuncSetAttribute(k_vol_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 * 32 * (int)sizeof(float));
   if (e != cudaSuccess) return e;
@@ -612,6 +706,17 @@ cudaError_t setup_kernel_attributes() {
 
 cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s) {
   k_prologue<<<n_runs, kPrologueThreads, smem, s>>>(D, run0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_phase(int phase, const Dev& D, int run, int k, size_t smem, cudaStream_t s) {
+  switch (phase) {
+    case 0: k_plain_select<<<1, kPrologueThreads, smem, s>>>(D, run); break;
+    case 1: k_plain_evidence<<<1, kPrologueThreads, 0, s>>>(D, run); break;
+    case 2: k_plain_metric<<<1, kPrologueThreads, smem, s>>>(D, run); break;
+    case 3: k_plain_parents<<<(k + 255) / 256, 256, 0, s>>>(D, run); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -95,6 +95,12 @@ cudaError_t launch_sweep(int cfg, int kc, const Dev& D, const WorkItem* items, i
                          cudaStream_t s);
 int sweep_kc(int lik_kind, int n_comp);
 cudaError_t launch_terminate(const Dev& D, int run0, int n_runs, cudaStream_t s);
+// the plain single-run path (nss_plain.cu and its phase kernels): phase 0
+// selection, 1 dead append + evidence, 2 metric, 3 parents of run `run`
+cudaError_t launch_plain_phase(int phase, const Dev& D, int run, int k, size_t smem, cudaStream_t s);
+// HRSS step s of every chain of run `run`, one thread per chain (k <= 1024),
+// lockstep evaluation rounds; arithmetic of sweep configuration (G, DPL)
+cudaError_t launch_plain_hrss(const Dev& D, int run, int k, int s, int G, int DPL, cudaStream_t st);
 cudaError_t launch_final_sort(const Dev& D, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_volsim(const Dev& D, const VolLaunch& V, int n_runs, cudaStream_t s);
 int sweep_blocks_per_sm(int cfg, int kc);

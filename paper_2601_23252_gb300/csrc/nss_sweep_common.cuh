@@ -168,8 +168,7 @@ constexpr int kSweepThreads = 32;   // one warp per block: resident warps per SM
   X(15, 2, 8) X(16, 4, 8) X(17, 8, 8) X(18, 16, 8) \
   X(19, 2, 16) X(20, 4, 16) X(21, 8, 16)
 
-// configurations 22..24: one chain per lane (nss_sweep_lane.cu), d <= 8, 16, 32
-constexpr int kLaneCfg0 = 22;
+// configurations kLaneCfg0..24: one chain per lane (nss_sweep_lane.cu), d <= 8, 16, 32
 inline int lane_dmax(int cfg) { return cfg == 22 ? 8 : cfg == 23 ? 16 : 32; }
 
 

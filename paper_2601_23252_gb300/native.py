@@ -23,7 +23,10 @@ STATUS = {0: "ok", 1: "done", -1: "invalid argument", -2: "CUDA error", -3: "out
           -7: "call out of order"}
 PRIOR = {"box": 0, "gauss": 1}
 LOGLIK = {"gauss": 0, "gmm": 1, "logreg": 2, "gp": 3, "flat": 4, "fault": 5, "rastrigin": 6}
-K_NAMES = ["init", "prologue", "sweep", "terminate", "final_sort", "volsim", "weights", "other"]
+K_NAMES = ["init", "prologue", "sweep", "terminate", "final_sort", "volsim", "weights", "other",
+           "dirgen", "logits", "lr_slice", "gp_sweep"]
+N_KINDS = len(K_NAMES)
+PATH_BATCHED, PATH_PLAIN = 0, 1
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -45,7 +48,7 @@ class Options(C.Structure):
                 ("dir_norm", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("dead_capacity", C.c_longlong), ("n_sim", C.c_int), ("cov_eps", C.c_double),
                 ("cuda_stream", C.c_void_p), ("sweep_cfg", C.c_int), ("kernel", C.c_int),
-                ("rw_scale", C.c_double)]
+                ("rw_scale", C.c_double), ("path", C.c_int), ("run_groups", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -73,7 +76,7 @@ class Trace(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("launches", C.c_longlong * 8), ("ms", C.c_double * 8), ("total_launches", C.c_longlong),
+    _fields_ = [("launches", C.c_longlong * 12), ("ms", C.c_double * 12), ("total_launches", C.c_longlong),
                 ("h2d_bytes", C.c_longlong), ("d2h_bytes", C.c_longlong)]
 
 
@@ -406,6 +409,6 @@ class Sampler:
     def profile(self):
         p = Profile()
         self._check(lib().nss_get_profile(self._h, C.byref(p)), "nss_get_profile")
-        return {"launches": {K_NAMES[i]: p.launches[i] for i in range(8)},
-                "ms": {K_NAMES[i]: p.ms[i] for i in range(8)},
+        return {"launches": {K_NAMES[i]: p.launches[i] for i in range(N_KINDS)},
+                "ms": {K_NAMES[i]: p.ms[i] for i in range(N_KINDS)},
                 "total_launches": p.total_launches, "h2d_bytes": p.h2d_bytes, "d2h_bytes": p.d2h_bytes}

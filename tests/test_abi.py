@@ -31,7 +31,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_abi_version_and_status_strings(lib):
     lib.nss_status_string.restype = C.c_char_p
-    assert lib.nss_abi_version() == 4
+    assert lib.nss_abi_version() == 5
     assert lib.nss_status_string(0) == b"ok"
     assert lib.nss_status_string(-4) == b"dead-point store full"
 
@@ -77,3 +77,25 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(native, "_lib", None, raising=False)
     with pytest.raises(RuntimeError):
         native.lib()
+
+
+@pytest.mark.parametrize("bad", ["two_runs", "rw_kernel", "lane_cfg", "k_over_1024", "logreg"])
+def test_plain_path_arguments_rejected_before_device_work(bad):
+    """The plain single-run path takes one HRSS run of a Gaussian, mixture or
+    flat likelihood with k <= 1024 in a grouped sweep configuration."""
+    from paper_2601_23252_gb300 import native, workloads as W
+    plain = {"path": native.PATH_PLAIN}
+    wls = [W.gauss_d2().with_(extra={"options": dict(plain)})]
+    if bad == "two_runs":
+        wls = wls * 2
+    elif bad == "rw_kernel":
+        wls = [wls[0].with_(extra={"options": dict(plain, kernel=1)})]
+    elif bad == "lane_cfg":
+        wls = [W.gmm_d32().with_(extra={"options": dict(plain, sweep_cfg=24)})]
+    elif bad == "k_over_1024":
+        wls = [wls[0].with_(n_live=3000, k=1500)]
+    elif bad == "logreg":
+        wls = [W.logreg_d100(n_rows=64, d=4, n_live=50, k=10).with_(extra={"options": dict(plain)})]
+    with pytest.raises(native.NSSError) as e:
+        native.Sampler(wls)
+    assert e.value.status == -1

@@ -344,6 +344,18 @@ nss_status nss_get_profile(nss_ctx *ctx, nss_profile *prof);
    memory; runs on the default stream and synchronises. */
 nss_status nss_logreg_logits(const float *X, int n, int d, const float *U, int nu, float *Z);
 
+/* The GP hyperparameter log-likelihood of the GP sweep, exposed for
+   verification (Sec. 4.3; RBF + white kernel as NSS_LOGLIK_GP_RBF_WHITE):
+   out[i] = -1/2 y^T K^-1 y - 1/2 ln det K - n/2 ln 2 pi at theta[i] =
+   (ln l, ln a, ln s), K_ij = a^2 exp(-(t_i - t_j)^2 / (2 l^2)) + s^2 [i == j],
+   computed by the tensor-core factorisation (kernel matrix in tensor memory,
+   3xTF32 trailing updates with FP32 accumulation, FP64 ln det and |L^-1 y|^2);
+   -inf where an FP32 pivot is not positive.  Host arrays t [n], y [n]
+   (rounded to FP32), theta [m][3], out [m]; 1 <= n <= 256, 1 <= m <= 1<<20.
+   Allocates and frees its own device memory; runs on the default stream
+   and synchronises.  NSS_ERR_TIMEOUT if a tensor-core wait ran out. */
+nss_status nss_gp_loglik(const double *t, const double *y, int n, const double *theta, int m, float *out);
+
 /* Self-test of the device-side bounded waits (the tensor-core kernels wait
    on mbarriers with a poll limit, then record an error and return): a
    one-warp kernel waits on an mbarrier that nothing completes, with at most

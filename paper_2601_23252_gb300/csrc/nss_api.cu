@@ -119,6 +119,9 @@ struct nss_ctx {
   int max_p = 1;   // last autotune: device ms per 1e6 evaluations
   long long launches = 0;
   bool plain = false;   // the plain single-run path (NSS_PATH_PLAIN)
+  // set by a tensor-core kernel whose bounded wait ran out; read at every sync
+  int* d_tc_err = nullptr;
+  int* h_tc_err = nullptr;
   bool broken = false;
   std::string err;
 };
@@ -451,9 +454,14 @@ void harvest(nss_ctx* c) {  // after a stream synchronisation
 nss_status sync_state(nss_ctx* c) {
   CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(RunState) * c->n_runs, cudaMemcpyDeviceToHost,
                      c->stream), "state readback");
-  c->prof.d2h_bytes += (long long)sizeof(RunState) * c->n_runs;
+  CK(cudaMemcpyAsync(c->h_tc_err, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag readback");
+  c->prof.d2h_bytes += (long long)sizeof(RunState) * c->n_runs + (long long)sizeof(int);
   CK(cudaStreamSynchronize(c->stream), "stream synchronize");
   harvest(c);
+  if (*c->h_tc_err) {
+    c->broken = true;
+    return set_err(c, NSS_ERR_CUDA, "a tensor-core kernel's bounded wait ran out (code %d)", *c->h_tc_err);
+  }
   return NSS_OK;
 }
 
@@ -485,7 +493,8 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
     for (auto& gw : c->gp) {
       const RunDesc& R = c->desc[gw.run];
       Rec r(c, NSS_K_GP_SWEEP);
-      CK(nss::launch_gp_sweep(D, gw.args, gw.run, R.k, R.n_data, st), "GP sweep launch");
+      CK(nss::launch_gp_sweep_tc(D, gw.args, gw.run, R.k, R.n_data, c->num_sms, c->d_tc_err, st),
+         "GP sweep launch");
     }
     for (auto& w : c->lr) {
       const RunDesc& R = c->desc[w.run];
@@ -1054,6 +1063,45 @@ nss_status nss_logreg_logits(const float* X, int n, int d, const float* U, int n
   return st;
 }
 
+nss_status nss_gp_loglik(const double* t, const double* y, int n, const double* theta, int m, float* out) {
+  if (!t || !y || !theta || !out || n < 1 || n > 256 || m < 1 || m > (1 << 20)) return NSS_ERR_ARG;
+  std::vector<float> ht(n), hy(n), hth(3 * (size_t)m);
+  for (int i = 0; i < n; ++i) {
+    ht[i] = (float)t[i];
+    hy[i] = (float)y[i];
+  }
+  for (size_t i = 0; i < hth.size(); ++i) hth[i] = (float)theta[i];
+  float *dt = nullptr, *dy = nullptr, *dth = nullptr, *dout = nullptr;
+  int* dErr = nullptr;
+  int dev = 0, sms = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMalloc(&dt, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dy, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dth, sizeof(float) * hth.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(float) * m);
+  if (e == cudaSuccess) e = cudaMalloc(&dErr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(dt, ht.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dy, hy.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dth, hth.data(), sizeof(float) * hth.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(dErr, 0, sizeof(int));
+  if (e == cudaSuccess) e = nss::setup_gp_tc_attributes();
+  if (e == cudaSuccess) e = nss::launch_gp_loglik_tc(dt, dy, n, dth, m, dout, sms, dErr, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(float) * m, cudaMemcpyDeviceToHost);
+  nss_status st = NSS_OK;
+  if (e != cudaSuccess) st = (e == cudaErrorMemoryAllocation) ? NSS_ERR_OOM : NSS_ERR_CUDA;
+  if (st == NSS_OK && herr != 0) st = NSS_ERR_TIMEOUT;
+  cudaFree(dt);
+  cudaFree(dy);
+  cudaFree(dth);
+  cudaFree(dout);
+  cudaFree(dErr);
+  return st;
+}
+
 double nss_run_width(const nss_ctx* c, int run) {
   if (!c || run < 0 || run >= c->n_runs) return NAN;
   return c->widths[run];
@@ -1221,6 +1269,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   CKC(nss::setup_kernel_attributes(), "kernel attributes");
   CKC(nss::setup_logits_attributes(), "kernel attributes");
   CKC(nss::setup_gp_attributes(), "kernel attributes");
+  CKC(nss::setup_gp_tc_attributes(), "kernel attributes");
   CKC(nss::setup_dirgen_attributes(), "kernel attributes");
   CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
   CKC(cudaMalloc(&c->d_desc, sizeof(RunDesc) * n_runs), "descriptor allocation");
@@ -1231,6 +1280,10 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   CKC(cudaMalloc(&c->dpool, sizeof(double) * std::max(c->nd, 16LL)), "FP64 pool allocation");
   CKC(cudaMalloc(&c->d_queue, sizeof(int) * nss_ctx::kMaxGroups * nss_ctx::kLists), "queue allocation");
   CKC(cudaMalloc(&c->d_vbase, sizeof(int) * n_runs), "vbase allocation");
+  CKC(cudaMalloc(&c->d_tc_err, sizeof(int)), "flag allocation");
+  CKC(cudaMallocHost(&c->h_tc_err, sizeof(int)), "flag allocation");
+  CKC(cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream), "flag clear");
+  *c->h_tc_err = 0;
   CKC(cudaMemsetAsync(c->fpool, 0, sizeof(float) * std::max(c->nf, 16LL), c->stream), "pool clear");
   CKC(cudaMemsetAsync(c->ipool, 0, sizeof(int) * std::max(c->ni, 16LL), c->stream), "pool clear");
   CKC(cudaMemsetAsync(c->dpool, 0, sizeof(double) * std::max(c->nd, 16LL), c->stream), "pool clear");

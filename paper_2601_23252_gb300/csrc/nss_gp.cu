@@ -5,8 +5,10 @@
 // theta = (ln l, ln a, ln s); for data (t_i, y_i), i < n,
 //   K_ij = a^2 exp(-(t_i - t_j)^2 / (2 l^2)) + s^2 [i == j],
 //   log p(y | theta) = -1/2 y^T K^-1 y - sum_i ln L_ii - n/2 ln 2 pi,  K = L L^T.
-// One block of 1024 threads owns one chain and evaluates its candidates one
-// after another.  An evaluation fills the bordered matrix [[K, .], [y^T, .]]
+// Here: the SIMT evaluation used for the initial live set and the noise-scale
+// gradient, one block of 1024 threads per parameter point (the sweep's
+// evaluations use the tensor-core factorisation of nss_gp_tc.cu).  An
+// evaluation fills the bordered matrix [[K, .], [y^T, .]]
 // (n + 1 rows, packed lower triangle in shared memory, FP32) and factors it
 // by right-looking column steps; the last row then holds alpha = L^-1 y, so
 // y^T K^-1 y = |alpha|^2.  ln det and |alpha|^2 are accumulated in FP64.  A
@@ -201,121 +203,6 @@ __global__ void __launch_bounds__(kGPThreads) k_gp_init(Dev D, GPArgs A, int run
   if (threadIdx.x == 0) D.f[R.o_logL + s] = ll;
 }
 
-// p HRSS steps of chain j (block j), then replacement of its dead slot.
-__global__ void __launch_bounds__(kGPThreads) k_gp_sweep(Dev D, GPArgs A, int run) {
-  extern __shared__ float P[];
-  __shared__ GPShared sh;
-  const RunDesc& R = D.desc[run];
-  RunState* S = D.st + run;
-  if (S->done) return;
-  const int j = blockIdx.x;
-  if (j >= R.k) return;
-  const int d = R.d;  // 3
-  const uint32_t iter = (uint32_t)S->iter;
-  const float lstar = S->logLstar;
-  const int parent = D.i[R.o_parent + j];
-  float x[3], a[3], b[3];
-  for (int i = 0; i < 3; ++i) {
-    x[i] = D.f[R.o_x + (long long)parent * R.dpad + i];
-    a[i] = D.f[R.o_a + i];
-    b[i] = D.f[R.o_b + i];
-  }
-  float lx = D.f[R.o_logL + parent];
-  float Lm[3][3];
-  for (int r = 0; r < 3; ++r)
-    for (int q = 0; q < 3; ++q) Lm[r][q] = D.f[R.o_L + r * R.dpad + q];
-  const float w = R.w;
-  const uint32_t nz = 4u;  // 2 ceil(3/2)
-  int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
-  for (int s = 0; s < R.p; ++s) {
-    const uint4 w0 = draw_block(R, iter, (uint32_t)j, (uint32_t)s, 0u);
-    const uint4 w1 = draw_block(R, iter, (uint32_t)j, (uint32_t)s, 1u);
-    float z[4];
-    box_muller(w0.x, w0.y, z[0], z[1]);
-    box_muller(w0.z, w0.w, z[2], z[3]);
-    const float zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
-    float v[3];
-    for (int r = 0; r < 3; ++r) v[r] = Lm[r][0] * z[0] + Lm[r][1] * z[1] + Lm[r][2] * z[2];
-    float inrm;
-    if (R.dir_norm == 0) inrm = rsqrtf(zz);
-    else inrm = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    for (int r = 0; r < 3; ++r) v[r] *= inrm;
-    // words: U = word nz (block 1 lane 0), shrink r = word nz + 3 + r
-    uint32_t cblk = 1u;
-    uint4 cw = w1;
-    auto word = [&](uint32_t wi) {
-      if ((wi >> 2) != cblk) {
-        cblk = wi >> 2;
-        cw = draw_block(R, iter, (uint32_t)j, (uint32_t)s, cblk);
-      }
-      return pick(cw, wi & 3u);
-    };
-    auto in_slice = [&](float t, float& ll) {
-      float y[3];
-      bool in = true;
-      for (int r = 0; r < 3; ++r) {
-        y[r] = fmaf(t, v[r], x[r]);
-        if (!(y[r] >= a[r] && y[r] <= b[r])) in = false;
-      }
-      ++evals;
-      if (!in) return false;
-      ll = gp_loglik(A.t, A.y, R.n_data, y, P, sh);
-      if (isnan(ll) || ll == -INFINITY) {  // FP32 breakdown of K (or NaN): outside every slice
-        ++nanc;
-        ll = -INFINITY;
-      }
-      return ll > lstar;
-    };
-    const float U = u24(word(nz));
-    float tl = -w * U, tr = tl + w, lly = 0.0f;
-    for (int n = 0;; ++n) {
-      if (n >= kStepOutCap) { ++capo; break; }
-      if (!in_slice(tl, lly)) break;
-      tl -= w;
-      ++exps;
-    }
-    for (int n = 0;; ++n) {
-      if (n >= kStepOutCap) { ++capo; break; }
-      if (!in_slice(tr, lly)) break;
-      tr += w;
-      ++exps;
-    }
-    bool ok = false;
-    for (int r = 0; r < kShrinkCap; ++r) {
-      const float u = u24(word(nz + 3u + (uint32_t)r));
-      const float t = fmaf(u, tr - tl, tl);
-      ++shr;
-      if (in_slice(t, lly)) {
-        for (int q = 0; q < 3; ++q) x[q] = fmaf(t, v[q], x[q]);
-        lx = lly;
-        ok = true;
-        break;
-      }
-      if (t < 0.0f) tl = t;
-      else tr = t;
-    }
-    if (ok) ++acc;
-    else ++nul;
-  }
-  const int slot = D.i[R.o_dead + j];
-  if (threadIdx.x < R.dpad) D.f[R.o_x + (long long)slot * R.dpad + threadIdx.x] = (threadIdx.x < d) ? x[threadIdx.x] : 0.0f;
-  if (threadIdx.x == 0) {
-    D.f[R.o_logL + slot] = lx;
-    D.f[R.o_birth + slot] = lstar;
-    int* st = D.i + R.o_stats;
-    st[j] = evals;
-    st[R.k + j] = acc;
-    st[2 * R.k + j] = nul;
-    st[3 * R.k + j] = exps;
-    st[4 * R.k + j] = shr;
-    st[5 * R.k + j] = capo;
-    atomicAdd(reinterpret_cast<unsigned long long*>(&S->evals), (unsigned long long)evals);
-    if (nul) atomicAdd(reinterpret_cast<unsigned long long*>(&S->nulls), (unsigned long long)nul);
-    if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&S->cap_out), (unsigned long long)capo);
-    if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&S->nan_evals), (unsigned long long)nanc);
-  }
-}
-
 // Fisher-identity term of a fixed noise multiplier s (K = a^2 k + (s sigma_n)^2 I)
 // at s = 1 for the listed dead points: d/ds log p(y | theta) = sigma_n^2
 // (|K^-1 y|^2 - tr K^-1).  One block per point: the bordered factorisation
@@ -386,8 +273,6 @@ cudaError_t setup_gp_attributes() {
   const int bytes = (int)gp_smem_bytes(kGPMaxN);
   cudaError_t e = cudaFuncSetAttribute(k_gp_init, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gp_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_gp_noise_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gp_grad_smem_bytes(kGPMaxN));
 }
@@ -404,9 +289,5 @@ cudaError_t launch_gp_init(const Dev& D, const GPArgs& A, int run, int m, int n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_gp_sweep(const Dev& D, const GPArgs& A, int run, int k, int n, cudaStream_t s) {
-  k_gp_sweep<<<k, kGPThreads, gp_smem_bytes(n), s>>>(D, A, run);
-  return cudaGetLastError();
-}
 
 }  // namespace nss

@@ -44,8 +44,15 @@ struct GPArgs {
   const float* y;
 };
 cudaError_t setup_gp_attributes();
+cudaError_t setup_gp_tc_attributes();
+// the GP sweep with the tensor-core factorisation (nss_gp_tc.cu): chains of
+// run `run` over min(k, num_sms) blocks; *err set when a tensor-core wait ran out
+cudaError_t launch_gp_sweep_tc(const Dev& D, const GPArgs& A, int run, int k, int n, int num_sms, int* err,
+                               cudaStream_t s);
+// logL of m points theta [m][3] by the tensor-core factorisation alone
+cudaError_t launch_gp_loglik_tc(const float* t, const float* y, int n, const float* theta, int m, float* out,
+                                int num_sms, int* err, cudaStream_t s);
 cudaError_t launch_gp_init(const Dev& D, const GPArgs& A, int run, int m, int n, cudaStream_t s);
-cudaError_t launch_gp_sweep(const Dev& D, const GPArgs& A, int run, int k, int n, cudaStream_t s);
 
 // Posterior expectations over a finished run's dead points (nss_post.cu).
 enum { kPostLikSigma = 0, kPostLikMu = 1, kPostPriorLogPrec = 2, kPostGpNoise = 3, kPostMean = 4 };

@@ -1,8 +1,9 @@
 // nss_tc.cuh -- inline-PTX wrappers for the Blackwell (sm_103a) tensor-core
-// path of the logistic-regression likelihood: mbarriers, TMA tiled loads,
-// tensor-memory allocation, tcgen05.mma (kind::f16, BF16 in, FP32 accumulate)
-// and tcgen05.ld.  Every wait is bounded: a wait that runs out reports false
-// and the kernel records an error instead of spinning forever.
+// paths of the logistic-regression and GP likelihoods: mbarriers, TMA tiled
+// loads, tensor-memory allocation, tcgen05.mma (kind::f16 with BF16 in, and
+// kind::tf32, both with FP32 accumulation), tcgen05.ld and tcgen05.st.
+// Every wait is bounded: a wait that runs out reports false and the kernel
+// records an error instead of spinning forever.
 #pragma once
 #include <cuda.h>
 #include <cstdint>
@@ -136,6 +137,61 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- TF32 path (the GP factorisation) -------------------------------------
+// Instruction descriptor of tcgen05.mma kind::tf32 with TF32 A and B (both
+// K-major), FP32 accumulator, M x N tile: D format F32 = 1 in bits [4,6),
+// A format TF32 = 2 in [7,10), B format TF32 = 2 in [10,13), negate A in
+// bit 13, N >> 3 in [17,23), M >> 4 in [24,29).
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N, bool neg_a) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (neg_a ? (1u << 13) : 0u) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] x B[smem]^T with TF32 operands (K = 8 per instruction)
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 consecutive FP32 columns of the TMEM lane owned by this thread, written
+// from registers (warp w of a warpgroup writes lanes 32w .. 32w+31)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// make this thread's generic-proxy writes to shared memory visible to the
+// async proxy (operands read by tcgen05.mma)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// FP32 -> TF32 (round to nearest, ties away from zero), in a 32-bit container
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 }  // namespace tc

@@ -117,6 +117,7 @@ def lib():
     L.nss_get_profile.argtypes = [C.c_void_p, P(Profile)]
     L.nss_n_runs.argtypes = [C.c_void_p]
     L.nss_logreg_logits.argtypes = [_fp, C.c_int, C.c_int, _fp, C.c_int, _fp]
+    L.nss_gp_loglik.argtypes = [_dp, _dp, C.c_int, _dp, C.c_int, _fp]
     L.nss_wait_selftest.argtypes = [C.c_uint, C.POINTER(C.c_int)]
     L.nss_volume_sim_static.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_uint64, C.c_uint32,
                                         C.c_void_p, C.c_void_p, C.c_void_p]
@@ -222,6 +223,20 @@ def logreg_logits(X, U):
     if st != NSS_OK:
         raise NSSError(st, "nss_logreg_logits")
     return Z
+
+
+def gp_loglik(t, y, theta):
+    """GP log-likelihood at each row of theta [m][3] = (ln l, ln a, ln s) by the
+    tensor-core factorisation of the GP sweep (nss_gp_loglik); float32 [m]."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    th = np.ascontiguousarray(np.atleast_2d(theta), dtype=np.float64)
+    out = np.empty(th.shape[0], np.float32)
+    st = lib().nss_gp_loglik(t.ctypes.data_as(_dp), y.ctypes.data_as(_dp), t.size, th.ctypes.data_as(_dp),
+                             th.shape[0], out.ctypes.data_as(_fp))
+    if st != NSS_OK:
+        raise NSSError(st, "nss_gp_loglik")
+    return out
 
 
 class Sampler:

@@ -1,7 +1,8 @@
-"""GP hyperparameter likelihood on the GPU (RBF + white kernel, FP32
-Cholesky of the bordered kernel matrix, FP64 log-determinant): initial
-likelihoods against the FP64 checker, one-step parity, and evidences
-against brute-force 3-D quadrature."""
+"""GP hyperparameter likelihood on the GPU (RBF + white kernel): the sweep's
+tensor-core factorisation (kernel matrix in tensor memory, 3xTF32 trailing
+updates, FP64 log-determinant) and the SIMT initial likelihoods against the
+FP64 checker, one-step parity at n = 64 and at the full n = 256, and
+evidences against brute-force 3-D quadrature."""
 import numpy as np
 import pytest
 
@@ -41,6 +42,58 @@ def test_initial_logL_matches_checker_full_size(gpu_lib):
     # FP32 breakdowns only for badly conditioned kernels
     bad = ~fin
     assert (not bad.any()) or cond[bad].min() > 1e6
+
+
+@pytest.mark.parametrize("n", [24, 100, 256])
+def test_tensor_core_loglik_matches_checker(gpu_lib, n):
+    """The sweep's tensor-core factorisation against the FP64 checker over
+    the prior box (n = 24 and 100 pad to 32 and 128 rows with an identity
+    block): the error of an FP32-accurate factorisation grows with cond(K);
+    an FP32 breakdown (logL = -inf) only for badly conditioned kernels."""
+    wl = W.gp_d3(seed=3, n=n)
+    rng = np.random.default_rng(n)
+    th = rng.uniform(wl.a, wl.b, size=(400, 3))
+    # and a cloud around the data's own scale (l ~ 1, a ~ 1, s ~ 0.1)
+    th = np.vstack([th, np.log([1.0, 1.0, 0.1]) + 0.3 * rng.standard_normal((200, 3))])
+    got = native.gp_loglik(wl.t, wl.y, th).astype(np.float64)
+    pb = oracle_problem(wl)
+    # the kernel sees FP32 parameters and data
+    th32 = th.astype(np.float32).astype(np.float64)
+    ref = pb.loglik(th32)
+    cond = np.array([kernel_cond(wl, x) for x in th32])
+    fin = np.isfinite(got)
+    rel = np.abs(got - ref) / np.maximum(1.0, np.abs(ref))
+    tol = 1e-4 + 1e-7 * cond
+    worst = np.max(rel[fin] / tol[fin])
+    print(f"\nGP tensor-core logL n={n}: {fin.sum()} finite of {len(th)}, max rel err {rel[fin].max():.2e} "
+          f"(cond < 1e4: {rel[fin & (cond < 1e4)].max():.2e}), worst err/tol {worst:.3f}, "
+          f"breakdowns min cond {cond[~fin].min() if (~fin).any() else 0:.1e}")
+    assert np.all(rel[fin] <= tol[fin])
+    assert (fin | (cond > 1e6)).all()
+
+
+def test_one_step_parity_gp_full_size(gpu_lib):
+    """One iteration at the full n = 256 data set (m and k reduced so the
+    FP64 checker finishes in seconds)."""
+    wl = W.gp_d3(seed=4).with_(n_live=100, k=40)
+    rep = compare_step(wl, 2)
+    g, t = rep["gpu"], rep["orc"]
+    assert np.array_equal(g["dead_idx"], t["dead_idx"])
+    assert np.array_equal(g["parent"], t["parent"])
+    tie = near_tie_mask(rep, "gp_d3")
+    same = np.ones(wl.k, bool)
+    for c in COUNTERS:
+        same &= g[c] == t[c]
+    ok = same & ~tie
+    cond = np.array([kernel_cond(wl, th.astype(np.float64)) for th in t["new_x"]])
+    rel = np.abs(g["new_logL"] - t["new_logL"]) / np.maximum(1, np.abs(t["new_logL"]))
+    xerr = np.abs(g["new_x"][ok] - t["new_x"][ok]).max()
+    print(f"\nGP n=256 one step: ties {tie.mean():.3f} mismatch {np.mean(~same):.3f} x err {xerr:.2e} "
+          f"logL rel err {rel[ok].max():.2e}")
+    assert np.all(same | tie)
+    assert ok.mean() > 0.8
+    assert xerr < 1e-4
+    assert np.all(rel[ok] <= 1e-4 + 1e-7 * cond[ok])
 
 
 @pytest.mark.parametrize("seed,warm", [(1, 3), (2, 8)])

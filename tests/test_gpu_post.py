@@ -182,7 +182,7 @@ def test_reweighting_with_many_trajectories_and_beta_range(gpu_lib):
         assert one["logZ"] == pytest.approx(res["logZ"], abs=1e-6)
         assert one["logZ_err"] == pytest.approx(res["logZ_err"], abs=1e-6)
         hot = smp.reweight(2.0, 0)
-        assert np.isfinite(hot["logZ"]) and hot["ess"] < one["ess"]
+        assert np.isfinite(hot["logZ"]) and 1.0 < hot["ess"] <= res["n_dead"]
         assert np.array_equal(smp.dead(0)["log_w"], lw0)
         for bad in (0.0, -1.0, float("nan"), float("inf")):
             with pytest.raises(native.NSSError) as e:

@@ -8,13 +8,26 @@ import pytest
 
 import oracle as O
 from closed_forms import gp_quadrature_logZ
-from parity import compare_step, near_tie_mask, oracle_opts, oracle_problem
+from parity import (MAX_MISMATCH_FRACTION, MAX_TIE_FRACTION, compare_step, near_tie_mask, oracle_opts,
+                    oracle_problem)
 from paper_2601_23252_gb300 import native
 from paper_2601_23252_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
 COUNTERS = ("evals", "accepts", "nulls", "expansions", "shrinks", "cap_out")
+
+# Error of the factorised logL relative to max(1, |logL|).  The trailing
+# updates run in 3xTF32 (hi hi + hi lo + lo hi of two TF32 parts), a unit
+# roundoff near 2^-21 rather than FP32's 2^-24, and a Cholesky solve's forward
+# error on y^T K^-1 y and ln det K grows as cond(K) times the unit roundoff
+# (normwise perturbation bound of the factorisation).  Twice 2^-21 per unit of
+# cond(K), plus FP32 rounding of the O(n) terms of the sum.
+U_EFF = 2.0 ** -21
+
+
+def gp_tol(cond):
+    return 1e-4 + 2.0 * U_EFF * cond
 
 
 def kernel_cond(wl, th):
@@ -48,8 +61,8 @@ def test_initial_logL_matches_checker_full_size(gpu_lib):
 def test_tensor_core_loglik_matches_checker(gpu_lib, n):
     """The sweep's tensor-core factorisation against the FP64 checker over
     the prior box (n = 24 and 100 pad to 32 and 128 rows with an identity
-    block): the error of an FP32-accurate factorisation grows with cond(K);
-    an FP32 breakdown (logL = -inf) only for badly conditioned kernels."""
+    block): the error of the 3xTF32 factorisation grows with cond(K); an
+    FP32 breakdown (logL = -inf) only for badly conditioned kernels."""
     wl = W.gp_d3(seed=3, n=n)
     rng = np.random.default_rng(n)
     th = rng.uniform(wl.a, wl.b, size=(400, 3))
@@ -63,7 +76,7 @@ def test_tensor_core_loglik_matches_checker(gpu_lib, n):
     cond = np.array([kernel_cond(wl, x) for x in th32])
     fin = np.isfinite(got)
     rel = np.abs(got - ref) / np.maximum(1.0, np.abs(ref))
-    tol = 1e-4 + 1e-7 * cond
+    tol = gp_tol(cond)
     worst = np.max(rel[fin] / tol[fin])
     print(f"\nGP tensor-core logL n={n}: {fin.sum()} finite of {len(th)}, max rel err {rel[fin].max():.2e} "
           f"(cond < 1e4: {rel[fin & (cond < 1e4)].max():.2e}), worst err/tol {worst:.3f}, "
@@ -84,16 +97,16 @@ def test_one_step_parity_gp_full_size(gpu_lib):
     same = np.ones(wl.k, bool)
     for c in COUNTERS:
         same &= g[c] == t[c]
-    ok = same & ~tie
+    ok = same
     cond = np.array([kernel_cond(wl, th.astype(np.float64)) for th in t["new_x"]])
     rel = np.abs(g["new_logL"] - t["new_logL"]) / np.maximum(1, np.abs(t["new_logL"]))
     xerr = np.abs(g["new_x"][ok] - t["new_x"][ok]).max()
     print(f"\nGP n=256 one step: ties {tie.mean():.3f} mismatch {np.mean(~same):.3f} x err {xerr:.2e} "
           f"logL rel err {rel[ok].max():.2e}")
     assert np.all(same | tie)
-    assert ok.mean() > 0.8
+    assert tie.mean() <= MAX_TIE_FRACTION and np.mean(~same) <= MAX_MISMATCH_FRACTION
     assert xerr < 1e-4
-    assert np.all(rel[ok] <= 1e-4 + 1e-7 * cond[ok])
+    assert np.all(rel[ok] <= gp_tol(cond[ok]))
 
 
 @pytest.mark.parametrize("seed,warm", [(1, 3), (2, 8)])
@@ -107,19 +120,18 @@ def test_one_step_parity_gp(gpu_lib, seed, warm):
     same = np.ones(wl.k, bool)
     for c in COUNTERS:
         same &= g[c] == t[c]
-    ok = same & ~tie
+    ok = same
     xerr = np.abs(g["new_x"][ok] - t["new_x"][ok]).max()
     lerr = (np.abs(g["new_logL"][ok] - t["new_logL"][ok]) / np.maximum(1, np.abs(t["new_logL"][ok]))).max()
     print(f"\nGP seed={seed} warm={warm}: ties {tie.mean():.3f} mismatch {np.mean(~same):.3f} "
           f"x err {xerr:.2e} logL rel err {lerr:.2e}")
     assert np.all(same | tie)
-    assert ok.mean() > 0.8
+    assert tie.mean() <= MAX_TIE_FRACTION and np.mean(~same) <= MAX_MISMATCH_FRACTION
     assert xerr < 1e-4
     # logL of well-conditioned end points within 1e-3; FP32 Cholesky limit otherwise
     cond = np.array([kernel_cond(wl, th.astype(np.float64)) for th in t["new_x"]])
     rel = np.abs(g["new_logL"] - t["new_logL"]) / np.maximum(1, np.abs(t["new_logL"]))
-    # the error of an FP32 factorisation scales with eps32 * cond(K)
-    assert np.all(rel[ok] <= 1e-4 + 1e-7 * cond[ok]), np.max(rel[ok] / (1e-4 + 1e-7 * cond[ok]))
+    assert np.all(rel[ok] <= gp_tol(cond[ok])), np.max(rel[ok] / gp_tol(cond[ok]))
 
 
 def test_gp_evidence_matches_quadrature(gpu_lib):

@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 from conftest import golden_path
-from parity import compare_step, near_tie_mask, oracle_opts, oracle_problem
+from parity import MAX_MISMATCH_FRACTION, MAX_TIE_FRACTION, TIES, compare_step, near_tie_mask, oracle_opts, oracle_problem
 from paper_2601_23252_gb300 import native
 from paper_2601_23252_gb300 import workloads as W
 
@@ -61,13 +61,13 @@ def test_one_step_parity_logistic(gpu_lib, seed, warm):
     same = np.ones(wl.k, bool)
     for c in COUNTERS:
         same &= g[c] == t[c]
-    ok = same & ~tie
+    ok = same
     xerr = np.abs(g["new_x"][ok] - t["new_x"][ok]).max()
     lerr = np.abs(g["new_logL"][ok] - t["new_logL"][ok]).max()
     print(f"\nlogreg seed={seed} warm={warm}: ties {tie.mean():.3f} mismatch {np.mean(~same):.3f} "
           f"x err {xerr:.2e} logL err {lerr:.2e}")
     assert np.all(same | tie)
-    assert ok.mean() > 0.8
+    assert tie.mean() <= MAX_TIE_FRACTION and np.mean(~same) <= MAX_MISMATCH_FRACTION
     scale = np.abs(t["new_x"][ok]).max()
     assert xerr <= 1e-5 * max(1.0, scale)
     assert lerr <= 1e-5 * np.abs(t["new_logL"][ok]).max() + 2e-3
@@ -75,8 +75,11 @@ def test_one_step_parity_logistic(gpu_lib, seed, warm):
 
 
 def test_full_size_step_sampled_chains(gpu_lib):
-    """One step at the full logistic size from the prior draw; a sample of
-    chains recomputed by the checker one HRSS step at a time."""
+    """One step at the full logistic size (N = 10000, d = 100, k = 1000,
+    p = 200) from the prior draw; 64 chains spread over the batch recomputed
+    by the checker one HRSS step at a time (FP64 logits of the same BF16-exact
+    rows).  At least 90% of them reproduce the GPU's counters exactly; any
+    other had a comparison within the FP32 error budget of its threshold."""
     wl = W.logreg_d100(seed=0)
     with native.Sampler(wl) as s:
         st0 = s.export_state()
@@ -91,24 +94,31 @@ def test_full_size_step_sampled_chains(gpu_lib):
     assert np.array_equal(g["parent"], par)
     L, _ = O.metric(x32)
     assert np.abs(g["L"] - L).max() / np.abs(L).max() < 1e-4
-    checked = 0
-    for j in (0, 17, 333, 999):
+    chains = np.unique(np.linspace(0, wl.k - 1, 64).round().astype(int))
+    exact, tied, worst_x, worst_l = 0, 0, 0.0, 0.0
+    for j in chains:
         x, lx = x32[par[j]].copy(), l32[par[j]]
-        tot = {c: 0 for c in ("evals", "accepts", "nulls")}
+        tot = {c: 0 for c in COUNTERS}
         tie = False
         for s_ in range(wl.p):
             x, lx, c = O.hrss_step(pb, L, wl.w, 0, ls, wl.seed, wl.run_id, 0, j, s_, x, lx)
             for key in tot:
                 tot[key] += c[key]
-            tie |= c["margin"] < 1e-2 or c["pmargin"] < 1e-4
-        if tie:
-            continue
-        checked += 1
-        assert g["evals"][j] == tot["evals"] and g["accepts"][j] == tot["accepts"]
-        assert np.abs(g["new_x"][j] - x).max() < 1e-4
-        assert abs(g["new_logL"][j] - lx) < 1e-5 * abs(lx) + 1e-2
-    print(f"\nfull-size logistic step: {checked} of 4 sampled chains compared exactly")
-    assert checked >= 2
+            tie |= c["margin"] < TIES["logreg_d100"][0] or c["pmargin"] < TIES["logreg_d100"][1]
+        same = all(int(g[key][j]) == tot[key] for key in COUNTERS)
+        tied += tie
+        if same:
+            exact += 1
+            worst_x = max(worst_x, float(np.abs(g["new_x"][j] - x).max()))
+            worst_l = max(worst_l, abs(float(g["new_logL"][j]) - lx) / abs(lx))
+        else:
+            assert tie, f"chain {j} differs from the checker without a near-tie"
+    n = len(chains)
+    print(f"\nfull-size logistic step: {exact} of {n} sampled chains exact, {tied} with a near-tie; "
+          f"x err {worst_x:.2e}, logL rel err {worst_l:.2e}")
+    assert exact >= 0.9 * n
+    assert worst_x < 1e-4
+    assert worst_l < 1e-5
 
 
 def test_logistic_evidence_against_checker(gpu_lib):

@@ -73,49 +73,70 @@ def test_gmm_d32_twenty_seeds_against_checker(gpu_lib):
     print(f"evals per HRSS step {np.mean(ev / steps):.2f}, iterations {np.mean([r['iters'] for r in res]):.1f}")
 
 
+def _traj_se(dd, w, gi, n_traj=16):
+    """Dispersion of the Fisher-identity estimate sum_i w_i g_i over simulated
+    volume trajectories (App. D.2: trapezoid dX from the checker's
+    trajectories of the run's own live counts)."""
+    ll = dd["logL"].astype(np.float64)
+    per = []
+    for t in range(n_traj):
+        lx = O.volume_trajectory(dd["nlive"], t, w.seed, w.run_id)
+        X = np.concatenate([[1.0], np.exp(lx), [0.0]])
+        dX = 0.5 * (X[:-2] - X[2:])
+        lw = ll + np.log(np.maximum(dX, 1e-300))
+        wt = np.exp(lw - special.logsumexp(lw))
+        per.append(np.sum(wt * gi))
+    return float(np.std(per, ddof=1))
+
+
 def test_batch64_closed_form(gpu_lib):
-    wls = W.batch64(seed=0)
+    """The 64 runs of the batched workload against their closed-form evidences
+    and closed-form d lnZ/dsigma (Fisher identity on the device).  The
+    gradient's error bar: the volume-trajectory dispersion of each run (App.
+    D.2), scaled by one factor kappa calibrated on independent repeats (the
+    same 64 problems under three more seeds): the trajectories model the
+    volume noise, while successive dead points of a finite HRSS chain stay
+    correlated, so the true run-to-run scatter is somewhat larger."""
+    base = W.batch64(seed=0)
+    reps = [w.with_(seed=100 + q) for q in range(3) for w in base]
+    wls = base + reps
+    nb = len(base)
     with native.Sampler(wls) as s:
         res = s.run()
-        # d lnZ/dsigma per run (Fisher identity, device kernel); its error is
-        # the dispersion of the same estimator over simulated volume
-        # trajectories (App. D.2: trapezoid dX from the checker's trajectories)
-        grads, ses = [], []
-        for r, w in enumerate(wls):
-            g = s.posterior(native.GRAD_LIK_SIGMA, r)[0]
+        grads = np.array([s.posterior(native.GRAD_LIK_SIGMA, r)[0] for r in range(len(wls))])
+        ses = []
+        for r, w in enumerate(base):
             dd = s.dead(r)
-            ll = dd["logL"].astype(np.float64)
             q = np.sum((dd["x"].astype(np.float64) - np.float32(w.mu[0][0])) ** 2, axis=1)
-            gi = q / w.sigma ** 3 - w.d / w.sigma
-            per = []
-            for t in range(16):
-                lx = O.volume_trajectory(dd["nlive"], t, w.seed, w.run_id)
-                X = np.concatenate([[1.0], np.exp(lx), [0.0]])
-                dX = 0.5 * (X[:-2] - X[2:])
-                lw = ll + np.log(np.maximum(dX, 1e-300))
-                wt = np.exp(lw - special.logsumexp(lw))
-                per.append(np.sum(wt * gi))
-            ses.append(np.std(per, ddof=1))
-            grads.append(g)
-    grads, ses = np.array(grads), np.array(ses)
+            ses.append(_traj_se(dd, w, q / w.sigma ** 3 - w.d / w.sigma))
+    ses = np.array(ses)
     # closed form: lnZ(sigma) = sum_i ln[Phi((b - mu)/sigma) - Phi((a - mu)/sigma)]
     h = 1e-6
     tg = np.array([(box_gauss_logZ(w.mu[0], w.sigma + h, w.a, w.b) - box_gauss_logZ(w.mu[0], w.sigma - h, w.a, w.b))
-                   / (2 * h) for w in wls])
-    zg = (grads - tg) / ses
-    print(f"\nbatch64 d lnZ/dsigma: max |dev|/se {np.max(np.abs(zg)):.2f}, mean {np.mean(zg):+.3f}")
-    # the trajectory dispersion (App. D.2) covers the volume noise only, not
-    # the scatter of the dead points themselves: a wider band for single runs
-    assert np.sum(np.abs(zg) > 3.0) <= 4
-    assert np.all(np.abs(zg) < 6.0)
-    assert abs(np.mean(zg)) < 3.0 / np.sqrt(len(wls)) + 0.2
-    truth = [box_gauss_logZ(w.mu[0], w.sigma, w.a, w.b) for w in wls]
-    lz = np.array([r["logZ"] for r in res]); err = np.array([r["logZ_err"] for r in res])
-    dev = lz - np.array(truth)
-    print(f"\nbatch64: max |dev|/err {np.max(np.abs(dev) / err):.2f}, mean dev/err {np.mean(dev / err):+.3f}")
+                   / (2 * h) for w in base])
+    g4 = grads.reshape(4, nb)                      # [seed][problem]
+    s_emp2 = g4.var(axis=0, ddof=1)                # run-to-run scatter, 3 dof per problem
+    kappa = float(np.sqrt(np.mean(s_emp2 / ses ** 2)))
+    zg = (g4[0] - tg) / (kappa * ses)
+    zm = (g4.mean(axis=0) - tg) / (kappa * ses / 2.0)
+    print(f"\nbatch64 d lnZ/dsigma: kappa {kappa:.3f}; seed 0: max |dev|/se {np.max(np.abs(zg)):.2f}, "
+          f"beyond 3 se {int(np.sum(np.abs(zg) > 3))}, mean {np.mean(zg):+.3f}; "
+          f"4-seed means: max |dev|/se {np.max(np.abs(zm)):.2f}, mean {np.mean(zm):+.3f}")
+    # the trajectories carry most of the scatter
+    assert 0.7 < kappa < 2.0
+    assert np.sum(np.abs(zg) > 3.0) <= 3
+    assert np.all(np.abs(zg) < 5.0)
+    assert abs(np.mean(zg)) < 3.0 / np.sqrt(nb) + 0.2
+    assert np.sum(np.abs(zm) > 3.0) <= 3
+    assert np.all(np.abs(zm) < 5.0)
+    truth = np.array([box_gauss_logZ(w.mu[0], w.sigma, w.a, w.b) for w in base])
+    lz = np.array([r["logZ"] for r in res[:nb]]); err = np.array([r["logZ_err"] for r in res[:nb]])
+    dev = lz - truth
+    print(f"batch64: max |dev|/err {np.max(np.abs(dev) / err):.2f}, mean dev/err {np.mean(dev / err):+.3f}, "
+          f"mean dev {dev.mean():+.4f} nat")
     assert np.sum(np.abs(dev) > 3.0 * err) <= 2
     assert np.all(np.abs(dev) < 4.0 * err)
-    assert abs(np.mean(dev / err)) < 3.0 / np.sqrt(len(wls)) + 0.1
+    assert abs(np.mean(dev / err)) < 3.0 / np.sqrt(nb) + 0.1
 
 
 def test_volume_simulation_matches_checker_on_gpu_dead_list(gpu_lib):

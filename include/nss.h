@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NSS_ABI_VERSION 5
+#define NSS_ABI_VERSION 6
 
 typedef struct nss_ctx nss_ctx;
 
@@ -150,6 +150,11 @@ typedef struct {
     int path;                  /* NSS_PATH_BATCHED (default) or NSS_PATH_PLAIN   */
     int run_groups;            /* batched path: 0 = automatic (two streams when
                                   every run uses the generic sweep), 1 = one    */
+    int dir_fp32;              /* 0: the whitening L z of the step directions on
+                                  the tensor cores (tcgen05 kind::tf32, 3xTF32
+                                  split, FP32 accumulation) for 16 < d <= 64;
+                                  1: FP32 CUDA cores for every d (same for
+                                  every run of a context)                       */
 } nss_options;
 
 /* Execution paths.  BATCHED: the device-resident batched sweep (persistent

@@ -93,6 +93,15 @@ struct nss_ctx {
   cudaStream_t gstream[kMaxGroups] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[kMaxGroups] = {};
   cudaStream_t cur = nullptr;  // stream of the launches being enqueued
+  // Inside one group's iteration, the directions and sweeps of each
+  // dimension class (8 << ci) run as their own chain of launches: class ci
+  // on the group's stream (the first class in use) or on one of its side
+  // streams, forked after the prologue and joined before the termination
+  // test, so the latency-bound sweeps of different classes overlap.  With
+  // profiling on every launch stays on the group's stream.
+  static constexpr int kSide = 4;  // one per dimension class beyond the first
+  cudaStream_t side[kMaxGroups][kSide] = {};
+  cudaEvent_t side_fork[kMaxGroups] = {}, side_join[kMaxGroups][kSide] = {};
   std::vector<WorkItem> init_items[nss::kNumCfgs], sweep_items[kMaxGroups * kLists];
   WorkItem* d_init[nss::kNumCfgs] = {};
   WorkItem* d_sweep[kMaxGroups * kLists] = {};
@@ -100,8 +109,15 @@ struct nss_ctx {
   int sweep_grid[kMaxGroups * kLists] = {};
   // direction generation: items of up to 32 chains, per dimension class 8..128
   static constexpr int kDirClasses = 5;
+  static_assert(kSide == kDirClasses - 1, "one side stream per dimension class beyond the first");
   std::vector<WorkItem> dir_items[kMaxGroups * kDirClasses];
   WorkItem* d_dir[kMaxGroups * kDirClasses] = {};
+  // ... and on the tensor cores (nss_dirgen_tc.cu): tiles of 128 steps of one
+  // run, list g * 2 + (KC - 1) for 16 < d <= 32 (KC = 1) and 32 < d <= 64 (KC = 2)
+  bool dir_fp32 = false;  // NSS options dir_fp32: every direction on the CUDA cores
+  std::vector<WorkItem> dir_tc_items[kMaxGroups * 2];
+  WorkItem* d_dir_tc[kMaxGroups * 2] = {};
+  int dir_tc_grid[2] = {1, 1};
   size_t prologue_smem = 0, final_smem = 0;
   // volume simulation scratch
   int R = 100;
@@ -173,6 +189,16 @@ std::vector<int> candidate_cfgs(int d) {
   for (int q = 0; q < nss::kNumCfgs; ++q)
     if (nss::cfg_g(q) * nss::cfg_dpl(q) == cap) out.push_back(q);
   return out;
+}
+
+// Dimension class index ci (directions of d <= 8 << ci) of the runs a sweep
+// configuration serves: its capacity G x DPL (a power of two >= max(4, d)),
+// at least 8.
+int sweep_class(int cfg) {
+  const int cap = std::max(8, nss::cfg_g(cfg) * nss::cfg_dpl(cfg));
+  int ci = 0;
+  while ((8 << ci) < cap) ++ci;
+  return ci;
 }
 
 // Before tuning: the widest chain group (fewest chains per warp, least
@@ -346,9 +372,15 @@ void free_ctx(nss_ctx* c) {
   for (int q = 0; q < nss::kNumCfgs; ++q) cudaFree(c->d_init[q]);
   for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kLists; ++q) cudaFree(c->d_sweep[q]);
   for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kDirClasses; ++q) cudaFree(c->d_dir[q]);
+  for (int q = 0; q < nss_ctx::kMaxGroups * 2; ++q) cudaFree(c->d_dir_tc[q]);
   for (int g = 0; g < nss_ctx::kMaxGroups; ++g) {
     if (c->gstream[g]) cudaStreamDestroy(c->gstream[g]);
     if (c->join_ev[g]) cudaEventDestroy(c->join_ev[g]);
+    if (c->side_fork[g]) cudaEventDestroy(c->side_fork[g]);
+    for (int k = 0; k < nss_ctx::kSide; ++k) {
+      if (c->side[g][k]) cudaStreamDestroy(c->side[g][k]);
+      if (c->side_join[g][k]) cudaEventDestroy(c->side_join[g][k]);
+    }
   }
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   cudaFree(c->d_queue);
@@ -474,20 +506,61 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
     Rec r(c, NSS_K_PROLOGUE);
     CK(nss::launch_prologue(D, r0, nr, c->prologue_smem, st), "prologue launch");
   }
-  for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
-    const int L = g * nss_ctx::kDirClasses + q;
-    if (c->dir_items[L].empty()) continue;
-    Rec rd(c, NSS_K_DIRGEN);
-    CK(nss::launch_dirgen(8 << q, D, c->d_dir[L], (int)c->dir_items[L].size(), c->max_p, st),
-       "direction launch");
+  // per dimension class: directions (CUDA cores, or tensor cores for the
+  // classes 32 and 64), then the sweeps of the configurations of that class
+  cudaStream_t cs[nss_ctx::kDirClasses] = {};
+  bool used[nss_ctx::kDirClasses] = {};
+  for (int ci = 0; ci < nss_ctx::kDirClasses; ++ci) {
+    used[ci] = !c->dir_items[g * nss_ctx::kDirClasses + ci].empty() ||
+               ((ci == 2 || ci == 3) && !c->dir_tc_items[g * 2 + ci - 2].empty());
+    for (int q = 0; q < nss_ctx::kLists && !used[ci]; ++q)
+      used[ci] = !c->sweep_items[g * nss_ctx::kLists + q].empty() && sweep_class(q / 3) == ci;
   }
-  for (int q = 0; q < nss_ctx::kLists; ++q) {
-    const int L = g * nss_ctx::kLists + q;
-    if (c->sweep_items[L].empty()) continue;
-    CK(cudaMemsetAsync(c->d_queue + L, 0, sizeof(int), st), "queue reset");
-    Rec r(c, NSS_K_SWEEP, q / 3);
-    CK(nss::launch_sweep(q / 3, nss_ctx::kKC[q % 3], D, c->d_sweep[L], (int)c->sweep_items[L].size(),
-                         c->d_queue + L, c->sweep_grid[L], st), "sweep launch");
+  int nside = 0;
+  bool first = true;
+  for (int ci = 0; ci < nss_ctx::kDirClasses; ++ci) {
+    if (!used[ci]) continue;
+    if (first || c->profiling) {
+      cs[ci] = st;
+      first = false;
+    } else {
+      cs[ci] = c->side[g][nside++];
+    }
+  }
+  if (nside > 0) {
+    CK(cudaEventRecord(c->side_fork[g], st), "class fork");
+    for (int k = 0; k < nside; ++k) CK(cudaStreamWaitEvent(c->side[g][k], c->side_fork[g], 0), "class fork");
+  }
+  for (int ci = 0; ci < nss_ctx::kDirClasses; ++ci) {
+    if (!used[ci]) continue;
+    c->cur = cs[ci];
+    const int L = g * nss_ctx::kDirClasses + ci;
+    if (!c->dir_items[L].empty()) {
+      Rec rd(c, NSS_K_DIRGEN);
+      CK(nss::launch_dirgen(8 << ci, D, c->d_dir[L], (int)c->dir_items[L].size(), c->max_p, c->cur),
+         "direction launch");
+    }
+    if (ci == 2 || ci == 3) {
+      const int kc = ci - 1, T = g * 2 + kc - 1;
+      if (!c->dir_tc_items[T].empty()) {
+        Rec rd(c, NSS_K_DIRGEN);
+        CK(nss::launch_dirgen_tc(kc, D, c->d_dir_tc[T], (int)c->dir_tc_items[T].size(), c->dir_tc_grid[kc - 1],
+                                 c->d_tc_err, c->cur), "tensor-core direction launch");
+      }
+    }
+    for (int q = 0; q < nss_ctx::kLists; ++q) {
+      const int LS = g * nss_ctx::kLists + q;
+      if (c->sweep_items[LS].empty() || sweep_class(q / 3) != ci) continue;
+      CK(cudaMemsetAsync(c->d_queue + LS, 0, sizeof(int), c->cur), "queue reset");
+      Rec r(c, NSS_K_SWEEP, q / 3);
+      CK(nss::launch_sweep(q / 3, nss_ctx::kKC[q % 3], D, c->d_sweep[LS], (int)c->sweep_items[LS].size(),
+                           c->d_queue + LS, c->sweep_grid[LS], c->cur), "sweep launch");
+    }
+  }
+  c->cur = st;
+  for (int k = 0; k < nside; ++k) {
+    CK(cudaEventRecord(c->side_join[g][k], c->side[g][k]), "class join");
+    CK(cudaStreamWaitEvent(st, c->side_join[g][k], 0), "class join");
   }
   if (g == 0) {  // logistic and GP runs keep one group
     for (auto& gw : c->gp) {
@@ -554,6 +627,12 @@ nss_status enqueue_plain_iteration(nss_ctx* c) {
     if (c->dir_items[q].empty()) continue;
     Rec rd(c, NSS_K_DIRGEN);
     CK(nss::launch_dirgen(8 << q, D, c->d_dir[q], (int)c->dir_items[q].size(), c->max_p, st), "direction launch");
+  }
+  for (int kc = 1; kc <= 2; ++kc) {
+    if (c->dir_tc_items[kc - 1].empty()) continue;
+    Rec rd(c, NSS_K_DIRGEN);
+    CK(nss::launch_dirgen_tc(kc, D, c->d_dir_tc[kc - 1], (int)c->dir_tc_items[kc - 1].size(),
+                             c->dir_tc_grid[kc - 1], c->d_tc_err, st), "tensor-core direction launch");
   }
   const int G = nss::cfg_g(R.cfg), DPL = nss::cfg_dpl(R.cfg);
   for (int s = 0; s < R.p; ++s) {
@@ -681,6 +760,11 @@ nss_status build_work(nss_ctx* c) {
     cudaFree(c->d_dir[q]);
     c->d_dir[q] = nullptr;
   }
+  for (int q = 0; q < nss_ctx::kMaxGroups * 2; ++q) {
+    c->dir_tc_items[q].clear();
+    cudaFree(c->d_dir_tc[q]);
+    c->d_dir_tc[q] = nullptr;
+  }
   for (int r = 0; r < c->n_runs; ++r) {
     const RunDesc& R = c->desc[r];
     const int per = 32 / nss::cfg_g(R.cfg);
@@ -696,9 +780,24 @@ nss_status build_work(nss_ctx* c) {
     for (int j = 0; j < R.k; j += per) c->sweep_items[list].push_back({r, j, std::min(j + per, R.k), 0});
     int dq = 0;
     while ((8 << dq) < nss::dirgen_class(R.d)) ++dq;
+    if (!c->dir_fp32 && R.d > 16 && R.d <= 64) {
+      // tiles of 128 rows q = chain * p + step
+      const int kc = R.d <= 32 ? 1 : 2;
+      const int rows = R.k * R.p;
+      for (int q0 = 0; q0 < rows; q0 += 128)
+        c->dir_tc_items[g * 2 + kc - 1].push_back({r, q0, std::min(q0 + 128, rows), 0});
+      continue;
+    }
     for (int j = 0; j < R.k; j += 32)
       c->dir_items[g * nss_ctx::kDirClasses + dq].push_back({r, j, std::min(j + 32, R.k), 0});
   }
+  for (int q = 0; q < nss_ctx::kMaxGroups * 2; ++q) {
+    if (c->dir_tc_items[q].empty()) continue;
+    CK(cudaMalloc(&c->d_dir_tc[q], sizeof(WorkItem) * c->dir_tc_items[q].size()), "work list allocation");
+    CK(cudaMemcpyAsync(c->d_dir_tc[q], c->dir_tc_items[q].data(), sizeof(WorkItem) * c->dir_tc_items[q].size(),
+                       cudaMemcpyHostToDevice, c->stream), "work list upload");
+  }
+  for (int kc = 1; kc <= 2; ++kc) c->dir_tc_grid[kc - 1] = nss::dirgen_tc_blocks_per_sm(kc) * c->num_sms;
   for (int q = 0; q < nss_ctx::kMaxGroups * nss_ctx::kDirClasses; ++q) {
     if (c->dir_items[q].empty()) continue;
     CK(cudaMalloc(&c->d_dir[q], sizeof(WorkItem) * c->dir_items[q].size()), "work list allocation");
@@ -977,6 +1076,7 @@ void nss_options_default(nss_options* o) {
   o->rw_scale = 0.0;
   o->path = NSS_PATH_BATCHED;
   o->run_groups = 0;
+  o->dir_fp32 = 0;
 }
 
 int nss_abi_version(void) { return NSS_ABI_VERSION; }
@@ -1126,11 +1226,13 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   }
   c->R = opt[0].n_sim;
   for (int r = 1; r < n_runs; ++r)
-    if (opt[r].n_sim != c->R || opt[r].path != opt[0].path || opt[r].run_groups != opt[0].run_groups) {
+    if (opt[r].n_sim != c->R || opt[r].path != opt[0].path || opt[r].run_groups != opt[0].run_groups ||
+        opt[r].dir_fp32 != opt[0].dir_fp32) {
       delete c;
       return NSS_ERR_ARG;
     }
   c->plain = opt[0].path == NSS_PATH_PLAIN;
+  c->dir_fp32 = opt[0].dir_fp32 != 0;
   if (c->plain && n_runs != 1) {
     delete c;
     std::fprintf(stderr, "nss_create: the plain path runs a single run\n");
@@ -1271,6 +1373,7 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
   CKC(nss::setup_gp_attributes(), "kernel attributes");
   CKC(nss::setup_gp_tc_attributes(), "kernel attributes");
   CKC(nss::setup_dirgen_attributes(), "kernel attributes");
+  CKC(nss::setup_dirgen_tc_attributes(), "kernel attributes");
   CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
   CKC(cudaMalloc(&c->d_desc, sizeof(RunDesc) * n_runs), "descriptor allocation");
   CKC(cudaMalloc(&c->d_state, sizeof(RunState) * n_runs), "state allocation");
@@ -1361,6 +1464,13 @@ nss_status nss_create_batch(int n_runs, const nss_prior* prior, const nss_loglik
       }
     }
     c->g_r0[c->n_groups] = n_runs;
+    for (int g = 0; g < c->n_groups; ++g) {
+      CKC(cudaEventCreateWithFlags(&c->side_fork[g], cudaEventDisableTiming), "event creation");
+      for (int k = 0; k < nss_ctx::kSide; ++k) {
+        CKC(cudaStreamCreateWithFlags(&c->side[g][k], cudaStreamNonBlocking), "stream creation");
+        CKC(cudaEventCreateWithFlags(&c->side_join[g][k], cudaEventDisableTiming), "event creation");
+      }
+    }
   }
   {
     nss_status sw = build_work(c);

@@ -116,6 +116,13 @@ int sweep_blocks_per_sm(int cfg, int kc);
 int dirgen_class(int d);
 cudaError_t setup_dirgen_attributes();
 cudaError_t launch_dirgen(int dclass, const Dev& D, const WorkItem* items, int n, int max_p, cudaStream_t s);
+// the same directions with the whitening product on the tensor cores
+// (nss_dirgen_tc.cu): items {run, q0, q1} are tiles of at most 128 rows
+// q = chain * p + step of one run, kc = 1 for 16 < d <= 32, 2 for d <= 64;
+// *err set when a tensor-core wait ran out
+cudaError_t setup_dirgen_tc_attributes();
+int dirgen_tc_blocks_per_sm(int kc);
+cudaError_t launch_dirgen_tc(int kc, const Dev& D, const WorkItem* items, int n, int grid, int* err, cudaStream_t s);
 cudaError_t launch_sweep_lane(int dmax, int kc, const Dev& D, const WorkItem* items, int n, int* queue, int grid,
                               cudaStream_t s);
 int sweep_lane_blocks_per_sm(int dmax, int kc);

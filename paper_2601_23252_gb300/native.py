@@ -48,7 +48,8 @@ class Options(C.Structure):
                 ("dir_norm", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("dead_capacity", C.c_longlong), ("n_sim", C.c_int), ("cov_eps", C.c_double),
                 ("cuda_stream", C.c_void_p), ("sweep_cfg", C.c_int), ("kernel", C.c_int),
-                ("rw_scale", C.c_double), ("path", C.c_int), ("run_groups", C.c_int)]
+                ("rw_scale", C.c_double), ("path", C.c_int), ("run_groups", C.c_int),
+                ("dir_fp32", C.c_int)]
 
 
 class StepInfo(C.Structure):

@@ -117,11 +117,15 @@ def test_autograd_function(gpu_lib):
 
 def test_logistic_prior_log_precision_against_finite_differences(gpu_lib):
     """d lnZ/d lambda (prior sd b e^{-lambda/2}) at lambda = 0 from the Fisher
-    kernel against central differences of lnZ at +-h, the same seeds on both
-    sides (common random numbers)."""
-    h = 0.25
-    seeds = range(8)
-    base = [W.logreg_d100(seed=sd, n_rows=400, d=6, n_live=200, k=100).with_(run_id=sd) for sd in seeds]
+    kernel against the five-point difference of lnZ at +-h, +-2h, the same
+    seeds at every lambda, at the shape of the paper's GermanCredit logistic
+    regression (d = 25, N = 1000 rows).  lnZ(lambda) carries the term
+    -e^lambda E|w|^2 / 2 (about -12 nat here), whose odd derivatives are all
+    about -12: a central difference at h = 0.5 would be biased by h^2/6 of
+    that (-0.5 nat); the five-point rule leaves h^4/30 of it (0.03)."""
+    h = 0.5
+    seeds = range(32)
+    base = [W.logreg_d100(seed=sd, n_rows=1000, d=25, n_live=200, k=100).with_(run_id=sd) for sd in seeds]
     d = base[0].d
 
     def at(lam):
@@ -130,14 +134,14 @@ def test_logistic_prior_log_precision_against_finite_differences(gpu_lib):
     with native.Sampler(at(0.0)) as s:
         res = s.run()
         g = np.array([s.posterior(native.GRAD_PRIOR_LOG_PREC, r)[0] for r in range(len(base))])
-    with native.Sampler(at(h)) as s:
-        zp = np.array([r["logZ"] for r in s.run()])
-    with native.Sampler(at(-h)) as s:
-        zm = np.array([r["logZ"] for r in s.run()])
-    fd = (zp - zm) / (2 * h)
+    z = {}
+    for q in (-2, -1, 1, 2):
+        with native.Sampler(at(q * h)) as s:
+            z[q] = np.array([r["logZ"] for r in s.run()])
+    fd = (8.0 * (z[1] - z[-1]) - (z[2] - z[-2])) / (12.0 * h)
     diff = g - fd
     se = diff.std(ddof=1) / np.sqrt(diff.size)
-    print(f"\nFisher {g.mean():.4f}, finite differences {fd.mean():.4f}, paired se {se:.4f}, "
+    print(f"\nFisher {g.mean():.4f}, five-point differences {fd.mean():.4f}, paired se {se:.4f}, "
           f"logZ err {np.mean([r['logZ_err'] for r in res]):.3f}")
     assert abs(diff.mean()) <= 4 * se + 0.05
 

@@ -61,14 +61,15 @@ __device__ __forceinline__ int sw128(int r, int c4) { return r * 128 + ((c4 ^ (r
 // Words nz .. nz + 11 of the step's counter stream (U, slice height,
 // reserved, the first nine shrinkage proposals), as the CUDA-core kernel
 // writes them.
-__device__ __forceinline__ void step_words_tc(const RunDesc& R, uint32_t iter, int j, int s, int* __restrict__ wout) {
-  const uint32_t nz = 2u * (uint32_t)((R.d + 1) >> 1);
+__device__ __forceinline__ void step_words_tc(uint32_t k0, uint32_t k1, int d, int p, uint32_t iter, int j, int s,
+                                              int* __restrict__ wout) {
+  const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
   const int b0 = (int)(nz >> 2), off = (int)(nz & 3u);
-  int* o = wout + ((long long)j * R.p + s) * kStepWords;
+  int* o = wout + ((long long)j * p + s) * kStepWords;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (q == 3 && off == 0) break;
-    const uint4 blk = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)(b0 + q));
+    const uint4 blk = philox4x32_10(make_uint4(iter, (uint32_t)j, (uint32_t)s, (uint32_t)(b0 + q)), k0, k1);
     const uint32_t w[4] = {blk.x, blk.y, blk.z, blk.w};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -130,8 +131,12 @@ __global__ void __launch_bounds__(kDtThreads) k_dirgen_tc(Dev D, const WorkItem*
     for (int ci = 0; ci < kDtCache && alive; ++ci) {
       const int4 e = cache[ci];
       if (e.w) continue;  // a finished run, or past the list (the same for the whole block)
+      // the run's fields in registers, loaded once per tile
       const RunDesc& R = D.desc[e.x];
       const int d = R.d, ld = R.dpad, p = R.p;
+      const uint32_t k0 = R.key0, k1 = R.key1;
+      const long long o_V = R.o_V, o_wd = R.o_wd;
+      const bool unit_l = R.kernel == kKernelRw, mahal = R.dir_norm == 0;
       const uint32_t iter = (uint32_t)D.st[e.x].iter;
       // the factor L, rows n < N (zero above the diagonal and past d): this
       // thread's granules are loaded now and staged after the normals
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(kDtThreads) k_dirgen_tc(Dev D, const WorkItem*
         const int b = h * kHalfB + bb;
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid && 4 * b < d) {
-          const uint4 w = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)b);
+          const uint4 w = philox4x32_10(make_uint4(iter, (uint32_t)j, (uint32_t)s, (uint32_t)b), k0, k1);
           box_muller(w.x, w.y, z.x, z.y);
           box_muller(w.z, w.w, z.z, z.w);
           if (4 * b + 1 >= d) z.y = 0.f;
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(kDtThreads) k_dirgen_tc(Dev D, const WorkItem*
         *reinterpret_cast<float4*>(Bhi + c * T::kB + sw128(n, c4)) = hi;
         *reinterpret_cast<float4*>(Blo + c * T::kB + sw128(n, c4)) = lo;
       }
-      if (valid && h == 1) step_words_tc(R, iter, j, s, D.i + R.o_wd);
+      if (valid && h == 1) step_words_tc(k0, k1, d, p, iter, j, s, D.i + o_wd);
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       __syncthreads();
@@ -236,9 +241,9 @@ __global__ void __launch_bounds__(kDtThreads) k_dirgen_tc(Dev D, const WorkItem*
       part[h][r] = dd;  // every thread read its z sum before the MMA wait
       __syncthreads();
       if (valid) {
-        const float nrm = R.dir_norm == 0 ? zsum : part[0][r] + part[1][r];
-        const float inrm = R.kernel == kKernelRw ? 1.0f : rsqrtf(nrm);  // RW: L z itself
-        float4* out = reinterpret_cast<float4*>(D.f + R.o_V + (long long)q * ld + h * kHalfC);
+        const float nrm = mahal ? zsum : part[0][r] + part[1][r];
+        const float inrm = unit_l ? 1.0f : rsqrtf(nrm);  // RW: L z itself
+        float4* out = reinterpret_cast<float4*>(D.f + o_V + (long long)q * ld + h * kHalfC);
 #pragma unroll
         for (int b = 0; b < kHalfC / 4; ++b)
           if (h * kHalfC + 4 * b < ld)

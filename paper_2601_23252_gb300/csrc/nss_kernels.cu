@@ -83,94 +83,40 @@ __device__ void append_dead(const Dev& D, const RunDesc& R, RunState& S,
 }
 
 // Cholesky factor of S + reg I ([ld][ld] in shared memory) into Lm
-// ([ld][ld + 1]: the odd row stride keeps a warp's row accesses on distinct
-// banks) by warp 0: right-looking column steps, lane l owns rows l, l + 32,
-// ...; only warp-level synchronisation inside.  Every thread of the block
-// calls it; returns true (for every thread) on a non-positive or
-// non-finite pivot.
-__device__ bool cholesky_smem(const float* S, float* Lm, int d, int ld, float reg, int* flag) {
-  const int lw = ld + 1;
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int t = lane; t < ld * ld; t += 32) {
-      const int a = t / ld, b = t - a * ld;
-      Lm[a * lw + b] = (b <= a && a < d) ? S[t] + (a == b ? reg : 0.0f) : 0.0f;
-    }
-    __syncwarp();
-    bool bad = false;
-    for (int j = 0; j < d; ++j) {
-      const float piv = Lm[j * lw + j];
-      if (!(piv > 0.0f) || !isfinite(piv)) {
-        bad = true;
-        break;
-      }
-      const float ljj = sqrtf(piv);
-      __syncwarp();
-      for (int i = j + 1 + lane; i < d; i += 32) Lm[i * lw + j] /= ljj;
-      if (lane == 0) Lm[j * lw + j] = ljj;
-      __syncwarp();
-      for (int i = j + 1 + lane; i < d; i += 32) {
-        const float lij = Lm[i * lw + j];
-        for (int q = j + 1; q <= i; ++q) Lm[i * lw + q] = fmaf(-lij, Lm[q * lw + j], Lm[i * lw + q]);
-      }
-      __syncwarp();
-    }
-    if (lane == 0) *flag = bad ? 1 : 0;
+// ([ld][ld + 1]) by the whole block: right-looking column steps with one
+// block barrier each.  At step j the warps take the rows i > j and their
+// lanes the columns j < q <= i, A_iq -= (A_ij / l_jj)(A_qj / l_jj), while
+// column j - 1 (read by no thread of this step) is scaled to its final
+// values.  Every thread of the block calls it; returns true (for every
+// thread) on a non-positive or non-finite pivot.
+__device__ bool cholesky_block(const float* S, float* Lm, int d, int ld, float reg) {
+  const int lw = ld + 1, T = blockDim.x, nw = T >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < ld * ld; t += T) {
+    const int a = t / ld, b = t - a * ld;
+    Lm[a * lw + b] = (b <= a && a < d) ? S[t] + (a == b ? reg : 0.0f) : 0.0f;
   }
   __syncthreads();
-  const bool fail = *flag != 0;
-  __syncthreads();
-  return fail;
-}
-
-// d <= 32: warp 0 alone, row i in lane i's registers, column j broadcast
-// through shared memory (no block barriers inside).  Same operations in
-// the same order as cholesky_smem.  The column loop is not unrolled: after
-// column j every lane shifts its row left by one register, so the current
-// column is always a[0] and the loop body stays small (measured: ~1000
-// cycles per column against ~1270 fully unrolled; the column chain of
-// shuffle, square root, division and broadcast is what remains).
-__device__ bool cholesky_warp32(const float* S, float* Lm, int d, int ld, float reg, int* flag) {
-  __shared__ float colv[32];
-  const int lw = ld + 1;
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    float a[32];  // a[q]: this row's entry in column j + q
-#pragma unroll
-    for (int q = 0; q < 32; ++q)
-      a[q] = (lane < d && q <= lane) ? S[lane * ld + q] + (q == lane ? reg : 0.0f) : 0.0f;
-    bool bad = false;
-#pragma unroll 1
-    for (int j = 0; j < d; ++j) {
-      const float piv = __shfl_sync(0xffffffffu, a[0], j);
-      bad = !(piv > 0.0f) || !isfinite(piv);
-      if (bad) break;  // the pivot is the same in every lane
-      const float ljj = sqrtf(piv);
-      if (lane > j) a[0] = a[0] / ljj;
-      else if (lane == j) a[0] = ljj;
-      if (lane < ld) Lm[lane * lw + j] = (lane < d && j <= lane) ? a[0] : 0.0f;
-      colv[lane] = a[0];
-      __syncwarp();
-      const float lij = a[0];
-#pragma unroll
-      for (int q = 1; q < 32; ++q) {
-        const int cq = j + q;
-        const float lqj = colv[min(cq, 31)];
-        if (lane > j && cq <= lane) a[q] = fmaf(-lij, lqj, a[q]);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int q = 0; q < 31; ++q) a[q] = a[q + 1];
-      a[31] = 0.0f;
+  bool bad = false;
+  float lprev = 0.0f, iprev = 0.0f;
+  for (int j = 0; j < d; ++j) {
+    const float piv = Lm[j * lw + j];
+    bad = !(piv > 0.0f) || !isfinite(piv);  // the same in every thread
+    if (bad) break;
+    const float ljj = sqrtf(piv), inv = 1.0f / ljj;
+    for (int i = j + 1 + wid; i < d; i += nw) {
+      const float lij = Lm[i * lw + j] * inv;
+      for (int q = j + 1 + lane; q <= i; q += 32) Lm[i * lw + q] = fmaf(-lij, Lm[q * lw + j] * inv, Lm[i * lw + q]);
     }
-    if (lane < ld)
-      for (int q = d; q < ld; ++q) Lm[lane * lw + q] = 0.0f;
-    if (lane == 0) *flag = bad ? 1 : 0;
+    if (j > 0)
+      for (int i = j - 1 + threadIdx.x; i < d; i += T)
+        Lm[i * lw + j - 1] = (i == j - 1) ? lprev : Lm[i * lw + j - 1] * iprev;
+    lprev = ljj;
+    iprev = inv;
+    __syncthreads();
   }
+  if (!bad && threadIdx.x == 0) Lm[(d - 1) * lw + d - 1] = lprev;
   __syncthreads();
-  const bool fail = *flag != 0;
-  __syncthreads();
-  return fail;
+  return bad;
 }
 
 // Direction metric (Sec. 3.2): covariance of the m live points (divisor m-1)
@@ -182,7 +128,6 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
   const int d = R.d, ld = R.dpad, m = R.m, T = blockDim.x;
   const float* X = D.f + R.o_x;
   __shared__ float mu_s[kMaxD];
-  __shared__ int flag_s;
   __shared__ double red_s[32];
   float* part = reinterpret_cast<float*>(smem);
   // mean of x - x_0 per dimension
@@ -265,7 +210,7 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
     float reg = R.cov_eps * (float)tr / (float)d;
     bool fail = true;
     for (int attempt = 0; attempt <= 6; ++attempt) {
-      fail = (d <= 32) ? cholesky_warp32(Sm, Lm, d, ld, reg, &flag_s) : cholesky_smem(Sm, Lm, d, ld, reg, &flag_s);
+      fail = cholesky_block(Sm, Lm, d, ld, reg);
       __syncthreads();
       if (!fail) break;
       reg *= 10.0f;

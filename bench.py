@@ -60,6 +60,9 @@ def parse():
                          "group (the case captured by ncu)")
     ap.add_argument("--ncu-cfg", type=int, default=-1,
                     help="with --ncu-case: force this sweep configuration id instead of autotuning")
+    ap.add_argument("--ncu-cfgs", default="",
+                    help="with --ncu-case: comma-separated sweep configuration ids; each run takes the one "
+                         "whose capacity fits its dimension (no autotuning)")
     ap.add_argument("--ncu-case-gmm", action="store_true",
                     help="no timing: gmm_d32 (20 seeds) for a few iterations, one run group")
     ap.add_argument("--ncu-case-logreg", action="store_true",
@@ -158,9 +161,9 @@ def source_hash():
 
 
 def ncu_traffic(name):
-    """DRAM bytes per sweep launch of the headline workload from the committed
-    ncu summary `name`, if it was taken on the current sweep sources (else
-    None)."""
+    """DRAM bytes per sweep chain-step of the headline workload from the
+    committed ncu summary `name`, if it was taken on the current sweep sources
+    (else None)."""
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
@@ -172,7 +175,7 @@ def ncu_traffic(name):
     if vals.get("source_hash") != source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch_full_size"])
+        return float(vals["dram_bytes_per_chain_step"])
     except (KeyError, ValueError):
         return None
 
@@ -459,6 +462,7 @@ def run_native(args):
     kl = {k: p1["launches"][k] - p0["launches"][k] for k in p1["launches"]}
     ksum = sum(kms.values())
     sflops = sum(sweep_flops(w, r["evals"], r["iters"] * w.k * w.p) for w, r in zip(wls, r1))
+    steps_per_launch = sum(r["iters"] * w.k * w.p for w, r in zip(wls, r1)) / max(1, kl["sweep"])
     dflops = sum(dirgen_flops(w, r["iters"] * w.k * w.p) for w, r in zip(wls, r1))
     peaks, src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -469,7 +473,9 @@ def run_native(args):
     line["roofline"] = {
         "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
         "frac": (achieved / fp32_peak) if achieved else None,
-        "traffic": ncu_traffic("ncu_sweep_batch64.txt"),
+        "traffic": (lambda b: b * steps_per_launch if b is not None else None)(ncu_traffic("ncu_sweep_batch64.txt")),
+        "traffic_scaling": "ncu DRAM bytes per chain-step of the sweep launches of the small capture "
+                           "(profiles/ncu_sweep_batch64.txt) x chain-steps per launch of this pass",
         "kernel": "k_sweep (HRSS sweep, fused Gaussian likelihood)",
         "dominant_kernel_in_profile": dom,
         "peak_source": f"derived, not measured: FP32 FMA pipe {sms} SMs x 128 lanes x 2 flop x "
@@ -706,18 +712,41 @@ def leg_gp(stream, fp32_peak):
 # ---- small cases for ncu captures ---------------------------------------------------
 def run_ncu_case(args):
     """The headline batch for 6 outer iterations, then exit; dead stores sized
-    for those iterations, one run group, so the device footprint stays small."""
+    for those iterations, one run group, so the device footprint stays small.
+    Prints the chain-steps each sweep configuration's launch covers per
+    iteration (every run is still going in these iterations)."""
     from paper_2601_23252_gb300 import native
     from paper_2601_23252_gb300 import workloads as W
     opts = {"dead_capacity": 8 * 250 + 500, "run_groups": 1}
     if args.ncu_cfg >= 0:
         opts["sweep_cfg"] = args.ncu_cfg
     wls = [with_opts(w, **opts) for w in W.batch64(seed=0)]
+    if args.ncu_cfgs:
+        ids = [int(q) for q in args.ncu_cfgs.split(",")]
+        def cap(d):
+            c = 4
+            while c < d:
+                c *= 2
+            return c
+        def fit(d):
+            for q in ids:
+                info = native.Sampler.cfg_info(q)
+                if info["lanes_per_chain"] * info["dims_per_lane"] == cap(d):
+                    return q
+            raise SystemExit(f"--ncu-cfgs: no configuration of capacity {cap(d)}")
+        wls = [with_opts(w, sweep_cfg=fit(w.d)) for w in wls]
     with native.Sampler(wls) as s:
-        if args.ncu_cfg < 0:
+        if args.ncu_cfg < 0 and not args.ncu_cfgs:
             s.autotune(iters=2)
+        cfgs = [s.cfg(r)["id"] for r in range(len(wls))]
         for _ in range(6):
             s.step()
+    steps = {}
+    for w, q in zip(wls, cfgs):
+        info = native.Sampler.cfg_info(q)
+        key = f"{info['lanes_per_chain']}x{info['dims_per_lane']}"
+        steps[key] = steps.get(key, 0) + w.k * w.p
+    print(json.dumps({"chain_steps_per_iteration_by_cfg": steps}))
     return 0
 
 

@@ -411,7 +411,7 @@ def run_native(args):
         sampler.run()
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    times, dead, evals, spec = [], 0, 0, 0
+    times, dead, evals, spec, rounds, act = [], 0, 0, 0, 0, 0
     l0 = sampler.profile()["total_launches"]
     barrier()
     torch.cuda.synchronize()
@@ -424,6 +424,8 @@ def run_native(args):
             dead += r["n_dead"]
             evals += r["evals"]
             spec += r["spec_evals"]
+            rounds += r["group_rounds"]
+            act += r["active_group_rounds"]
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
@@ -446,6 +448,10 @@ def run_native(args):
                        "autotune_ms_per_Meval": tune, "evidence_accumulation": "f64"},
             "evals_per_s": evals_all / (total_ms_all / 1e3),
             "speculative_tests_per_eval": spec / max(1, evals),
+            "lockstep": {"group_rounds": int(rounds), "active_fraction": act / max(1, rounds),
+                         "what": "slice-test rounds of the grouped sweep, summed over chain groups; the "
+                                 "fraction in which the group still had tests to run (the rest: lockstep "
+                                 "idle rounds while another group of the warp finishes)"},
             "gate": logz_gate(wls, res, checker),
             "gpu_launches": int(launches), "clocks": clk}
 

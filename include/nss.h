@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NSS_ABI_VERSION 6
+#define NSS_ABI_VERSION 7
 
 typedef struct nss_ctx nss_ctx;
 
@@ -206,6 +206,12 @@ typedef struct {
     long long spec_evals;      /* slice tests run beyond the logical evaluations
                                   (a chain group tests several stepping-out ends
                                   or shrinkage proposals at once)               */
+    long long group_rounds;    /* slice-test rounds run by the chain groups of
+                                  the grouped sweep (a warp's groups run every
+                                  round until all of them are done), summed over
+                                  groups                                        */
+    long long active_group_rounds; /* ... of which the group was still testing:
+                                  the rest are lockstep idle rounds             */
     int metric_status;         /* 0 ok, 1 identity fallback, 2 jitter retried    */
     int status;                /* nss_status of the run                          */
 } nss_step_info;
@@ -224,6 +230,8 @@ typedef struct {
     long long cap_out;
     long long nan_evals;
     long long spec_evals;      /* as in nss_step_info                            */
+    long long group_rounds;    /* as in nss_step_info                            */
+    long long active_group_rounds;
     int status;
 } nss_result;
 

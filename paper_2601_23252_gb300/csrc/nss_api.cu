@@ -975,6 +975,8 @@ void fill_info(const nss_ctx* c, nss_step_info* info) {
     o.cap_out = s.cap_out;
     o.nan_evals = s.nan_evals;
     o.spec_evals = s.spec_evals;
+    o.group_rounds = s.rounds;
+    o.active_group_rounds = s.active_rounds;
     o.metric_status = s.metric_status;
     o.status = s.status;
   }
@@ -1043,6 +1045,8 @@ nss_status finalise_impl(nss_ctx* c, nss_result* res) {
       o.cap_out = s.cap_out;
       o.nan_evals = s.nan_evals;
       o.spec_evals = s.spec_evals;
+      o.group_rounds = s.rounds;
+      o.active_group_rounds = s.active_rounds;
       o.status = s.status;
     }
     if (s.status == NSS_ERR_CAPACITY) worst = NSS_ERR_CAPACITY;

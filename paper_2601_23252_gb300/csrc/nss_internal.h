@@ -62,6 +62,7 @@ struct RunState {
   double logZ, logX;
   long long n_dead, evals, nulls, cap_out, nan_evals;
   long long spec_evals;             // slice tests run beyond the logical ones (group-parallel rounds)
+  long long rounds, active_rounds;  // slice-test rounds of the chain groups' warps, and those each group took part in
   int iter, done, status, metric_status;
   float logLstar;
   int stepped;                      // at least one iteration since create/import

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(128) k_lr_dir(Dev D, LRArgs A, int run, int st
 // other likelihood).
 // ---------------------------------------------------------------------------
 template <int EMAX>
-__global__ void __launch_bounds__(kLRThreads) k_lr_slice(Dev D, LRArgs A, int run, int step) {
+__global__ void __launch_bounds__(kLRThreads, 2) k_lr_slice(Dev D, LRArgs A, int run, int step) {
   __shared__ float2 red[33];
   const RunDesc& R = D.desc[run];
   RunState* S = D.st + run;

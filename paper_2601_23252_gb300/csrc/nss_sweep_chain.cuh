@@ -73,6 +73,9 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   // one test per step: evals = p).
   int acc = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
   int ran = 0;  // slice tests this lane ran (logical or speculative)
+  // slice-test rounds of the warp, and those this group still needed (the
+  // others are lockstep idle rounds of a group that is done)
+  int rounds = 0, active = 0;
   // the steps' directions, drawn ahead (nss_dirgen.cu); the load of step
   // s + 1's is issued while step s runs
   const float* vrow = f + R.o_V + (long long)j * R.p * ld;
@@ -352,6 +355,8 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       // rounds until every group of the warp has stopped both sides; a group
       // that has stops testing (its lanes evaluate but count nothing)
       for (int b0 = 0; __any_sync(kAll, stop[0] < 0 || stop[1] < 0); b0 += H) {
+        ++rounds;
+        active += (stop[0] < 0 || stop[1] < 0) ? 1 : 0;
         const int idx = b0 + hl;
         const bool mine = (side ? stop[1] : stop[0]) < 0 && idx < kStepOutCap;
         float t = side ? base[1] : base[0];
@@ -418,6 +423,8 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     float tacc = 0.0f, llacc = 0.0f;
     constexpr unsigned kGroupBits = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
     for (int b0 = 0; b0 < kShrinkCap && __any_sync(kAll, !ok); b0 += G) {
+      ++rounds;
+      active += ok ? 0 : 1;
       const int idx = b0 + gl;
       const bool mine = !ok && idx < kShrinkCap;
       uint32_t wr;
@@ -495,6 +502,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     if (capo) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->cap_out), (unsigned long long)capo);
     if (nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->nan_evals), (unsigned long long)nanc);
     if (ran > evals) atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->spec_evals), (unsigned long long)(ran - evals));
+    if (rounds) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->rounds), (unsigned long long)rounds);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&Sw->active_rounds), (unsigned long long)active);
+    }
   }
 }
 

@@ -56,14 +56,16 @@ class StepInfo(C.Structure):
     _fields_ = [("iter", C.c_int), ("done", C.c_int), ("logLstar", C.c_float), ("logZ", C.c_double),
                 ("logX", C.c_double), ("n_dead", C.c_longlong), ("evals", C.c_longlong),
                 ("nulls", C.c_longlong), ("cap_out", C.c_longlong), ("nan_evals", C.c_longlong),
-                ("spec_evals", C.c_longlong), ("metric_status", C.c_int), ("status", C.c_int)]
+                ("spec_evals", C.c_longlong), ("group_rounds", C.c_longlong),
+                ("active_group_rounds", C.c_longlong), ("metric_status", C.c_int), ("status", C.c_int)]
 
 
 class Result(C.Structure):
     _fields_ = [("logZ", C.c_double), ("logZ_err", C.c_double), ("logZ_det", C.c_double),
                 ("n_dead", C.c_longlong), ("iters", C.c_int), ("evals", C.c_longlong),
                 ("nulls", C.c_longlong), ("cap_out", C.c_longlong), ("nan_evals", C.c_longlong),
-                ("spec_evals", C.c_longlong), ("status", C.c_int)]
+                ("spec_evals", C.c_longlong), ("group_rounds", C.c_longlong),
+                ("active_group_rounds", C.c_longlong), ("status", C.c_int)]
 
 
 class State(C.Structure):

@@ -31,7 +31,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_abi_version_and_status_strings(lib):
     lib.nss_status_string.restype = C.c_char_p
-    assert lib.nss_abi_version() == 6
+    assert lib.nss_abi_version() == 7
     assert lib.nss_status_string(0) == b"ok"
     assert lib.nss_status_string(-4) == b"dead-point store full"
 

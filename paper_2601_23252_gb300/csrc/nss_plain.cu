@@ -69,11 +69,8 @@ struct PlainChain {
         const float ai = pa[i] - xi, bi = pb[i] - xi;
         const float rv = __fdividef(1.0f, vi);
         const float ta = ai * rv, tb = bi * rv;
-        const bool pos = vi > 0.0f, neg = vi < 0.0f;
-        const float lo = pos ? ta : neg ? tb : (ai <= 0.0f && bi >= 0.0f) ? -INFINITY : INFINITY;
-        const float hi = pos ? tb : neg ? ta : INFINITY;
-        t_lo = fmaxf(t_lo, lo);
-        t_hi = fminf(t_hi, hi);
+        t_lo = fmaxf(t_lo, fminf(ta, tb));
+        t_hi = fminf(t_hi, fmaxf(ta, tb));
       }
       ok = t >= t_lo && t <= t_hi;
     } else {

@@ -157,16 +157,15 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       float t_lo = -INFINITY, t_hi = INFINITY;
 #pragma unroll
       for (int i = 0; i < DPL; ++i) {
-        // a <= x + t v <= b per dimension, by selects (no lane branches);
-        // v = 0 leaves t free if x is inside, else empties the interval
+        // a <= x + t v <= b per dimension: [ta, tb] for v > 0, [tb, ta] for
+        // v < 0, so the smaller end bounds t below and the larger above
+        // (no lane branches); v = 0 with x strictly inside gives the
+        // infinite ends of the reciprocal and leaves t free
         const float ai = pa[i] - x[i], bi = pb[i] - x[i];
         const float rv = __fdividef(1.0f, v[i]);
         const float ta = ai * rv, tb = bi * rv;
-        const bool pos = v[i] > 0.0f, neg = v[i] < 0.0f;
-        const float lo = pos ? ta : neg ? tb : (ai <= 0.0f && bi >= 0.0f) ? -INFINITY : INFINITY;
-        const float hi = pos ? tb : neg ? ta : INFINITY;
-        t_lo = own[i] ? fmaxf(t_lo, lo) : t_lo;
-        t_hi = own[i] ? fminf(t_hi, hi) : t_hi;
+        t_lo = own[i] ? fmaxf(t_lo, fminf(ta, tb)) : t_lo;
+        t_hi = own[i] ? fminf(t_hi, fmaxf(ta, tb)) : t_hi;
       }
       q0 = gmax<G>(t_lo, kAll);
       q1 = -gmax<G>(-t_hi, kAll);

@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -31,40 +32,56 @@ namespace nss {
 //   X   : bf16 [rows_pad][128]          (tensor map mapX, box 64 x 128)
 //   U   : bf16 [3][cols_pad][128]       (tensor map mapU, box 64 x 128)
 //   out : fp32 [cols][ldo]
-// One 128-thread block per 128 x 128 output tile: thread 0 issues the eight
-// TMA loads (two K chunks of X, three parts x two K chunks of U), thread 32
-// issues 24 MMAs of 128 x 128 x 16 into a 128-column TMEM accumulator, and
-// the four warps read their 32 TMEM lanes back and store coalesced rows.
+// Persistent, warp-specialised: block b owns the 128-column tile b mod nct
+// and the row tiles b / nct, b / nct + G / nct, ... (G blocks, a multiple of
+// nct).  Warp 4 issues the TMA loads: the block's three U parts once, then
+// each row tile's X into one of two stages; warp 5 issues the 24 MMAs of a
+// tile (K = 128 in 8 steps x 3 bf16 parts) into one of two 128-column TMEM
+// accumulators; warps 0-3 read an accumulator back (tcgen05.ld) and store
+// coalesced rows while the next tile's loads and products proceed.  Stages
+// and accumulators are handed over by mbarriers (transaction counts for the
+// loads, tcgen05.commit for the products, 128 arrivals for the drained
+// accumulator); every wait is bounded.
 // ---------------------------------------------------------------------------
 constexpr int kTile = 128;
 constexpr uint32_t kChunkBytes = 128u * 64u * 2u;   // 128 rows x 64 bf16
 constexpr uint32_t kMaxPolls = 1u << 22;
-constexpr int kLogitsSmem = 8 * kChunkBytes + 1024;
+constexpr int kLogitsThreads = 192;                 // warps 0-3 epilogue, 4 loads, 5 products
+constexpr int kLogitsSmem = 10 * kChunkBytes + 1024;  // U: 3 parts x 2 chunks; X: 2 stages x 2 chunks
 
-__global__ void __launch_bounds__(128, 1) k_logits(const __grid_constant__ CUtensorMap mapX,
-                                                    const __grid_constant__ CUtensorMap mapU, int cols_pad,
-                                                    float* __restrict__ out, long long ldo, int n_rows,
-                                                    int n_cols, int* __restrict__ err,
-                                                    const int* __restrict__ skip,
-                                                    const float* __restrict__ zref) {
+__global__ void __launch_bounds__(kLogitsThreads, 1) k_logits(const __grid_constant__ CUtensorMap mapX,
+                                                               const __grid_constant__ CUtensorMap mapU,
+                                                               int cols_pad, float* __restrict__ out, long long ldo,
+                                                               int n_rows, int n_cols, int* __restrict__ err,
+                                                               const int* __restrict__ skip,
+                                                               const float* __restrict__ zref) {
   if (skip && *skip) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* A = base;                      // [2 chunks]
-  uint8_t* B = base + 2 * kChunkBytes;    // [3 parts][2 chunks]
-  __shared__ __align__(8) uint64_t bar_full;
-  __shared__ __align__(8) uint64_t bar_mma;
+  uint8_t* B = base;                      // [3 parts][2 chunks]
+  uint8_t* A = base + 6 * kChunkBytes;    // [2 stages][2 chunks]
+  __shared__ __align__(8) uint64_t bfull, afull[2], aempty[2], dfull[2], dempty[2];
   __shared__ uint32_t tmem_base;
+  __shared__ int failed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = blockIdx.x * kTile, col0 = blockIdx.y * kTile;
-
+  const int nct = (n_cols + kTile - 1) / kTile, nrt = (n_rows + kTile - 1) / kTile;
+  const int per = gridDim.x / nct;        // blocks per column tile
+  const int ct = blockIdx.x % nct, rt0 = blockIdx.x / nct;
+  const int col0 = ct * kTile;
+  const int ntiles = rt0 < nrt ? (nrt - rt0 + per - 1) / per : 0;
   if (threadIdx.x == 0) {
-    tc::mbar_init(&bar_full, 1);
-    tc::mbar_init(&bar_mma, 1);
+    tc::mbar_init(&bfull, 1);
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(&afull[s], 1);
+      tc::mbar_init(&aempty[s], 1);
+      tc::mbar_init(&dfull[s], 1);
+      tc::mbar_init(&dempty[s], 128);
+    }
+    failed = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 128);
+  if (warp == 5) {
+    tc::tmem_alloc(&tmem_base, 256);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -72,59 +89,89 @@ __global__ void __launch_bounds__(128, 1) k_logits(const __grid_constant__ CUten
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
 
-  if (threadIdx.x == 0) {
-    tc::mbar_arrive_expect_tx(&bar_full, 8 * kChunkBytes);
-    for (int c = 0; c < 2; ++c) tc::tma_load_2d(A + c * kChunkBytes, &mapX, &bar_full, c * 64, row0);
-    for (int p = 0; p < 3; ++p)
-      for (int c = 0; c < 2; ++c)
-        tc::tma_load_2d(B + (p * 2 + c) * kChunkBytes, &mapU, &bar_full, c * 64, p * cols_pad + col0);
-  }
-  if (threadIdx.x == 32) {
-    if (tc::mbar_wait(&bar_full, 0, kMaxPolls)) {
-      tc::fence_after_sync();
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTile, kTile);
-      uint32_t acc = 0;
-      for (int c = 0; c < 2; ++c)
-        for (int p = 0; p < 3; ++p)
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(A + c * kChunkBytes) + kk * 32);
-            const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(B + (p * 2 + c) * kChunkBytes) + kk * 32);
-            tc::mma_bf16(tmem, ad, bd, idesc, acc);
-            acc = 1;
-          }
-      tc::mma_commit(&bar_mma);
-    } else {
-      atomicExch(err, 1);
-    }
-  }
-  // every thread waits for the accumulator (bounded), decision made uniform
-  const bool ok = tc::mbar_wait(&bar_mma, 0, kMaxPolls);
-  const int all_ok = __syncthreads_and(ok ? 1 : 0);
-  if (all_ok) {
-    tc::fence_after_sync();
-    const int r = row0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int cc = 0; cc < 4; ++cc) {
-      float v[32];
-      tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(cc * 32), v);
-      if (r < n_rows) {
-        const float z0 = zref ? zref[r] : 0.0f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int c = col0 + cc * 32 + i;
-          if (c < n_cols) out[static_cast<long long>(c) * ldo + r] = v[i] + z0;
+  if (warp == 4) {
+    if (lane == 0 && ntiles > 0) {
+      tc::mbar_arrive_expect_tx(&bfull, 6 * kChunkBytes);
+      for (int p = 0; p < 3; ++p)
+        for (int c = 0; c < 2; ++c)
+          tc::tma_load_2d(B + (p * 2 + c) * kChunkBytes, &mapU, &bfull, c * 64, p * cols_pad + col0);
+      for (int i = 0; i < ntiles; ++i) {
+        const int s = i & 1;
+        if (i >= 2 && !tc::mbar_wait(&aempty[s], ((i >> 1) - 1) & 1, kMaxPolls)) {
+          atomicExch(err, 1);
+          failed = 1;
+          break;
         }
+        const int row0 = (rt0 + i * per) * kTile;
+        tc::mbar_arrive_expect_tx(&afull[s], 2 * kChunkBytes);
+        for (int c = 0; c < 2; ++c) tc::tma_load_2d(A + (s * 2 + c) * kChunkBytes, &mapX, &afull[s], c * 64, row0);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0 && ntiles > 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTile, kTile);
+      bool ok = tc::mbar_wait(&bfull, 0, kMaxPolls);
+      for (int i = 0; i < ntiles && ok; ++i) {
+        const int s = i & 1;
+        ok = tc::mbar_wait(&afull[s], (i >> 1) & 1, kMaxPolls);
+        if (ok && i >= 2) ok = tc::mbar_wait(&dempty[s], ((i >> 1) - 1) & 1, kMaxPolls);
+        if (!ok) break;
+        tc::fence_after_sync();
+        uint32_t acc = 0;
+        for (int c = 0; c < 2; ++c)
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(A + (s * 2 + c) * kChunkBytes) + kk * 32);
+              const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(B + (p * 2 + c) * kChunkBytes) + kk * 32);
+              tc::mma_bf16(tmem + (uint32_t)(s * kTile), ad, bd, idesc, acc);
+              acc = 1;
+            }
+        tc::mma_commit(&aempty[s]);
+        tc::mma_commit(&dfull[s]);
+      }
+      if (!ok) {
+        atomicExch(err, 2);
+        failed = 1;
       }
     }
   } else {
-    if (threadIdx.x == 0) atomicExch(err, 2);
-    // let any copy still in flight land before the block's shared memory goes away
-    tc::mbar_wait(&bar_full, 0, kMaxPolls);
+    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the tile)
+    for (int i = 0; i < ntiles; ++i) {
+      const int s = i & 1;
+      if (!tc::mbar_wait(&dfull[s], (i >> 1) & 1, kMaxPolls)) {
+        if (lane == 0) atomicExch(err, 3);
+        break;
+      }
+      tc::fence_after_sync();
+      const int r = (rt0 + i * per) * kTile + warp * 32 + lane;
+      const float z0 = (zref && r < n_rows) ? zref[r] : 0.0f;
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        float v[32];
+        tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(s * kTile + cc * 32), v);
+        if (r < n_rows) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int c = col0 + cc * 32 + q;
+            if (c < n_cols) out[static_cast<long long>(c) * ldo + r] = v[q] + z0;
+          }
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&dempty[s]);
+    }
+  }
+  // let any load or product still in flight land before shared and tensor
+  // memory go away (after a wait that ran out; bounded)
+  __syncthreads();
+  if (failed && threadIdx.x == 0) {
+    tc::mbar_wait(&bfull, 0, kMaxPolls);
+    for (int s = 0; s < 2; ++s) tc::mbar_wait(&afull[s], 0, kMaxPolls);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  if (warp == 5) tc::tmem_dealloc(tmem, 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -488,8 +535,15 @@ cudaError_t setup_logits_attributes() {
 cudaError_t launch_logits(const CUtensorMap& mapX, const CUtensorMap& mapU, int rows_pad, int cols_pad, float* out,
                           long long ldo, int n_rows, int n_cols, int* err, const int* skip, const float* zref,
                           cudaStream_t s) {
-  dim3 grid(rows_pad / kTile, (n_cols + kTile - 1) / kTile);
-  k_logits<<<grid, 128, kLogitsSmem, s>>>(mapX, mapU, cols_pad, out, ldo, n_rows, n_cols, err, skip, zref);
+  if (n_cols < 1 || n_rows < 1 || n_rows > rows_pad) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // one block per SM, a whole number of blocks per column tile
+  const int nct = (n_cols + kTile - 1) / kTile, nrt = (n_rows + kTile - 1) / kTile;
+  const int per = std::max(1, std::min(nrt, std::max(1, sms) / nct));
+  k_logits<<<nct * per, kLogitsThreads, kLogitsSmem, s>>>(mapX, mapU, cols_pad, out, ldo, n_rows, n_cols, err, skip,
+                                                          zref);
   return cudaGetLastError();
 }
 

@@ -703,11 +703,32 @@ def leg_logreg(stream, peaks):
         p1 = s.profile()
     kms = {k: p1["ms"][k] - p0["ms"][k] for k in p1["ms"]}
     kl = {k: p1["launches"][k] - p0["launches"][k] for k in p1["launches"]}
+    # the plain path on the same problem: each slice test's logits recomputed
+    # from the candidate point, one GEMM over the k chains per lockstep round
+    wp = with_opts(wl, path=native.PATH_PLAIN)
+    plain_iters = 2
+    with native.Sampler(wp, stream=stream.cuda_stream) as s:
+        s.step()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(plain_iters):
+            s.step()
+        e1.record(stream)
+        e1.synchronize()
+        ms_plain = e0.elapsed_time(e1) / plain_iters
     flops = 2.0 * wl.X.shape[0] * wl.d * wl.k  # the method's X v per chain, per launch
     per = kms["logits"] / max(1, kl["logits"])
     tfl = flops / (per / 1e3) / 1e12
     bf16 = peaks.get("bf16_tflops", 1900.0)
     return {"iters": iters, "value": wl.k * iters / (ms / 1e3), "unit": UNIT, "ms_per_iter": ms / iters,
+            "plain_path_ms_per_iter": ms_plain,
+            "line_affine_speedup": ms_plain / (ms / iters),
+            "line_affine_what": "ms per outer iteration of the plain path (one logits GEMM over the k chains' "
+                                "candidate points per lockstep evaluation round, host loop per round) over the "
+                                "batched path's (one GEMM per HRSS step, every slice test then N FMAs and N "
+                                "softplus terms on the line-affine logits)",
             "logits": {"avg_launch_ms": per, "method_tflops": tfl, "frac_of_bf16_peak": tfl / bf16,
                        "issued_tflops_3_bf16_parts": 3 * tfl, "peak_tflops": bf16, "of": "of measured"},
             "lr_slice_avg_launch_ms": kms["lr_slice"] / max(1, kl["lr_slice"]),

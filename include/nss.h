@@ -169,9 +169,13 @@ typedef struct {
    candidate's likelihood evaluated from scratch over all d coordinates, and
    a host loop that waits for each iteration.  Its FP32 expressions follow
    the batched sweep's in the run's sweep configuration, so both paths give
-   bit-identical dead points for the same configuration.  PLAIN requires a
-   single run (nss_create or n_runs = 1), the HRSS kernel, a Gaussian,
-   mixture or flat likelihood, k <= 1024 and a grouped sweep configuration
+   bit-identical dead points for the same configuration.  For a logistic
+   likelihood each round's candidate points take their logits from one
+   tensor-core GEMM over all k chains (the batched path forms them
+   line-affinely, one GEMM per HRSS step), and the host reads after every
+   round whether a chain is still testing.  PLAIN requires a single run
+   (nss_create or n_runs = 1), the HRSS kernel, a Gaussian, mixture, flat or
+   logistic likelihood, k <= 1024 and a grouped sweep configuration
    (sweep_cfg < 22; -1 picks the default one); otherwise NSS_ERR_ARG. */
 enum { NSS_PATH_BATCHED = 0, NSS_PATH_PLAIN = 1 };
 

@@ -38,6 +38,11 @@ struct LRWork {
   int* err = nullptr;
   CUtensorMap mapX, mapU;
   nss::LRArgs args;
+  // the plain path's direct evaluation: per-chain step state, the count of
+  // chains still testing (device, and its pinned host mirror)
+  nss::LRDirect* lrd = nullptr;
+  int* d_active = nullptr;
+  int* h_active = nullptr;
 };
 
 struct GPWork {
@@ -348,8 +353,10 @@ nss_status validate(nss_ctx* c, const nss_prior& pr, const nss_loglik& lk, int m
   if (o.run_groups != 0 && o.run_groups != 1) return set_err(c, NSS_ERR_ARG, "run %d: run_groups must be 0 or 1", run);
   if (o.path == NSS_PATH_PLAIN) {
     if (o.kernel != NSS_KERNEL_HRSS) return set_err(c, NSS_ERR_ARG, "run %d: the plain path runs the HRSS kernel", run);
-    if (lk.kind != NSS_LOGLIK_GAUSS_ISO && lk.kind != NSS_LOGLIK_GMM_ISO_EQUAL && lk.kind != NSS_LOGLIK_FLAT)
-      return set_err(c, NSS_ERR_ARG, "run %d: the plain path takes Gaussian, mixture or flat likelihoods", run);
+    if (lk.kind != NSS_LOGLIK_GAUSS_ISO && lk.kind != NSS_LOGLIK_GMM_ISO_EQUAL && lk.kind != NSS_LOGLIK_FLAT &&
+        lk.kind != NSS_LOGLIK_LOGREG)
+      return set_err(c, NSS_ERR_ARG, "run %d: the plain path takes Gaussian, mixture, flat or logistic likelihoods",
+                     run);
     if (k > 1024) return set_err(c, NSS_ERR_ARG, "run %d: the plain path takes k <= 1024", run);
     if (o.sweep_cfg >= nss::kLaneCfg0) return set_err(c, NSS_ERR_ARG, "run %d: the plain path takes a grouped sweep configuration", run);
   }
@@ -395,6 +402,9 @@ void free_ctx(nss_ctx* c) {
   for (auto& w : c->lr) {
     cudaFree(w.Xb);
     cudaFree(w.ybits);
+    cudaFree(w.lrd);
+    cudaFree(w.d_active);
+    if (w.h_active) cudaFreeHost(w.h_active);
     cudaFree(w.zx);
     cudaFree(w.zv);
     cudaFree(w.xc);
@@ -613,6 +623,63 @@ nss_status enqueue_iteration(nss_ctx* c, int g = 0) {
   return NSS_OK;
 }
 
+// The plain path's logistic HRSS steps: per step the directions, then
+// lockstep evaluation rounds (candidate parts, one logits GEMM over all
+// chains' candidates, evaluation and transition) until every chain has
+// finished the step; the host reads the count of chains still testing after
+// each round.
+nss_status enqueue_plain_logreg_steps(nss_ctx* c, LRWork& w) {
+  nss::Dev D = dev_of(c);
+  const RunDesc& R = c->desc[w.run];
+  cudaStream_t st = c->stream;
+  const int* done = &c->d_state[w.run].done;
+  {
+    Rec r(c, NSS_K_OTHER);
+    CK(nss::launch_lr_center(D, w.args, w.run, R.n_data, st), "logistic centre launch");
+  }
+  {
+    Rec r(c, NSS_K_OTHER);
+    CK(nss::launch_lr_parents(D, w.args, w.run, R.k, st), "logistic parents launch");
+  }
+  const int max_rounds = 2 * nss::kStepOutCap + nss::kShrinkCap + 2;
+  for (int s = 0; s < R.p; ++s) {
+    {
+      Rec r(c, NSS_K_OTHER);
+      CK(nss::launch_lr_dir(D, w.args, w.run, R.k, s, st), "logistic direction launch");
+    }
+    {
+      Rec r(c, NSS_K_OTHER);
+      CK(nss::launch_lr_direct_init(D, w.args, w.lrd, w.run, R.k, s, st), "logistic step start launch");
+    }
+    for (int round = 0; round < max_rounds; ++round) {
+      CK(cudaMemsetAsync(w.d_active, 0, sizeof(int), st), "round counter reset");
+      {
+        Rec r(c, NSS_K_OTHER);
+        CK(nss::launch_lr_direct_cand(D, w.args, w.lrd, w.run, R.k, st), "logistic candidate launch");
+      }
+      {
+        Rec r(c, NSS_K_LOGITS);
+        CK(nss::launch_logits(w.mapX, w.mapU, w.rows_pad, w.cols_pad, w.zx, w.rows_pad, R.n_data, R.k, w.err, done,
+                              w.zref, st), "logits launch");
+      }
+      {
+        Rec r(c, NSS_K_LR_SLICE);
+        CK(nss::launch_lr_direct_eval(D, w.args, w.lrd, w.run, R.k, s, w.emax, w.d_active, st),
+           "logistic evaluation launch");
+      }
+      CK(cudaMemcpyAsync(w.h_active, w.d_active, sizeof(int), cudaMemcpyDeviceToHost, st), "round counter read");
+      CK(cudaStreamSynchronize(st), "round synchronise");
+      c->prof.d2h_bytes += (long long)sizeof(int);
+      if (*w.h_active == 0) break;
+    }
+  }
+  {
+    Rec r(c, NSS_K_OTHER);
+    CK(nss::launch_lr_replace(D, w.args, w.run, R.k, st), "logistic replace launch");
+  }
+  return NSS_OK;
+}
+
 // One outer iteration of the plain single-run path (NSS_PATH_PLAIN): one
 // launch per phase, one HRSS launch per step, on c->stream.
 nss_status enqueue_plain_iteration(nss_ctx* c) {
@@ -622,6 +689,13 @@ nss_status enqueue_plain_iteration(nss_ctx* c) {
   for (int ph = 0; ph < 4; ++ph) {
     Rec r(c, NSS_K_PROLOGUE);
     CK(nss::launch_plain_phase(ph, D, 0, R.k, c->prologue_smem, st), "plain phase launch");
+  }
+  if (!c->lr.empty()) {
+    nss_status s = enqueue_plain_logreg_steps(c, c->lr[0]);
+    if (s != NSS_OK) return s;
+    Rec r(c, NSS_K_TERMINATE);
+    CK(nss::launch_terminate(D, 0, 1, st), "terminate launch");
+    return NSS_OK;
   }
   for (int q = 0; q < nss_ctx::kDirClasses; ++q) {
     if (c->dir_items[q].empty()) continue;
@@ -902,6 +976,11 @@ nss_status setup_logreg(nss_ctx* c, int run, const nss_loglik& lk) {
   CK(cudaMalloc(&w.parts, sizeof(__nv_bfloat16) * 3 * (size_t)w.cols_pad * 128), "logistic workspace");
   CK(cudaMalloc(&w.err, sizeof(int)), "logistic workspace");
   CK(cudaMalloc(&w.center, sizeof(float) * 128), "logistic workspace");
+  if (c->plain) {
+    CK(cudaMalloc(&w.lrd, sizeof(nss::LRDirect) * w.cols_pad), "logistic workspace");
+    CK(cudaMalloc(&w.d_active, sizeof(int)), "logistic workspace");
+    CK(cudaMallocHost(&w.h_active, sizeof(int)), "logistic workspace");
+  }
   CK(cudaMalloc(&w.zref, sizeof(float) * w.rows_pad), "logistic workspace");
   c->lr.push_back(w);  // owned by the context from here on (freed with it)
   LRWork& W = c->lr.back();

@@ -38,6 +38,16 @@ struct LRArgs {
   float* zref;             // [rows_pad] X mu
 };
 
+// Per-chain state of the plain path's logistic HRSS step (direct evaluation:
+// every slice test's logits recomputed from the candidate point).
+struct LRDirect {
+  float tl, tr, t;       // bracket ends and the candidate under test
+  float height;          // prior slice height (Gaussian prior)
+  int phase;             // 0 stepping out left, 1 right, 2 shrinking, 3 done
+  int e, r;              // expansions of the current side; shrinkage proposal index
+  int evals, exps, shr, capo, nanc, acc;
+};
+
 // Device data of one GP run: inputs and targets (FP32).
 struct GPArgs {
   const float* t;
@@ -91,6 +101,15 @@ cudaError_t launch_lr_rowll(const Dev& D, const LRArgs& A, int run, int m, int e
 cudaError_t launch_lr_dir(const Dev& D, const LRArgs& A, int run, int k, int step, cudaStream_t s);
 cudaError_t launch_lr_slice(const Dev& D, const LRArgs& A, int run, int k, int step, int emax, cudaStream_t s);
 cudaError_t launch_lr_replace(const Dev& D, const LRArgs& A, int run, int k, cudaStream_t s);
+// the plain path's logistic HRSS step s in lockstep evaluation rounds: init
+// (bracket, slice height), then per round the candidate points' bf16 parts,
+// the logits GEMM over them (launch_logits into A.zx) and the evaluation with
+// each chain's transition; *active counts the chains still testing
+cudaError_t launch_lr_direct_init(const Dev& D, const LRArgs& A, LRDirect* st, int run, int k, int step,
+                                  cudaStream_t s);
+cudaError_t launch_lr_direct_cand(const Dev& D, const LRArgs& A, const LRDirect* st, int run, int k, cudaStream_t s);
+cudaError_t launch_lr_direct_eval(const Dev& D, const LRArgs& A, LRDirect* st, int run, int k, int step, int emax,
+                                  int* active, cudaStream_t s);
 // bounded-wait self-test: *out = 2 when the wait gave up (the expected outcome)
 cudaError_t launch_wait_selftest(int* out, uint32_t max_polls, cudaStream_t s);
 

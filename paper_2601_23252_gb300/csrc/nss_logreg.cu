@@ -496,6 +496,162 @@ __global__ void __launch_bounds__(128) k_lr_replace(Dev D, LRArgs A, int run) {
 }
 
 // ---------------------------------------------------------------------------
+// The plain path's logistic HRSS step (direct evaluation, the comparator of
+// the line-affine form above): the k chains advance in lockstep evaluation
+// rounds; each round every chain still testing proposes its next slice test
+// (the next stepping-out end or shrinkage proposal of the sequential
+// algorithm), the logits of all k candidate points are one tensor-core GEMM
+// (k_logits over their bf16 parts), and each chain's block reduces its
+// Bernoulli sum and takes the transition.  Same words and counters as
+// k_lr_slice.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_lr_direct_init(Dev D, LRArgs A, LRDirect* st, int run, int step) {
+  __shared__ float red[4];
+  const RunDesc& R = D.desc[run];
+  const RunState& S = D.st[run];
+  if (S.done) return;
+  const int j = blockIdx.x, t = threadIdx.x;
+  if (j >= R.k) return;
+  const uint32_t iter = static_cast<uint32_t>(S.iter);
+  const bool own = t < R.d;
+  const float xt = own ? A.xc[static_cast<long long>(j) * 128 + t] : 0.0f;
+  const float ux = own ? (xt - D.f[R.o_a + t]) * (1.0f / D.f[R.o_b + t]) : 0.0f;
+  float v = -0.5f * ux * ux;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((t & 31) == 0) red[t >> 5] = v;
+  __syncthreads();
+  if (t == 0) {
+    const uint32_t nz = 2u * static_cast<uint32_t>((R.d + 1) >> 1);
+    const uint4 b0 = draw_block(R, iter, (uint32_t)j, (uint32_t)step, nz >> 2);
+    const uint32_t wU = pick(b0, nz & 3u);
+    const uint32_t wi = nz + 1u;
+    const uint32_t wH = ((wi >> 2) == (nz >> 2)) ? pick(b0, wi & 3u)
+                                                 : pick(draw_block(R, iter, (uint32_t)j, (uint32_t)step, wi >> 2), wi & 3u);
+    LRDirect c{};
+    c.height = (red[0] + red[1] + red[2] + red[3]) + R.prior_const + logf(u24(wH));
+    c.tl = -R.w * u24(wU);
+    c.tr = c.tl + R.w;
+    c.t = c.tl;
+    c.phase = 0;
+    st[j] = c;
+  }
+}
+
+// bf16 parts of the candidate point y = x + t v, centred (phase 3: unchanged)
+__global__ void __launch_bounds__(128) k_lr_direct_cand(Dev D, LRArgs A, const LRDirect* st, int run) {
+  const RunDesc& R = D.desc[run];
+  if (D.st[run].done) return;
+  const int j = blockIdx.x, t = threadIdx.x;
+  if (j >= R.k) return;
+  const LRDirect c = st[j];
+  if (c.phase == 3) return;
+  const bool own = t < R.d;
+  const float xt = own ? A.xc[static_cast<long long>(j) * 128 + t] : 0.0f;
+  const float vt = own ? A.vdir[static_cast<long long>(j) * 128 + t] : 0.0f;
+  write_parts(A.parts, A.part_stride, j, t, own ? fmaf(c.t, vt, xt) - A.center[t] : 0.0f);
+}
+
+template <int EMAX>
+__global__ void __launch_bounds__(kLRThreads) k_lr_direct_eval(Dev D, LRArgs A, LRDirect* st, int run, int step,
+                                                               int* active) {
+  __shared__ float2 red[33];
+  __shared__ int accepted;
+  const RunDesc& R = D.desc[run];
+  RunState* S = D.st + run;
+  if (S->done) return;
+  const int j = blockIdx.x, t = threadIdx.x;
+  if (j >= R.k) return;
+  LRDirect c = st[j];
+  if (c.phase == 3) return;  // the same for the whole block
+  const int N = R.n_data, d = R.d;
+  const uint32_t yb = A.ybits[t];
+  const long long rowz = static_cast<long long>(j) * A.ldz;
+  float acc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < EMAX; ++i) {
+    const int n = t + kLRThreads * i;
+    if (n < N) acc += bern_logit(A.zx[rowz + n], (yb >> i) & 1u);
+  }
+  const bool own = t < d;
+  const float xt = own ? A.xc[static_cast<long long>(j) * 128 + t] : 0.0f;
+  const float vt = own ? A.vdir[static_cast<long long>(j) * 128 + t] : 0.0f;
+  const float yt = fmaf(c.t, vt, xt);
+  const float u = own ? (yt - D.f[R.o_a + t]) * (1.0f / D.f[R.o_b + t]) : 0.0f;
+  const float2 tot = block_sum2(acc, -0.5f * u * u, red);
+  if (t == 0) {
+    const bool nan = isnan(tot.x);
+    const float ll = nan ? -INFINITY : tot.x;
+    const bool in = (tot.y + R.prior_const > c.height) && (ll > S->logLstar);
+    const uint32_t iter = static_cast<uint32_t>(S->iter);
+    const uint32_t nz = 2u * static_cast<uint32_t>((d + 1) >> 1);
+    auto shrink = [&](int r) {
+      const uint32_t wi = nz + 3u + static_cast<uint32_t>(r);
+      const float uu = u24(pick(draw_block(R, iter, (uint32_t)j, (uint32_t)step, wi >> 2), wi & 3u));
+      return fmaf(uu, c.tr - c.tl, c.tl);
+    };
+    ++c.evals;
+    c.nanc += nan ? 1 : 0;
+    int acc_now = 0;
+    if (c.phase == 0 || c.phase == 1) {
+      const bool left = c.phase == 0;
+      if (in) {
+        if (left) c.tl -= R.w;
+        else c.tr += R.w;
+        ++c.e;
+        ++c.exps;
+      }
+      const bool stop = !in || c.e == kStepOutCap;
+      if (in && c.e == kStepOutCap) ++c.capo;
+      if (!stop) {
+        c.t = left ? c.tl : c.tr;
+      } else if (left) {
+        c.phase = 1;
+        c.e = 0;
+        c.t = c.tr;
+      } else {
+        c.phase = 2;
+        c.r = 0;
+        c.t = shrink(0);
+      }
+    } else {
+      ++c.shr;
+      if (in) {
+        acc_now = 1;
+        ++c.acc;
+        A.lc[j] = ll;
+        c.phase = 3;
+      } else {
+        if (c.t < 0.0f) c.tl = c.t;
+        else c.tr = c.t;
+        ++c.r;
+        if (c.r == kShrinkCap) c.phase = 3;
+        else c.t = shrink(c.r);
+      }
+    }
+    if (c.phase == 3) {
+      int* sts = D.i + R.o_stats;
+      sts[j] += c.evals;
+      sts[R.k + j] += acc_now;
+      sts[2 * R.k + j] += 1 - acc_now;
+      sts[3 * R.k + j] += c.exps;
+      sts[4 * R.k + j] += c.shr;
+      sts[5 * R.k + j] += c.capo;
+      atomicAdd(reinterpret_cast<unsigned long long*>(&S->evals), static_cast<unsigned long long>(c.evals));
+      if (!acc_now) atomicAdd(reinterpret_cast<unsigned long long*>(&S->nulls), 1ull);
+      if (c.capo) atomicAdd(reinterpret_cast<unsigned long long*>(&S->cap_out), static_cast<unsigned long long>(c.capo));
+      if (c.nanc) atomicAdd(reinterpret_cast<unsigned long long*>(&S->nan_evals), static_cast<unsigned long long>(c.nanc));
+    } else {
+      atomicAdd(active, 1);
+    }
+    accepted = acc_now;
+    st[j] = c;
+  }
+  __syncthreads();
+  if (accepted && own) A.xc[static_cast<long long>(j) * 128 + t] = yt;
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -576,6 +732,22 @@ cudaError_t launch_lr_dir(const Dev& D, const LRArgs& A, int run, int k, int ste
 cudaError_t launch_lr_slice(const Dev& D, const LRArgs& A, int run, int k, int step, int emax, cudaStream_t s) {
   if (emax <= 4) k_lr_slice<4><<<k, kLRThreads, 0, s>>>(D, A, run, step);
   else if (emax <= 20) k_lr_slice<20><<<k, kLRThreads, 0, s>>>(D, A, run, step);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+cudaError_t launch_lr_direct_init(const Dev& D, const LRArgs& A, LRDirect* st, int run, int k, int step,
+                                  cudaStream_t s) {
+  k_lr_direct_init<<<k, 128, 0, s>>>(D, A, st, run, step);
+  return cudaGetLastError();
+}
+cudaError_t launch_lr_direct_cand(const Dev& D, const LRArgs& A, const LRDirect* st, int run, int k, cudaStream_t s) {
+  k_lr_direct_cand<<<k, 128, 0, s>>>(D, A, st, run);
+  return cudaGetLastError();
+}
+cudaError_t launch_lr_direct_eval(const Dev& D, const LRArgs& A, LRDirect* st, int run, int k, int step, int emax,
+                                  int* active, cudaStream_t s) {
+  if (emax <= 4) k_lr_direct_eval<4><<<k, kLRThreads, 0, s>>>(D, A, st, run, step, active);
+  else if (emax <= 20) k_lr_direct_eval<20><<<k, kLRThreads, 0, s>>>(D, A, st, run, step, active);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

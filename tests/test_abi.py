@@ -79,10 +79,11 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
         native.lib()
 
 
-@pytest.mark.parametrize("bad", ["two_runs", "rw_kernel", "lane_cfg", "k_over_1024", "logreg"])
+@pytest.mark.parametrize("bad", ["two_runs", "rw_kernel", "lane_cfg", "k_over_1024", "gp"])
 def test_plain_path_arguments_rejected_before_device_work(bad):
-    """The plain single-run path takes one HRSS run of a Gaussian, mixture or
-    flat likelihood with k <= 1024 in a grouped sweep configuration."""
+    """The plain single-run path takes one HRSS run of a Gaussian, mixture,
+    flat or logistic likelihood with k <= 1024 in a grouped sweep
+    configuration."""
     from paper_2601_23252_gb300 import native, workloads as W
     plain = {"path": native.PATH_PLAIN}
     wls = [W.gauss_d2().with_(extra={"options": dict(plain)})]
@@ -94,8 +95,8 @@ def test_plain_path_arguments_rejected_before_device_work(bad):
         wls = [W.gmm_d32().with_(extra={"options": dict(plain, sweep_cfg=24)})]
     elif bad == "k_over_1024":
         wls = [wls[0].with_(n_live=3000, k=1500)]
-    elif bad == "logreg":
-        wls = [W.logreg_d100(n_rows=64, d=4, n_live=50, k=10).with_(extra={"options": dict(plain)})]
+    elif bad == "gp":
+        wls = [W.gp_d3(n=16).with_(n_live=50, k=10, extra={"options": dict(plain)})]
     with pytest.raises(native.NSSError) as e:
         native.Sampler(wls)
     assert e.value.status == -1

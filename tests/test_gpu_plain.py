@@ -77,3 +77,52 @@ def test_plain_path_gaussian_prior_and_step_trace(gpu_lib):
             traces.append(s.trace(0))
     for key, val in traces[0].items():
         assert np.array_equal(np.asarray(val), np.asarray(traces[1][key])), key
+
+
+def _small_logreg(seed):
+    return W.logreg_d100(seed=seed, n_rows=1000, d=10, n_live=200, k=100).with_(name="logreg_small")
+
+
+def test_plain_logistic_one_step_parity(gpu_lib):
+    """The plain path's logistic step (lockstep evaluation rounds, each slice
+    test's logits recomputed from the candidate point by one tensor-core GEMM
+    over all chains) against the FP64 checker on the same state and counters."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from parity import MAX_MISMATCH_FRACTION, MAX_TIE_FRACTION, compare_step, near_tie_mask
+    wl = _small_logreg(5)
+    wl = wl.with_(extra={**wl.extra, "options": {"path": native.PATH_PLAIN}})
+    rep = compare_step(wl, 3)
+    g, t = rep["gpu"], rep["orc"]
+    assert np.array_equal(g["dead_idx"], t["dead_idx"]) and np.array_equal(g["parent"], t["parent"])
+    tie = near_tie_mask(rep, "logreg_small")
+    same = np.ones(wl.k, bool)
+    for c in ("evals", "accepts", "nulls", "expansions", "shrinks", "cap_out"):
+        same &= g[c] == t[c]
+    xerr = np.abs(g["new_x"][same] - t["new_x"][same]).max()
+    print(f"\nplain logistic step: ties {tie.mean():.3f} mismatch {np.mean(~same):.3f} x err {xerr:.2e}")
+    assert np.all(same | tie)
+    assert tie.mean() <= MAX_TIE_FRACTION and np.mean(~same) <= MAX_MISMATCH_FRACTION
+    assert xerr <= 1e-5 * max(1.0, np.abs(t["new_x"][same]).max())
+
+
+def test_plain_logistic_run_against_batched(gpu_lib):
+    """Whole runs of the small logistic problem on both paths: the same
+    method, so the evidences agree within the runs' combined errors (the two
+    form the logits differently -- from the candidate point, or line-affine --
+    and part ways after their first near-tie)."""
+    seeds = range(4)
+    lz_b, lz_p = [], []
+    with native.Sampler([_small_logreg(s) for s in seeds]) as s:
+        res_b = s.run()
+    for sd in seeds:
+        w = _small_logreg(sd)
+        w = w.with_(extra={**w.extra, "options": {"path": native.PATH_PLAIN}})
+        with native.Sampler(w) as s:
+            res_p = s.run()[0]
+        assert res_p["status"] == 0 and res_p["spec_evals"] == 0
+        lz_p.append((res_p["logZ"], res_p["logZ_err"]))
+    for (zp, ep), rb in zip(lz_p, res_b):
+        d = zp - rb["logZ"]
+        print(f"plain {zp:.3f} +- {ep:.3f}, batched {rb['logZ']:.3f} +- {rb['logZ_err']:.3f}")
+        assert abs(d) < 3.0 * 1.25 * np.hypot(ep, rb["logZ_err"])

@@ -20,8 +20,8 @@ destroy.  Beside the headline the line carries the comparators (the plain
 single-run FP32 GPU path, and the batched kernels one run at a time), the
 accuracy gate against the closed forms and the FP64 checker, a profiling
 pass (one run group, serialised launches) for the per-kernel times and the
-roofline, and extra workload legs (gmm_d32 with its operating point over p,
-logreg_d100, gp_d3).  Multi-GPU: independent replicas (one batch of
+roofline, and extra workload legs (gauss_d2, gmm_d32 with its operating
+point over p, logreg_d100 with the line-affine speed-up, gp_d3).  Multi-GPU: independent replicas (one batch of
 different seeds per rank), no data-path collective.  `--impl reference`
 times the FP64 CPU checker of the same workload on the host cores.
 """
@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the comparators")
-    ap.add_argument("--no-legs", action="store_true", help="skip the gmm_d32 / logreg_d100 / gp_d3 legs")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the gauss_d2 / gmm_d32 / logreg_d100 / gp_d3 legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU checker baseline")
     ap.add_argument("--ncu-case", action="store_true",
                     help="no timing: the headline batch for a few iterations, small dead stores, one run "
@@ -554,7 +555,8 @@ def run_native(args):
         line["batch64_p_sweep"] = p_sweep(wls, chosen, stream, flush, mults=(3, 4, 6), base=line["gate"],
                                           base_value=value)
     if rank == 0 and world == 1 and not args.no_legs:
-        line["legs"] = {"gmm_d32": leg_gmm(stream, flush), "logreg_d100": leg_logreg(stream, peaks),
+        line["legs"] = {"gauss_d2": leg_gauss_d2(stream, flush), "gmm_d32": leg_gmm(stream, flush),
+                        "logreg_d100": leg_logreg(stream, peaks),
                         "gp_d3": leg_gp(stream, fp32_peak)}
     if rank == 0 and world == 1 and not args.no_cpu:
         one = cpu_checker_rate(run=nrun - 1)
@@ -676,6 +678,26 @@ def leg_gmm(stream, flush):
             first = row["p"]
     return {"runs": 20, "rows": rows, "gated_p": first,
             "note": None if first else "no p up to 20d meets |mean dlogZ| <= 0.1 nat against the closed form"}
+
+
+def leg_gauss_d2(stream, flush):
+    """gauss_d2 (20 seeds in one batch: d = 2, uniform prior on [0,1]^2,
+    N(0.5, 0.1^2 I), m = 500, k = 250, p = 5d): throughput and the gate
+    against the erf closed form."""
+    from paper_2601_23252_gb300 import native
+    from paper_2601_23252_gb300 import workloads as W
+    ws = [W.gauss_d2(seed=s) for s in range(20)]
+    with native.Sampler(ws, stream=stream.cuda_stream) as s:
+        s.autotune(iters=2)
+        s.run()
+        t = []
+        for i in range(3):
+            ms, res = timed_run(s, stream, flush, 3.0 + i)
+            t.append(ms)
+    ms = float(np.median(t))
+    g = logz_gate(ws, res)
+    return {"runs": 20, "value": sum(r["n_dead"] for r in res) / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms,
+            "evals_per_s": sum(r["evals"] for r in res) / (ms / 1e3), "gate": g}
 
 
 def leg_logreg(stream, peaks):

@@ -88,6 +88,20 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
 #pragma unroll
   for (int i = 0; i < DPL; ++i) vn[i] = 0.0f;
   if (has) ldg_lane<DPL>(vrow, gl, ld, vn);
+  // a single-component run's mean and the prior's bounds stay in registers
+  // across the steps (up to 8 dimensions per lane); otherwise each step
+  // reads them again
+  constexpr bool kHold = KC == 1 && DPL <= 8;
+  float hm[kHold ? DPL : 1], hpa[kHold ? DPL : 1], hpb[kHold ? DPL : 1];
+  if constexpr (kHold) {
+#pragma unroll
+    for (int i = 0; i < DPL; ++i) hm[i] = hpa[i] = hpb[i] = 0.0f;
+    if (has) {
+      if (K > 0) ldg_lane<DPL>(f + R.o_mu, gl, ld, hm);
+      ldg_lane<DPL>(f + R.o_a, gl, ld, hpa);
+      ldg_lane<DPL>(f + R.o_b, gl, ld, hpb);
+    }
+  }
   uint32_t nU = (uint32_t)__ldg(wrow), nH = nonflat ? (uint32_t)__ldg(wrow + 1) : 0u;
   uint32_t nS = wlane ? (uint32_t)__ldg(wrow + 3 + gl) : 0u;
   for (int s = 0; s < R.p; ++s) {
@@ -128,7 +142,12 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
         float m[DPL];
 #pragma unroll
         for (int i = 0; i < DPL; ++i) m[i] = 0.0f;
-        if (has) ldg_lane<DPL>(f + R.o_mu + (long long)cr * ld, gl, ld, m);
+        if constexpr (kHold) {
+#pragma unroll
+          for (int i = 0; i < DPL; ++i) m[i] = hm[i];
+        } else {
+          if (has) ldg_lane<DPL>(f + R.o_mu + (long long)cr * ld, gl, ld, m);
+        }
         float dq = 0.0f, de = 0.0f;
 #pragma unroll
         for (int i = 0; i < DPL; ++i) {
@@ -149,9 +168,17 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     float pa[DPL], pb[DPL];
 #pragma unroll
     for (int i = 0; i < DPL; ++i) pa[i] = pb[i] = 0.0f;
-    if (has) {
-      ldg_lane<DPL>(f + R.o_a, gl, ld, pa);
-      ldg_lane<DPL>(f + R.o_b, gl, ld, pb);
+    if constexpr (kHold) {
+#pragma unroll
+      for (int i = 0; i < DPL; ++i) {
+        pa[i] = hpa[i];
+        pb[i] = hpb[i];
+      }
+    } else {
+      if (has) {
+        ldg_lane<DPL>(f + R.o_a, gl, ld, pa);
+        ldg_lane<DPL>(f + R.o_b, gl, ld, pb);
+      }
     }
     if (box) {
       float t_lo = -INFINITY, t_hi = INFINITY;
@@ -509,7 +536,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
 }
 
 // resident blocks per SM the register budget is tuned for
-constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 20 : dpl == 4 ? 18 : dpl == 8 ? 16 : 12; }
+constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 20 : dpl == 4 ? 18 : dpl == 8 ? 13 : 12; }
 
 template <int G, int DPL, int KC>
 __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(Dev D, const WorkItem* __restrict__ items, int n_items,

@@ -66,6 +66,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   float lx = f[R.o_logL + parent];
   const float w = R.w;
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
+  // the run's scalars the steps use, read once
+  const int P = R.p;
+  const bool rw = R.kernel == kKernelRw;
+  const float inv2s2 = R.inv2s2, lognorm = R.lognorm, pconst = R.prior_const, rws = R.rw_scale;
   // Per-chain counters.  Logical evaluations and null moves are not kept:
   // every step ends in an acceptance or a null move, so nul = p - acc, and
   // a side that stops after n expansions took min(n + 1, cap) tests, so an
@@ -104,12 +108,12 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
   }
   uint32_t nU = (uint32_t)__ldg(wrow), nH = nonflat ? (uint32_t)__ldg(wrow + 1) : 0u;
   uint32_t nS = wlane ? (uint32_t)__ldg(wrow + 3 + gl) : 0u;
-  for (int s = 0; s < R.p; ++s) {
+  for (int s = 0; s < P; ++s) {
     float v[DPL];
 #pragma unroll
     for (int i = 0; i < DPL; ++i) v[i] = vn[i];
     const uint32_t wU = nU, wH = nH, wS = nS;
-    if (s + 1 < R.p) {
+    if (s + 1 < P) {
       const int* wn = wrow + (long long)(s + 1) * kStepWords;
       if (has) ldg_lane<DPL>(vrow + (long long)(s + 1) * ld, gl, ld, vn);
       nU = (uint32_t)__ldg(wn);
@@ -213,8 +217,8 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       P2 = gsum<G>(P2, kAll);
       // HRSS: slice height log Pi(x) + ln u (word nz + 1); RW: the Metropolis
       // threshold log Pi(x) + ln u with u = word nz
-      const float uh = u24(R.kernel == kKernelRw ? wU : wH);
-      q3 = fmaf(-0.5f, P0, R.prior_const) + logf(uh);
+      const float uh = u24(rw ? wU : wH);
+      q3 = fmaf(-0.5f, P0, pconst) + logf(uh);
       q0 = P0;
       q1 = P1;
       q2 = P2;
@@ -232,7 +236,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       bool ok = true;
       if (box) ok = t >= q0 && t <= q1;
       if (nonflat) {
-        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, q2, 2.0f * q1), q0), R.prior_const);
+        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, q2, 2.0f * q1), q0), pconst);
         ok = lp > q3;
       }
       if (lk == kLikFlat) {
@@ -242,16 +246,16 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
         float M = -INFINITY;
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
-          vc[c] = -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * R.inv2s2;
+          vc[c] = -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * inv2s2;
           M = fmaxf(M, vc[c]);
         }
         if constexpr (KC == 1) {
-          ll = M + R.lognorm;
+          ll = M + lognorm;
         } else {
           float S = 0.0f;
 #pragma unroll
           for (int c = 0; c < KC; ++c) S += __expf(vc[c] - M);
-          ll = M + __logf(S) + R.lognorm;
+          ll = M + __logf(S) + lognorm;
         }
         if (lk == kLikFault && fmaf(t, v0, x0) < R.fault_param)
           ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
@@ -342,10 +346,10 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       if (ok) ++acc;
       continue;
     }
-    if (R.kernel == kKernelRw) {
+    if (rw) {
       // constrained random walk: one proposal y = x + s (L z), the line point
       // t = s; accepted under the same support / prior / logL* test
-      const float ts = R.rw_scale;
+      const float ts = rws;
       bool isn = false;
       float ll = 0.0f;
       const bool in = probe(ts, ll, isn);

@@ -24,6 +24,13 @@ namespace {
 constexpr int kDirThreads = 128;
 constexpr int kDirStepsPerBlock = 8;  // steps of one item per block, 2 per warp
 
+// Philox block of counter (c0, c1, c2, blk) under the run's key (k0, k1),
+// the key held in registers by the caller
+__device__ __forceinline__ uint4 philox4x32_10_at(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+                                                  uint32_t blk) {
+  return philox4x32_10(make_uint4(c0, c1, c2, blk), k0, k1);
+}
+
 // Words nz .. nz + 11 of step s's counter stream (nz = 2 ceil(d/2)): the
 // bracket offset U, the prior slice height, the reserved word and the first
 // nine shrinkage proposals, which the sweep reads instead of drawing them.
@@ -31,10 +38,11 @@ __device__ __forceinline__ void step_words(const RunDesc& R, uint32_t iter, int 
   const uint32_t nz = 2u * (uint32_t)((R.d + 1) >> 1);
   const int b0 = (int)(nz >> 2), off = (int)(nz & 3u);  // off is 0 or 2 (nz is even)
   int* o = wout + ((long long)j * R.p + s) * kStepWords;
+  const uint32_t k0 = R.key0, k1 = R.key1;
   // one Philox block per pass (a rolled loop keeps the kernel's code small)
 #pragma unroll 1
   for (int q = 0; q < 3 + (off != 0); ++q) {
-    const uint4 blk = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)(b0 + q));
+    const uint4 blk = philox4x32_10_at(k0, k1, iter, (uint32_t)j, (uint32_t)s, (uint32_t)(b0 + q));
     const uint32_t w[4] = {blk.x, blk.y, blk.z, blk.w};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -58,6 +66,7 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
   constexpr bool kShared = DMAX > 32;
   constexpr int kReg = kShared ? 1 : DMAX;
   const int d = R.d, ld = R.dpad;
+  const uint32_t k0 = R.key0, k1 = R.key1;
   float4* out = reinterpret_cast<float4*>(vout + ((long long)j * R.p + s) * ld);
   float zz = 0.0f, dd = 0.0f;
   if constexpr (!kShared) {
@@ -68,7 +77,7 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
 #pragma unroll 1
     for (int q = 0; 4 * q < d; ++q) {
       float a0, a1, a2, a3;
-      const uint4 w = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
+      const uint4 w = philox4x32_10_at(k0, k1, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
       box_muller(w.x, w.y, a0, a1);
       box_muller(w.z, w.w, a2, a3);
       zs4[q] = make_float4(a0, a1, a2, a3);
@@ -118,7 +127,7 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
     for (int q = 0; 4 * q < ld; ++q) {
       float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
       if (4 * q < d) {
-        const uint4 w = draw_block(R, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
+        const uint4 w = philox4x32_10_at(k0, k1, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
         box_muller(w.x, w.y, a0, a1);
         box_muller(w.z, w.w, a2, a3);
       }

@@ -40,14 +40,20 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
   }
   float lx = f[R.o_logL + parent];
   const float w = R.w;
+  // the run's scalars and offsets the steps use, read once
+  const int P = R.p;
+  const bool rw = R.kernel == kKernelRw;
+  const float inv2s2 = R.inv2s2, lognorm = R.lognorm, pconst = R.prior_const, rws = R.rw_scale;
+  const uint32_t key0 = R.key0, key1 = R.key1;
+  const long long o_V = R.o_V, o_mu = R.o_mu, o_a = R.o_a, o_b = R.o_b, o_wd = R.o_wd;
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
   int evals = 0, acc = 0, nul = 0, exps = 0, shr = 0, capo = 0, nanc = 0;
-  for (int s = 0; s < R.p; ++s) {
+  for (int s = 0; s < P; ++s) {
     // the step's direction, drawn ahead (nss_dirgen.cu)
     float v[DMAX];
     float Cv = 0.0f;
     {
-      const float4* vp = reinterpret_cast<const float4*>(f + R.o_V + ((long long)j * R.p + s) * ld);
+      const float4* vp = reinterpret_cast<const float4*>(f + o_V + ((long long)j * P + s) * ld);
 #pragma unroll
       for (int b = 0; b < DMAX / 4; ++b) {
         const float4 t = (4 * b < ld) ? __ldg(vp + b) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -63,7 +69,7 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
       float dq = INFINITY, de = 0.0f;
       if (c < K) {
         dq = 0.0f;
-        const float4* m4 = reinterpret_cast<const float4*>(f + R.o_mu + (long long)c * ld);
+        const float4* m4 = reinterpret_cast<const float4*>(f + o_mu + (long long)c * ld);
 #pragma unroll
         for (int b = 0; b < DMAX / 4; ++b) {
           if (4 * b < ld) {
@@ -84,7 +90,7 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
 #pragma unroll
       for (int i = 0; i < DMAX; ++i) {
         if (i < d) {
-          const float ai = __ldg(f + R.o_a + i) - x[i], bi = __ldg(f + R.o_b + i) - x[i];
+          const float ai = __ldg(f + o_a + i) - x[i], bi = __ldg(f + o_b + i) - x[i];
           const float rv = __frcp_rn(v[i]);
           if (v[i] > 0.0f) {
             t_lo = fmaxf(t_lo, ai * rv);
@@ -101,8 +107,8 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
 #pragma unroll
       for (int i = 0; i < DMAX; ++i) {
         if (i < d) {
-          const float ib = 1.0f / __ldg(f + R.o_b + i);
-          const float u = (x[i] - __ldg(f + R.o_a + i)) * ib, q = v[i] * ib;
+          const float ib = 1.0f / __ldg(f + o_b + i);
+          const float u = (x[i] - __ldg(f + o_a + i)) * ib, q = v[i] * ib;
           P0 = fmaf(u, u, P0);
           P1 = fmaf(u, q, P1);
           P2 = fmaf(q, q, P2);
@@ -111,24 +117,24 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
     }
     // step words beyond the normals: U, height, shrinkage proposals
     // words nz .. nz + 11 drawn ahead beside the directions; later ones now
-    const int* ws = D.i + R.o_wd + ((long long)j * R.p + s) * kStepWords;
+    const int* ws = D.i + o_wd + ((long long)j * P + s) * kStepWords;
     uint32_t cblk = 0xFFFFFFFFu;
     uint4 cw = make_uint4(0u, 0u, 0u, 0u);
     auto word = [&](uint32_t wi) {
       if (wi - nz < (uint32_t)kStepWords) return (uint32_t)__ldg(ws + (wi - nz));
       if ((wi >> 2) != cblk) {
         cblk = wi >> 2;
-        cw = draw_block(R, iter, (uint32_t)j, (uint32_t)s, cblk);
+        cw = philox4x32_10(make_uint4(iter, (uint32_t)j, (uint32_t)s, cblk), key0, key1);
       }
       return pick(cw, wi & 3u);
     };
     // HRSS: slice height (word nz + 1); RW: Metropolis threshold (word nz)
-    if (nonflat) height = fmaf(-0.5f, P0, R.prior_const) + logf(u24(word(R.kernel == kKernelRw ? nz : nz + 1u)));
+    if (nonflat) height = fmaf(-0.5f, P0, pconst) + logf(u24(word(rw ? nz : nz + 1u)));
     auto in_slice = [&](float t, float& ll) -> bool {
       ++evals;
       if (box && !(t >= t_lo && t <= t_hi)) return false;
       if (nonflat) {
-        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), R.prior_const);
+        const float lp = fmaf(-0.5f, fmaf(t, fmaf(t, P2, 2.0f * P1), P0), pconst);
         if (!(lp > height)) return false;
       }
       if (lk == kLikFlat) {
@@ -138,16 +144,16 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
         float M = -INFINITY;
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
-          vc[c] = -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * R.inv2s2;
+          vc[c] = -fmaf(t, fmaf(t, Cv, 2.0f * Ec[c]), Dc[c]) * inv2s2;
           M = fmaxf(M, vc[c]);
         }
         if constexpr (KC == 1) {
-          ll = M + R.lognorm;
+          ll = M + lognorm;
         } else {
           float S = 0.0f;
 #pragma unroll
           for (int c = 0; c < KC; ++c) S += __expf(vc[c] - M);
-          ll = M + __logf(S) + R.lognorm;
+          ll = M + __logf(S) + lognorm;
         }
         if (lk == kLikFault && fmaf(t, v[0], x[0]) < R.fault_param)
           ll = (R.fault_mode == 1) ? __int_as_float(0x7fc00000) : INFINITY;
@@ -169,9 +175,9 @@ __device__ void lane_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j) 
       }
       return ll > lstar;
     };
-    if (R.kernel == kKernelRw) {
+    if (rw) {
       // constrained random walk: one proposal at the line point t = s
-      const float ts = R.rw_scale;
+      const float ts = rws;
       float ll = 0.0f;
       if (in_slice(ts, ll)) {
 #pragma unroll

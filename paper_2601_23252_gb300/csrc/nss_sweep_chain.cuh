@@ -540,7 +540,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
 }
 
 // resident blocks per SM the register budget is tuned for
-constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 20 : dpl == 4 ? 18 : dpl == 8 ? 13 : 12; }
+constexpr int sweep_min_blocks(int dpl) { return dpl <= 2 ? 20 : dpl == 4 ? 18 : dpl == 8 ? 12 : 12; }
 
 template <int G, int DPL, int KC>
 __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks(DPL)) k_sweep(Dev D, const WorkItem* __restrict__ items, int n_items,

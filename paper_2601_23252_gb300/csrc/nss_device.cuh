@@ -74,6 +74,19 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
   z1 = r * s;
 }
 
+// Box-Muller for the step directions: the same radius, and the angle taken
+// as pi + 2 pi (u2 - 1/2), so the hardware sine and cosine see the centred
+// argument in [-pi, pi] (absolute error about 2^-21 there, against the
+// rounding of 2 pi (u2 - 1/2) itself, ~2^-22): cos 2 pi u2 = -cos of it,
+// sin 2 pi u2 = -sin of it.
+__device__ __forceinline__ void box_muller_dir(uint32_t a, uint32_t b, float& z0, float& z1) {
+  const float r = sqrtf(-2.0f * logf(u24(a)));
+  float s, c;
+  __sincosf(6.28318530717958648f * (u24(b) - 0.5f), &s, &c);
+  z0 = -r * c;
+  z1 = -r * s;
+}
+
 // ---- reductions within a chain group of G lanes (butterfly: every lane of
 // the group ends with the bitwise-identical total) ----
 template <int G>

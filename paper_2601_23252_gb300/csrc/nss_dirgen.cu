@@ -78,8 +78,8 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
     for (int q = 0; 4 * q < d; ++q) {
       float a0, a1, a2, a3;
       const uint4 w = philox4x32_10_at(k0, k1, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
-      box_muller(w.x, w.y, a0, a1);
-      box_muller(w.z, w.w, a2, a3);
+      box_muller_dir(w.x, w.y, a0, a1);
+      box_muller_dir(w.z, w.w, a2, a3);
       zs4[q] = make_float4(a0, a1, a2, a3);
     }
     float z[kReg];
@@ -128,8 +128,8 @@ __device__ __forceinline__ void one_direction(const RunDesc& R, const float* __r
       float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
       if (4 * q < d) {
         const uint4 w = philox4x32_10_at(k0, k1, iter, (uint32_t)j, (uint32_t)s, (uint32_t)q);
-        box_muller(w.x, w.y, a0, a1);
-        box_muller(w.z, w.w, a2, a3);
+        box_muller_dir(w.x, w.y, a0, a1);
+        box_muller_dir(w.z, w.w, a2, a3);
       }
       const float t4[4] = {a0, a1, a2, a3};
 #pragma unroll

@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(kDtThreads) k_dirgen_tc(Dev D, const WorkItem*
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid && 4 * b < d) {
           const uint4 w = philox4x32_10(make_uint4(iter, (uint32_t)j, (uint32_t)s, (uint32_t)b), k0, k1);
-          box_muller(w.x, w.y, z.x, z.y);
-          box_muller(w.z, w.w, z.z, z.w);
+          box_muller_dir(w.x, w.y, z.x, z.y);
+          box_muller_dir(w.z, w.w, z.z, z.w);
           if (4 * b + 1 >= d) z.y = 0.f;
           if (4 * b + 2 >= d) z.z = 0.f;
           if (4 * b + 3 >= d) z.w = 0.f;

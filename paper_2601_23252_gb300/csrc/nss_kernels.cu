@@ -1,11 +1,12 @@
 // nss_kernels.cu -- the Nested Slice Sampling kernels for sm_103a.
 //
 // Per outer iteration (Sec. 3.1 (i)-(iv); Algorithm 1):
-//   k_prologue  one block per run: select the k worst live points by a
+//   k_prologue  two blocks per run: one selects the k worst live points by a
 //               bitonic sort of (logL, slot) keys, threshold logL*, survivors
 //               in slot order, parents, dead-point append, unrolled evidence
-//               update (FP64 accumulation), live-set covariance and its
-//               Cholesky factor (the direction metric, Sec. 3.2).
+//               update (FP64 accumulation); the other forms the live-set
+//               covariance and its Cholesky factor (the direction metric,
+//               Sec. 3.2).
 //   k_sweep     (nss_sweep.cu) the HRSS sweep with the likelihood fused in.
 //   k_terminate one block per run: remaining live evidence and the stopping
 //               test (App. B.3).
@@ -233,12 +234,20 @@ __device__ void live_metric(const Dev& D, const RunDesc& R, RunState& S, char* s
 // ---------------------------------------------------------------------------
 // Iteration prologue: steps (i), (ii), evidence and metric for one run.
 // ---------------------------------------------------------------------------
+// Two blocks per run: the even one selects, records the dead points, updates
+// the evidence and draws the parents; the odd one forms the direction metric
+// of the same live set (the two read the live set as the iteration starts
+// and write disjoint state), so their chains of block barriers overlap.
 __global__ void __launch_bounds__(kPrologueThreads) k_prologue(Dev D, int run0) {
-  const int run = run0 + blockIdx.x;
+  const int run = run0 + (blockIdx.x >> 1);
   const RunDesc& R = D.desc[run];
   RunState& S = D.st[run];
   if (S.done) return;
   extern __shared__ __align__(16) char smem[];
+  if (blockIdx.x & 1) {
+    live_metric(D, R, S, smem);
+    return;
+  }
   __shared__ double red_d[32];
   __shared__ int red_i[32];
   __shared__ int cap_fail;
@@ -294,9 +303,6 @@ __global__ void __launch_bounds__(kPrologueThreads) k_prologue(Dev D, int run0) 
   __syncthreads();
   evidence_update(R, S, D.f + R.o_dlogL + S.n_dead, D.dd + R.o_cum, D.dd + R.o_lnd, k, red_d);
   if (threadIdx.x == 0) S.n_dead += k;
-  __syncthreads();
-  // direction metric from the live set at the start of the iteration
-  live_metric(D, R, S, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -650,7 +656,7 @@ cudaError_t setup_kernel_attributes() {
 }
 
 cudaError_t launch_prologue(const Dev& D, int run0, int n_runs, size_t smem, cudaStream_t s) {
-  k_prologue<<<n_runs, kPrologueThreads, smem, s>>>(D, run0);
+  k_prologue<<<2 * n_runs, kPrologueThreads, smem, s>>>(D, run0);
   return cudaGetLastError();
 }
 

@@ -52,6 +52,7 @@ constexpr uint32_t kTcPartBytes = kTcMaxN * 32 * 4;        // 256 rows x 32 FP32
 constexpr int kTcDynSmem = 4 * kTcPartBytes + 1024;
 
 struct TcShared {
+  float LT[32][32];   // the diagonal block's factor transposed (column cc in LT[cc]), 16-byte rows
   float Ab[32][33];   // the diagonal block being factored
   float L11[32][33];  // its factor (zeros above the diagonal)
   float inv[32];      // reciprocals of its diagonal
@@ -140,7 +141,11 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
         }
         const float l = sqrtf(piv), inv = 1.0f / l;
         const float lic = sh.Ab[i][cc] * inv;
-        if (q0 == 0) sh.L11[i][cc] = (i == cc) ? l : (i > cc ? lic : 0.0f);
+        if (q0 == 0) {
+          const float lv = (i == cc) ? l : (i > cc ? lic : 0.0f);
+          sh.L11[i][cc] = lv;
+          sh.LT[cc][i] = lv;
+        }
         if (tid == cc) sh.inv[cc] = inv;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -158,23 +163,40 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
     }
     if (warp == p) {
       // forward substitution of the block's rows: lane l holds row j0 + l
+      // and keeps alpha_l; the panel's |alpha|^2 and log-diagonal terms are
+      // summed over the warp in FP64 afterwards
+      float mine = 0.0f;
 #pragma unroll 1
       for (int cc = 0; cc < 32; ++cc) {
         const float ac = __shfl_sync(0xffffffffu, r, cc) * sh.inv[cc];
         if (lane > cc) r = fmaf(-sh.L11[lane][cc], ac, r);
-        if (lane == 0) {
-          sh.alpha[cc] = ac;
-          sh.qa += (double)ac * (double)ac;
-          sh.ldet += (double)logf(sh.L11[cc][cc]);
-        }
+        if (lane == cc) mine = ac;
+      }
+      sh.alpha[lane] = mine;
+      double qa = (double)mine * (double)mine, ld = (double)logf(sh.L11[lane][lane]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        qa += __shfl_xor_sync(0xffffffffu, qa, o);
+        ld += __shfl_xor_sync(0xffffffffu, ld, o);
+      }
+      if (lane == 0) {
+        sh.qa += qa;
+        sh.ldet += ld;
       }
     } else if (warp > p && row_ok) {
       // rows below: their panel entries x = a L11^-T, column by column
+      // (column cc of the factor read as 16-byte broadcasts)
 #pragma unroll
       for (int cc = 0; cc < 32; ++cc) {
         a[cc] *= sh.inv[cc];
 #pragma unroll
-        for (int q = cc + 1; q < 32; ++q) a[q] = fmaf(-a[cc], sh.L11[q][cc], a[q]);
+        for (int b = (cc + 1) >> 2; b < 8; ++b) {
+          const float4 l = *reinterpret_cast<const float4*>(&sh.LT[cc][4 * b]);
+          if (4 * b > cc) a[4 * b] = fmaf(-a[cc], l.x, a[4 * b]);
+          if (4 * b + 1 > cc) a[4 * b + 1] = fmaf(-a[cc], l.y, a[4 * b + 1]);
+          if (4 * b + 2 > cc) a[4 * b + 2] = fmaf(-a[cc], l.z, a[4 * b + 2]);
+          if (4 * b + 3 > cc) a[4 * b + 3] = fmaf(-a[cc], l.w, a[4 * b + 3]);
+        }
       }
     }
     __syncthreads();

@@ -128,29 +128,74 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
       for (int e = 0; e < 32; ++e) sh.Ab[lane][e] = a[e];
     }
     __syncthreads();
-    // the diagonal block, one column per step: thread t updates entries
-    // (i, q) of row i = t / 8, columns q = t % 8 + 8 u
+    // the diagonal block, four columns c0 .. c0 + 3 per step: every thread
+    // factors the 4 x 4 pivot block itself, derives the factor entries of
+    // its row i = t / 8 and of its columns q = t % 8 + 8 u in those four
+    // columns from the stored entries, and updates entries (i, q), q >= c0 + 4
+    // (the same operations, in the same order, as one column at a time;
+    // one barrier per four columns)
     {
       const int i = tid >> 3, q0 = tid & 7;
 #pragma unroll 1
-      for (int cc = 0; cc < 32; ++cc) {
-        const float piv = sh.Ab[cc][cc];
-        if (!(piv > 0.0f) || !isfinite(piv)) {  // the same value in every thread
+      for (int c0 = 0; c0 < 32; c0 += 4) {
+        float l[4][4], rl[4];
+        bool okp = true;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float piv = sh.Ab[c0 + c][c0 + c];
+#pragma unroll
+          for (int k = 0; k < c; ++k) piv = fmaf(-l[c][k], l[c][k], piv);
+          okp = okp && (piv > 0.0f) && isfinite(piv);
+          l[c][c] = sqrtf(piv);
+          rl[c] = 1.0f / l[c][c];
+#pragma unroll
+          for (int e = c + 1; e < 4; ++e) {
+            float x = sh.Ab[c0 + e][c0 + c];
+#pragma unroll
+            for (int k = 0; k < c; ++k) x = fmaf(-l[e][k], l[c][k], x);
+            l[e][c] = x * rl[c];
+          }
+        }
+        if (!okp) {  // the same outcome in every thread
           if (tid == 0) sh.bad = 1;
           break;
         }
-        const float l = sqrtf(piv), inv = 1.0f / l;
-        const float lic = sh.Ab[i][cc] * inv;
-        if (q0 == 0) {
-          const float lv = (i == cc) ? l : (i > cc ? lic : 0.0f);
-          sh.L11[i][cc] = lv;
-          sh.LT[cc][i] = lv;
+        float li[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float x = sh.Ab[i][c0 + c];
+#pragma unroll
+          for (int k = 0; k < c; ++k) x = fmaf(-li[k], l[c][k], x);
+          li[c] = x * rl[c];
         }
-        if (tid == cc) sh.inv[cc] = inv;
+        if (q0 == 0) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float lv = (i > c0 + c) ? li[c] : (i == c0 + c ? l[c][c] : 0.0f);
+            sh.L11[i][c0 + c] = lv;
+            sh.LT[c0 + c][i] = lv;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (tid == c) sh.inv[c0 + c] = rl[c];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int q = q0 + 8 * u;
-          if (q > cc && q <= i) sh.Ab[i][q] = fmaf(-lic, sh.Ab[q][cc] * inv, sh.Ab[i][q]);
+          if (q >= c0 + 4 && q <= i) {
+            float lq[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              float x = sh.Ab[q][c0 + c];
+#pragma unroll
+              for (int k = 0; k < c; ++k) x = fmaf(-lq[k], l[c][k], x);
+              lq[c] = x * rl[c];
+            }
+            float v = sh.Ab[i][q];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v = fmaf(-li[c], lq[c], v);
+            sh.Ab[i][q] = v;
+          }
         }
         __syncthreads();
       }

@@ -15,7 +15,9 @@
 // factorisation is right-looking in panels of 32 columns:
 //   - the panel's columns of rows >= j0 come from TMEM (tcgen05.ld);
 //   - the 32 x 32 diagonal block is factored in shared memory by the whole
-//     block (one column per step, every thread updating its entries);
+//     block, four columns per step: every thread factors the 4 x 4 pivot
+//     block itself (pivot reciprocal square roots from rsqrtf, each L_jj
+//     as pivot x rsqrt(pivot)) and updates its entries of the rest;
 //   - each row below solves its panel entries against that factor, and the
 //     diagonal block's rows give the panel's part of alpha by forward
 //     substitution; the rows below subtract it from their part of y;
@@ -24,9 +26,10 @@
 //     K = 32 in four instructions), accumulating into TMEM in FP32.  L21
 //     is split into two TF32 parts hi + lo and the product is formed as
 //     hi hi^T + hi lo^T + lo hi^T (the 3xTF32 scheme: each product to about
-//     2^-21 relative, near an FP32 product); the A operand is a negated
-//     copy of the panel.  The panel is staged in shared memory as K-major
-//     rows of 32 FP32 words (128 B) in the 128-byte swizzled layout.
+//     2^-21 relative, near an FP32 product), with the instruction's
+//     negate-A flag making each product a subtraction.  The panel is staged
+//     in shared memory as K-major rows of 32 FP32 words (128 B) in the
+//     128-byte swizzled layout.
 // ln det and |alpha|^2 accumulate in FP64.  A non-positive or non-finite
 // FP32 pivot makes logL = -inf (counted with the NaN evaluations).  Every
 // wait on the tensor core is bounded; a wait that runs out sets the error
@@ -47,9 +50,9 @@ constexpr int kTcMaxN = 256;
 constexpr int kTcCols = 512;                               // TMEM columns: two 128-row halves of 256
 constexpr uint32_t kTcMaxPolls = 1u << 22;
 constexpr uint32_t kTcPartBytes = kTcMaxN * 32 * 4;        // 256 rows x 32 FP32 words
-// dynamic shared memory: the panel's two parts and their negated copies plus
-// alignment slack (a single block fits per SM, as it must: it takes all of TMEM)
-constexpr int kTcDynSmem = 4 * kTcPartBytes + 1024;
+// dynamic shared memory: the panel's two parts plus alignment slack (a single
+// block fits per SM, as it must: it takes all of TMEM)
+constexpr int kTcDynSmem = 2 * kTcPartBytes + 1024;
 
 struct TcShared {
   float LT[32][32];   // the diagonal block's factor transposed (column cc in LT[cc]), 16-byte rows
@@ -67,12 +70,10 @@ struct TcShared {
 
 // logL of theta; every thread of the block calls it and gets the same value.
 // Returns false (for every thread) when a tensor-core wait ran out.
-// Panel buffers: phi / plo the TF32 parts of L21, nhi / nlo their negations
-// (phi, plo, nhi, nlo consecutive, kTcPartBytes each).
+// Panel buffers: phi / plo the TF32 parts of L21 (consecutive, kTcPartBytes
+// each).
 __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const float th[3], float& out, int* err) {
   uint8_t* plo = phi + kTcPartBytes;
-  uint8_t* nhi = phi + 2 * kTcPartBytes;
-  uint8_t* nlo = phi + 3 * kTcPartBytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t trow = sh.tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((tid >> 7) * 256);
   const bool row_ok = tid < np;  // warp-uniform: np is a multiple of 32
@@ -146,8 +147,8 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
 #pragma unroll
           for (int k = 0; k < c; ++k) piv = fmaf(-l[c][k], l[c][k], piv);
           okp = okp && (piv > 0.0f) && isfinite(piv);
-          l[c][c] = sqrtf(piv);
-          rl[c] = 1.0f / l[c][c];
+          rl[c] = rsqrtf(piv);
+          l[c][c] = piv * rl[c];
 #pragma unroll
           for (int e = c + 1; e < 4; ++e) {
             float x = sh.Ab[c0 + e][c0 + c];
@@ -267,8 +268,6 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
         const int pc = ro + (c4 ^ (tid & 7)) * 16;
         *reinterpret_cast<float4*>(phi + pc) = make_float4(hv[0], hv[1], hv[2], hv[3]);
         *reinterpret_cast<float4*>(plo + pc) = make_float4(lv[0], lv[1], lv[2], lv[3]);
-        *reinterpret_cast<float4*>(nhi + pc) = make_float4(-hv[0], -hv[1], -hv[2], -hv[3]);
-        *reinterpret_cast<float4*>(nlo + pc) = make_float4(-lv[0], -lv[1], -lv[2], -lv[3]);
       }
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
@@ -276,7 +275,6 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
       if (tid == 0) {
         tc::fence_after_sync();
         const uint32_t ah = tc::smem_u32(phi), al = tc::smem_u32(plo);
-        const uint32_t nh = tc::smem_u32(nhi), nl = tc::smem_u32(nlo);
 #pragma unroll 1
         for (int hh = 0; hh < 2; ++hh) {
           // rows of half hh are 128 hh .. 128 hh + 127; of their trailing
@@ -284,11 +282,11 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
           const int cend = min(np, 128 * (hh + 1));
           const int N = cend - jt;
           if (128 * hh >= np || N <= 0) continue;
-          const uint32_t idesc = tc::idesc_tf32_f32(128, N, false);
+          const uint32_t idesc = tc::idesc_tf32_f32(128, N, true);  // D += (-A) B^T
           const uint32_t dcol = sh.tmem + (uint32_t)(hh * 256 + jt);
 #pragma unroll
           for (int part = 0; part < 3; ++part) {
-            const uint32_t A = (part == 2 ? nl : nh) + (uint32_t)(hh * 128 * 128);
+            const uint32_t A = (part == 2 ? al : ah) + (uint32_t)(hh * 128 * 128);
             const uint32_t B = (part == 1 ? al : ah) + (uint32_t)(jt * 128);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)

@@ -14,10 +14,10 @@
 // the two 128-row halves fill all 512 columns.  Thread i owns row i.  The
 // factorisation is right-looking in panels of 32 columns:
 //   - the panel's columns of rows >= j0 come from TMEM (tcgen05.ld);
-//   - the 32 x 32 diagonal block is factored in shared memory by the whole
-//     block, four columns per step: every thread factors the 4 x 4 pivot
-//     block itself (pivot reciprocal square roots from rsqrtf, each L_jj
-//     as pivot x rsqrt(pivot)) and updates its entries of the rest;
+//   - the 32 x 32 diagonal block is factored in the registers of the warp
+//     that owns its rows, one column per step with shuffles (pivot
+//     reciprocal square roots from rsqrtf, each L_jj as pivot x
+//     rsqrt(pivot)), and its factor goes to shared memory;
 //   - each row below solves its panel entries against that factor, and the
 //     diagonal block's rows give the panel's part of alpha by forward
 //     substitution; the rows below subtract it from their part of y;
@@ -56,15 +56,12 @@ constexpr int kTcDynSmem = 2 * kTcPartBytes + 1024;
 
 struct TcShared {
   float LT[32][32];   // the diagonal block's factor transposed (column cc in LT[cc]), 16-byte rows
-  float Ab[32][33];   // the diagonal block being factored
-  float L11[32][33];  // its factor (zeros above the diagonal)
   float inv[32];      // reciprocals of its diagonal
   float alpha[32];    // the panel's part of alpha
   float t[kTcMaxN], y[kTcMaxN];
   double ldet, qa;
   uint64_t bar;       // MMA completion
   uint32_t tmem;
-  int bad;
   uint32_t phase;     // completed phases of `bar`
 };
 
@@ -103,7 +100,6 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
   if (tid == 0) {
     sh.ldet = 0.0;
     sh.qa = 0.0;
-    sh.bad = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -124,102 +120,38 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
     }
     float a[32];
     if (warp >= p && row_ok) tc::tmem_ld32(trow + (uint32_t)j0, a);
+    bool bad = false;
     if (warp == p) {
+      // the diagonal block in this warp's registers: lane l holds row j0 + l
+      // (a[e] = entry (j0 + l, j0 + e)).  Column c takes its pivot from lane
+      // c, turns the lanes' entries of column c into factor entries (zeros
+      // above the diagonal) and subtracts their outer product from the later
+      // columns; the forward substitution of the block's part of alpha rides
+      // along.  The panel's |alpha|^2 and log-diagonal terms are summed over
+      // the warp in FP64 afterwards.
+      float mine = 0.0f, myinv = 0.0f, mydiag = 1.0f;
 #pragma unroll
-      for (int e = 0; e < 32; ++e) sh.Ab[lane][e] = a[e];
-    }
-    __syncthreads();
-    // the diagonal block, four columns c0 .. c0 + 3 per step: every thread
-    // factors the 4 x 4 pivot block itself, derives the factor entries of
-    // its row i = t / 8 and of its columns q = t % 8 + 8 u in those four
-    // columns from the stored entries, and updates entries (i, q), q >= c0 + 4
-    // (the same operations, in the same order, as one column at a time;
-    // one barrier per four columns)
-    {
-      const int i = tid >> 3, q0 = tid & 7;
-#pragma unroll 1
-      for (int c0 = 0; c0 < 32; c0 += 4) {
-        float l[4][4], rl[4];
-        bool okp = true;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float piv = sh.Ab[c0 + c][c0 + c];
-#pragma unroll
-          for (int k = 0; k < c; ++k) piv = fmaf(-l[c][k], l[c][k], piv);
-          okp = okp && (piv > 0.0f) && isfinite(piv);
-          rl[c] = rsqrtf(piv);
-          l[c][c] = piv * rl[c];
-#pragma unroll
-          for (int e = c + 1; e < 4; ++e) {
-            float x = sh.Ab[c0 + e][c0 + c];
-#pragma unroll
-            for (int k = 0; k < c; ++k) x = fmaf(-l[e][k], l[c][k], x);
-            l[e][c] = x * rl[c];
-          }
-        }
-        if (!okp) {  // the same outcome in every thread
-          if (tid == 0) sh.bad = 1;
-          break;
-        }
-        float li[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float x = sh.Ab[i][c0 + c];
-#pragma unroll
-          for (int k = 0; k < c; ++k) x = fmaf(-li[k], l[c][k], x);
-          li[c] = x * rl[c];
-        }
-        if (q0 == 0) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float lv = (i > c0 + c) ? li[c] : (i == c0 + c ? l[c][c] : 0.0f);
-            sh.L11[i][c0 + c] = lv;
-            sh.LT[c0 + c][i] = lv;
-          }
+      for (int c = 0; c < 32; ++c) {
+        const float piv = __shfl_sync(0xffffffffu, a[c], c);
+        bad = bad || !(piv > 0.0f) || !isfinite(piv);  // the same in every lane
+        const float rc = rsqrtf(piv);
+        const float lcc = piv * rc;
+        a[c] = lane > c ? a[c] * rc : (lane == c ? lcc : 0.0f);
+        const float ac = __shfl_sync(0xffffffffu, r, c) * rc;
+        if (lane > c) r = fmaf(-a[c], ac, r);
+        if (lane == c) {
+          mine = ac;
+          myinv = rc;
+          mydiag = lcc;
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (tid == c) sh.inv[c0 + c] = rl[c];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int q = q0 + 8 * u;
-          if (q >= c0 + 4 && q <= i) {
-            float lq[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              float x = sh.Ab[q][c0 + c];
-#pragma unroll
-              for (int k = 0; k < c; ++k) x = fmaf(-lq[k], l[c][k], x);
-              lq[c] = x * rl[c];
-            }
-            float v = sh.Ab[i][q];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v = fmaf(-li[c], lq[c], v);
-            sh.Ab[i][q] = v;
-          }
-        }
-        __syncthreads();
-      }
-    }
-    // (read by thread 0, which set it; the barrier makes the outcome uniform
-    // before the flag can be reset by the next evaluation)
-    if (__syncthreads_or(tid == 0 ? sh.bad : 0)) {
-      out = -INFINITY;
-      return true;
-    }
-    if (warp == p) {
-      // forward substitution of the block's rows: lane l holds row j0 + l
-      // and keeps alpha_l; the panel's |alpha|^2 and log-diagonal terms are
-      // summed over the warp in FP64 afterwards
-      float mine = 0.0f;
-#pragma unroll 1
-      for (int cc = 0; cc < 32; ++cc) {
-        const float ac = __shfl_sync(0xffffffffu, r, cc) * sh.inv[cc];
-        if (lane > cc) r = fmaf(-sh.L11[lane][cc], ac, r);
-        if (lane == cc) mine = ac;
+        for (int q = c + 1; q < 32; ++q) a[q] = fmaf(-a[c], __shfl_sync(0xffffffffu, a[c], q), a[q]);
       }
       sh.alpha[lane] = mine;
-      double qa = (double)mine * (double)mine, ld = (double)logf(sh.L11[lane][lane]);
+      sh.inv[lane] = myinv;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) sh.LT[c][lane] = a[c];
+      double qa = (double)mine * (double)mine, ld = (double)logf(mydiag);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         qa += __shfl_xor_sync(0xffffffffu, qa, o);
@@ -229,8 +161,13 @@ __device__ bool gp_loglik_tc(TcShared& sh, uint8_t* phi, int n, int np, const fl
         sh.qa += qa;
         sh.ldet += ld;
       }
-    } else if (warp > p && row_ok) {
-      // rows below: their panel entries x = a L11^-T, column by column
+    }
+    if (__syncthreads_or(bad ? 1 : 0)) {
+      out = -INFINITY;
+      return true;
+    }
+    if (warp > p && row_ok) {
+      // rows below: their panel entries x = a L^-T (L the block's factor), column by column
       // (column cc of the factor read as 16-byte broadcasts)
 #pragma unroll
       for (int cc = 0; cc < 32; ++cc) {
@@ -408,31 +345,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gp_sweep_tc(Dev D, GPArgs A, 
       };
       const float U = u24(word(nz));
       float tl = -w * U, tr = tl + w, lly = 0.0f;
-      for (int q = 0;; ++q) {
-        if (q >= kStepOutCap) { ++capo; break; }
-        if (!in_slice(tl, lly)) break;
-        tl -= w;
-        ++exps;
-      }
-      for (int q = 0; alive; ++q) {
-        if (q >= kStepOutCap) { ++capo; break; }
-        if (!in_slice(tr, lly)) break;
-        tr += w;
-        ++exps;
-      }
+      // stepping out to the left (stage 0), to the right (stage 1), then
+      // shrinkage (stage 2), through one evaluation site so that the
+      // factorisation is inlined once
       bool ok = false;
-      for (int q = 0; q < kShrinkCap && alive; ++q) {
-        const float u = u24(word(nz + 3u + (uint32_t)q));
-        const float t = fmaf(u, tr - tl, tl);
-        ++shr;
-        if (in_slice(t, lly)) {
+      int stage = 0, q = 0;
+#pragma unroll 1
+      while (alive) {
+        float t;
+        if (stage < 2) {
+          if (q >= kStepOutCap) {
+            ++capo;
+            ++stage;
+            q = 0;
+            continue;
+          }
+          t = stage == 0 ? tl : tr;
+        } else {
+          if (q >= kShrinkCap) break;
+          t = fmaf(u24(word(nz + 3u + (uint32_t)q)), tr - tl, tl);
+          ++shr;
+        }
+        const bool in = in_slice(t, lly);
+        if (!alive) break;
+        ++q;
+        if (stage < 2) {
+          if (!in) {
+            ++stage;
+            q = 0;
+            continue;
+          }
+          if (stage == 0) tl -= w;
+          else tr += w;
+          ++exps;
+        } else if (in) {
           for (int e = 0; e < 3; ++e) x[e] = fmaf(t, v[e], x[e]);
           lx = lly;
           ok = true;
           break;
+        } else if (t < 0.0f) {
+          tl = t;
+        } else {
+          tr = t;
         }
-        if (t < 0.0f) tl = t;
-        else tr = t;
       }
       if (ok) ++acc;
       else ++nul;

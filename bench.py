@@ -44,6 +44,23 @@ sys.path.insert(0, ROOT)
 METRIC = "NS dead points/s and logL evals/s vs plain path at |ΔlogZ|≤0.1 nat, % roofline"
 UNIT = "dead points/s"
 WORKLOAD = "batch64"
+# The headline batch runs p = 4d slice steps per chain: the smallest p/d of
+# {3, 4, 6} whose mean log Z over 256 runs (the 64 problems x 4 seeds) meets
+# |dlogZ| <= 0.1 nat against the closed forms.  At the configuration's 3d the
+# method itself misses it (the FP64 checker's own 64 runs sit +0.128 nat
+# above the closed forms); 3d stays in the p sweep beside it.
+HEADLINE_P_PER_D = 4
+
+
+def headline_batch(seed):
+    """The 64 runs of the headline batch at p = HEADLINE_P_PER_D * d."""
+    from paper_2601_23252_gb300 import workloads as W
+    return [w.with_(p=HEADLINE_P_PER_D * w.d) for w in W.batch64(seed=seed)]
+
+
+def checker_file(c):
+    """The FP64 checker's runs of batch64 seed 0 at p = c d."""
+    return "oracle_batch64_logz.txt" if c == 3 else f"oracle_batch64_p{c}d_logz.txt"
 
 
 def parse():
@@ -211,8 +228,7 @@ def cpu_checker_rate(budget_s=12.0, run=0, seed=0):
     from the start, for about budget_s seconds of iterations: dead points per
     second on one core."""
     import oracle as O
-    from paper_2601_23252_gb300 import workloads as W
-    wl = W.batch64(seed=seed)[run]
+    wl = headline_batch(seed)[run]
     pb = O.Problem((wl.prior, wl.a, wl.b), wl.lik, **wl.oracle_kwargs())
     op = O.make_opts(wl.n_live, wl.k, wl.p, seed=wl.seed, run_id=wl.run_id)
     t0 = time.perf_counter()
@@ -296,7 +312,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * budget,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "runs": 64, "d": "U{4..64}",
-                                            "n_live": 500, "k": 250, "p": "3d",
+                                            "n_live": 500, "k": 250, "p": f"{HEADLINE_P_PER_D}d",
                                             "sample_per_step": f"{budget:.0f} s of checker iterations on every "
                                                                "host core, one run of the batch per core"},
             "evals_per_s": float(np.mean(evr)),
@@ -417,7 +433,7 @@ def run_native(args):
             torch.distributed.barrier()
 
     seed = rank  # one batch of 64 runs per rank
-    wls = W.batch64(seed=seed)
+    wls = headline_batch(seed)
     nrun = len(wls)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
@@ -455,12 +471,16 @@ def run_native(args):
     value = dead_all / (total_ms_all / 1e3)
     sampler.close()
 
-    checker = read_checker("oracle_batch64_logz.txt", 3, 4) if seed == 0 else {}
+    checker = read_checker(checker_file(HEADLINE_P_PER_D), 3, 4) if seed == 0 else {}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "runs_per_gpu": nrun, "d": "U{4..64}", "sigma": "logU[0.01,0.1]",
-                       "mu": 0.5, "n_live": 500, "k": 250, "p": "3d",
+                       "mu": 0.5, "n_live": 500, "k": 250, "p": f"{HEADLINE_P_PER_D}d",
+                       "p_configured": "3d",
+                       "p_why": "the smallest p/d of {3, 4, 6} meeting |mean dlogZ| <= 0.1 nat over 256 runs; "
+                                "at 3d the FP64 checker itself sits +0.128 nat above the closed forms "
+                                "(batch64_p_sweep has the 3d row)",
                        "dead_points_per_batch": dead // max(1, args.steps),
                        "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (512 MB write)",
                        "profiling": "off in the timed steps",
@@ -553,7 +573,7 @@ def run_native(args):
         line.update(comparators(wls, chosen, res, stream, value))
     if rank == 0 and world == 1:
         line["batch64_p_sweep"] = p_sweep(wls, chosen, stream, flush, mults=(3, 4, 6), base=line["gate"],
-                                          base_value=value)
+                                          base_value=value, base_c=HEADLINE_P_PER_D)
     if rank == 0 and world == 1 and not args.no_legs:
         line["legs"] = {"gauss_d2": leg_gauss_d2(stream, flush), "gmm_d32": leg_gmm(stream, flush),
                         "logreg_d100": leg_logreg(stream, peaks),
@@ -623,29 +643,34 @@ def comparators(wls, chosen, res, stream, value):
     return out
 
 
-def p_sweep(wls, chosen, stream, flush, mults, base, base_value):
+def p_sweep(wls, chosen, stream, flush, mults, base, base_value, base_c):
     """The headline batch with p = c*d for the multipliers c: dead points/s
-    and the accuracy gate at each, and the smallest c whose gate passes."""
+    and the accuracy gate at each, and the smallest c whose gate passes
+    (c = base_c is the headline itself)."""
     from paper_2601_23252_gb300 import native
     rows = []
     for c in mults:
-        if c == 3:
-            rows.append({"p_per_d": 3, "value": base_value, "mean_dlogZ_vs_closed_form":
+        if c == base_c:
+            rows.append({"p_per_d": c, "value": base_value, "mean_dlogZ_vs_closed_form":
                          base["mean_dlogZ_vs_closed_form"], "se": base["se_vs_closed_form"],
-                         "closed_form_pass": bool(base["closed_form_within_3err"] and base["mean_within_0p1_nat"])})
+                         "closed_form_pass": bool(base["closed_form_within_3err"] and base["mean_within_0p1_nat"]),
+                         "pass": base["pass"], "headline": True})
             continue
         ws = [with_opts(w.with_(p=c * w.d), sweep_cfg=chosen[r]["id"]) for r, w in enumerate(wls)]
         with native.Sampler(ws, stream=stream.cuda_stream) as s:
             s.run()
             ms, res = timed_run(s, stream, flush, 1.0)
-        g = logz_gate(ws, res, more=repeats(wls, chosen, stream, seeds=(101, 102, 103), p_per_d=c))
+        g = logz_gate(ws, res, read_checker(checker_file(c), 3, 4),
+                      more=repeats(wls, chosen, stream, seeds=(101, 102, 103), p_per_d=c))
         rows.append({"p_per_d": c, "value": sum(r["n_dead"] for r in res) / (ms / 1e3),
                      "mean_dlogZ_vs_closed_form": g["mean_dlogZ_vs_closed_form"], "se": g["se_vs_closed_form"],
-                     "closed_form_pass": g["pass"]})
+                     "closed_form_pass": bool(g["closed_form_within_3err"] and g["mean_within_0p1_nat"]),
+                     "pass": g["pass"], "mean_dlogZ_vs_checker": g.get("mean_dlogZ_vs_checker"),
+                     "checker_mean_dlogZ_vs_closed_form": g.get("checker_mean_dlogZ_vs_closed_form")})
     ok = [r for r in rows if r["closed_form_pass"]]
     return {"rows": rows, "gated_operating_point": ok[0] if ok else None,
-            "note": "closed-form gate over 4 seeds of the 64 problems (256 runs; the checker's runs exist "
-                    "for p = 3d, seed 0); one timed batch per p"}
+            "note": "closed-form gate over 4 seeds of the 64 problems (256 runs), paired with the FP64 "
+                    "checker's runs of seed 0 where they exist (p = 3d, 4d); one timed batch per p"}
 
 
 def leg_gmm(stream, flush):
@@ -793,7 +818,7 @@ def run_ncu_case(args):
     opts = {"dead_capacity": 8 * 250 + 500, "run_groups": 1}
     if args.ncu_cfg >= 0:
         opts["sweep_cfg"] = args.ncu_cfg
-    wls = [with_opts(w, **opts) for w in W.batch64(seed=0)]
+    wls = [with_opts(w, **opts) for w in headline_batch(0)]
     if args.ncu_cfgs:
         ids = [int(q) for q in args.ncu_cfgs.split(",")]
         def cap(d):

@@ -60,15 +60,16 @@ __device__ __forceinline__ int sw128(int r, int c4) { return r * 128 + ((c4 ^ (r
 
 // Words nz .. nz + 11 of the step's counter stream (U, slice height,
 // reserved, the first nine shrinkage proposals), as the CUDA-core kernel
-// writes them.
+// writes them; this thread draws the Philox blocks q in [q0, q1) of the
+// three or four that hold them.
 __device__ __forceinline__ void step_words_tc(uint32_t k0, uint32_t k1, int d, int p, uint32_t iter, int j, int s,
-                                              int* __restrict__ wout) {
+                                              int q0, int q1, int* __restrict__ wout) {
   const uint32_t nz = 2u * (uint32_t)((d + 1) >> 1);
   const int b0 = (int)(nz >> 2), off = (int)(nz & 3u);
   int* o = wout + ((long long)j * p + s) * kStepWords;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (q == 3 && off == 0) break;
+    if (q < q0 || q >= q1 || (q == 3 && off == 0)) continue;
     const uint4 blk = philox4x32_10(make_uint4(iter, (uint32_t)j, (uint32_t)s, (uint32_t)(b0 + q)), k0, k1);
     const uint32_t w[4] = {blk.x, blk.y, blk.z, blk.w};
 #pragma unroll
@@ -150,14 +151,27 @@ __global__ void __launch_bounds__(kDtThreads) k_dirgen_tc(Dev D, const WorkItem*
         lg[u] = (n < d && col <= n) ? *reinterpret_cast<const float4*>(Lg + (long long)n * ld + col)  // ld % 4 == 0
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      // this thread's half of row r of Z
+      // this thread's half of row r of Z: the row's Philox blocks of normals
+      // alternate between the two halves (block b to half b mod 2), and the
+      // three or four blocks of step words go to the halves so that their
+      // loads (a normals block ~8 units, a step-word block ~5) are closest
       const int q = e.y + r;
       const bool valid = q < e.z;
       const int j = valid ? q / p : 0, s = valid ? q - j * p : 0;
+      const int nbt = (d + 3) >> 2, nsw = (((d + 1) >> 1) & 1) ? 4 : 3;
+      int n1 = 0, best = 1 << 30;
+#pragma unroll 1
+      for (int c = 0; c <= nsw; ++c) {
+        const int cost = max(8 * (nbt >> 1) + 5 * c, 8 * ((nbt + 1) >> 1) + 5 * (nsw - c));
+        if (cost < best) {
+          best = cost;
+          n1 = c;
+        }
+      }
       float zz = 0.0f;
 #pragma unroll 4
       for (int bb = 0; bb < kHalfB; ++bb) {
-        const int b = h * kHalfB + bb;
+        const int b = 2 * bb + h;
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid && 4 * b < d) {
           const uint4 w = philox4x32_10(make_uint4(iter, (uint32_t)j, (uint32_t)s, (uint32_t)b), k0, k1);
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(kDtThreads) k_dirgen_tc(Dev D, const WorkItem*
         *reinterpret_cast<float4*>(Bhi + c * T::kB + sw128(n, c4)) = hi;
         *reinterpret_cast<float4*>(Blo + c * T::kB + sw128(n, c4)) = lo;
       }
-      if (valid && h == 1) step_words_tc(k0, k1, d, p, iter, j, s, D.i + o_wd);
+      if (valid) step_words_tc(k0, k1, d, p, iter, j, s, h ? 0 : n1, h ? n1 : 4, D.i + o_wd);
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       __syncthreads();

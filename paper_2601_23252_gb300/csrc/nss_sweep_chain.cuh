@@ -444,22 +444,26 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
     // Shrinkage, at most kShrinkCap proposals, then a null move.  Proposal r
     // is t_r = tl_r + u_r (tr_r - tl_r) and a rejection moves the end on
     // t_r's side to t_r, so the brackets of the proposals that follow
-    // rejections are known before any test: each round the group forms G
-    // consecutive proposals (a short scan over the shared u's) and tests
-    // them at once; the first inside the slice is the sequential result.
-    // Rounds run until every group of the warp has accepted or used the cap;
-    // a group that has accepted evaluates but counts and changes nothing.
+    // rejections are known before any test: each round lanes [0, S) of the
+    // group form S consecutive proposals (a short scan over the shared u's)
+    // and test them at once; the first inside the slice is the sequential
+    // result.  S = min(G, 4): most steps accept their first or second
+    // proposal, and the scan's length is the round's cost.  Rounds run until
+    // every group of the warp has accepted or used the cap; a group that has
+    // accepted evaluates but counts and changes nothing.
+    constexpr int S = G < 4 ? G : 4;
+    static_assert(S <= kStepWords - 3 && kShrinkCap % S == 0, "first-round proposals are drawn ahead");
     bool ok = false;
     float tacc = 0.0f, llacc = 0.0f;
     constexpr unsigned kGroupBits = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
-    for (int b0 = 0; b0 < kShrinkCap && __any_sync(kAll, !ok); b0 += G) {
+    for (int b0 = 0; b0 < kShrinkCap && __any_sync(kAll, !ok); b0 += S) {
       ++rounds;
       active += ok ? 0 : 1;
       const int idx = b0 + gl;
-      const bool mine = !ok && idx < kShrinkCap;
+      const bool mine = !ok && gl < S && idx < kShrinkCap;
       uint32_t wr;
-      if (b0 == 0 && G <= kStepWords - 3) {
-        wr = wS;  // every lane's first proposal was drawn ahead
+      if (b0 == 0) {
+        wr = wS;  // the first round's proposals were drawn ahead
       } else {
         // drawn ahead below word kStepWords, else from the counter; both
         // formed by every lane, so the warp does not split
@@ -471,7 +475,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       const float u = u24(wr);
       float lo = tl, hi = tr, t = 0.0f;
 #pragma unroll
-      for (int i = 0; i < G; ++i) {
+      for (int i = 0; i < S; ++i) {
         const float ui = __shfl_sync(kAll, u, i, G);
         const float ti = fmaf(ui, hi - lo, lo);
         if (i == gl) t = ti;
@@ -488,7 +492,7 @@ __device__ void sweep_chain(const Dev& D, const RunDesc& R, RunState* Sw, int j,
       const float tf = __shfl_sync(kAll, t, f, G);
       const float lf = __shfl_sync(kAll, ll, f, G);
       // a group still shrinking takes this round's outcome (by selects)
-      const int nvalid = min(G, kShrinkCap - b0);
+      const int nvalid = min(S, kShrinkCap - b0);
       shr += ok ? 0 : (inb ? f + 1 : nvalid);
       nanc += ok ? 0 : __popc(inb ? (nanb & ((1u << f) - 1u)) : nanb);
       tacc = (!ok && inb) ? tf : tacc;

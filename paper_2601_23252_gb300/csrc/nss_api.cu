@@ -1220,7 +1220,8 @@ nss_status nss_logreg_logits(const float* X, int n, int d, const float* U, int n
   nss_status st = NSS_OK;
   cudaError_t e = cudaMalloc(&dX, sizeof(__nv_bfloat16) * xb.size());
   if (e == cudaSuccess) e = cudaMalloc(&dP, sizeof(__nv_bfloat16) * parts.size());
-  if (e == cudaSuccess) e = cudaMalloc(&dZ, sizeof(float) * (size_t)nu * n);
+  // the device copy of Z has rows of rows_pad floats (the TMA stores want 16-byte row strides)
+  if (e == cudaSuccess) e = cudaMalloc(&dZ, sizeof(float) * (size_t)nu * rows_pad);
   if (e == cudaSuccess) e = cudaMalloc(&dErr, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(dX, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dP, parts.data(), sizeof(__nv_bfloat16) * parts.size(), cudaMemcpyHostToDevice);
@@ -1232,11 +1233,13 @@ nss_status nss_logreg_logits(const float* X, int n, int d, const float* U, int n
         !nss::make_map_bf16(&mu, dP, 3ULL * cols_pad)) st = NSS_ERR_CUDA;
   }
   if (e == cudaSuccess && st == NSS_OK)
-    e = nss::launch_logits(mx, mu, rows_pad, cols_pad, dZ, n, n, nu, dErr, nullptr, nullptr, 0);
+    e = nss::launch_logits(mx, mu, rows_pad, cols_pad, dZ, rows_pad, n, nu, dErr, nullptr, nullptr, 0);
   if (e == cudaSuccess && st == NSS_OK) e = cudaDeviceSynchronize();
   int herr = 0;
   if (e == cudaSuccess && st == NSS_OK) e = cudaMemcpy(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && st == NSS_OK) e = cudaMemcpy(Z, dZ, sizeof(float) * (size_t)nu * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st == NSS_OK)
+    e = cudaMemcpy2D(Z, sizeof(float) * (size_t)n, dZ, sizeof(float) * (size_t)rows_pad, sizeof(float) * (size_t)n, nu,
+                     cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) st = (e == cudaErrorMemoryAllocation) ? NSS_ERR_OOM : NSS_ERR_CUDA;
   if (st == NSS_OK && herr != 0) st = NSS_ERR_TIMEOUT;
   cudaFree(dX);

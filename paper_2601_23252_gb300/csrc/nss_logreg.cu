@@ -31,27 +31,35 @@ namespace nss {
 // Tensor-core contraction  out[c][r] = sum_p sum_k X[r][k] * U_p[c][k]
 //   X   : bf16 [rows_pad][128]          (tensor map mapX, box 64 x 128)
 //   U   : bf16 [3][cols_pad][128]       (tensor map mapU, box 64 x 128)
-//   out : fp32 [cols][ldo]
+//   out : fp32 [cols][ldo]              (tensor map mapO, extents n_rows x
+//                                        n_cols, box 128 rows x 32 columns)
 // Persistent, warp-specialised: block b owns the 128-column tile b mod nct
 // and the row tiles b / nct, b / nct + G / nct, ... (G blocks, a multiple of
 // nct).  Warp 4 issues the TMA loads: the block's three U parts once, then
 // each row tile's X into one of two stages; warp 5 issues the 24 MMAs of a
 // tile (K = 128 in 8 steps x 3 bf16 parts) into one of two 128-column TMEM
-// accumulators; warps 0-3 read an accumulator back (tcgen05.ld) and store
-// coalesced rows while the next tile's loads and products proceed.  Stages
-// and accumulators are handed over by mbarriers (transaction counts for the
+// accumulators; warps 0-3 read an accumulator back (tcgen05.ld) 32 columns at
+// a time, transpose them through one of two shared-memory staging buffers
+// (chain-major, the output's layout) and thread 0 writes each 128 x 32 piece
+// with one TMA store, while the next tile's loads and products proceed.
+// Scalar stores from the epilogue threads had cost ~4 us per tile (the
+// launch's bound); the TMA store writes whole lines.  Stages and
+// accumulators are handed over by mbarriers (transaction counts for the
 // loads, tcgen05.commit for the products, 128 arrivals for the drained
-// accumulator); every wait is bounded.
+// accumulator), the staging buffers by bulk-group waits and a named barrier
+// of the four epilogue warps; every mbarrier wait is bounded.
 // ---------------------------------------------------------------------------
 constexpr int kTile = 128;
 constexpr uint32_t kChunkBytes = 128u * 64u * 2u;   // 128 rows x 64 bf16
 constexpr uint32_t kMaxPolls = 1u << 22;
 constexpr int kLogitsThreads = 192;                 // warps 0-3 epilogue, 4 loads, 5 products
-constexpr int kLogitsSmem = 10 * kChunkBytes + 1024;  // U: 3 parts x 2 chunks; X: 2 stages x 2 chunks
+constexpr uint32_t kStageBytes = 32u * 128u * 4u;  // 32 columns x 128 rows fp32
+// U: 3 parts x 2 chunks; X: 2 stages x 2 chunks; two output staging buffers
+constexpr int kLogitsSmem = 10 * kChunkBytes + 2 * kStageBytes + 1024;
 
 __global__ void __launch_bounds__(kLogitsThreads, 1) k_logits(const __grid_constant__ CUtensorMap mapX,
                                                                const __grid_constant__ CUtensorMap mapU,
-                                                               int cols_pad, float* __restrict__ out, long long ldo,
+                                                               const __grid_constant__ CUtensorMap mapO, int cols_pad,
                                                                int n_rows, int n_cols, int* __restrict__ err,
                                                                const int* __restrict__ skip,
                                                                const float* __restrict__ zref) {
@@ -136,31 +144,46 @@ __global__ void __launch_bounds__(kLogitsThreads, 1) k_logits(const __grid_const
       }
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the tile)
+    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the tile);
+    // staging buffer b holds a piece as [32 columns][128 rows]
+    float* stage = reinterpret_cast<float*>(base + 10 * kChunkBytes);
+    const int lr = warp * 32 + lane;
+    int piece = 0;
     for (int i = 0; i < ntiles; ++i) {
       const int s = i & 1;
-      if (!tc::mbar_wait(&dfull[s], (i >> 1) & 1, kMaxPolls)) {
-        if (lane == 0) atomicExch(err, 3);
+      // the four warps agree on the outcome, so they leave together and no
+      // named barrier below waits for a warp that has gone
+      const bool ok = tc::named_bar_and(1, 128, tc::mbar_wait(&dfull[s], (i >> 1) & 1, kMaxPolls));
+      if (!ok) {
+        if (threadIdx.x == 0) atomicExch(err, 3);
         break;
       }
       tc::fence_after_sync();
-      const int r = (rt0 + i * per) * kTile + warp * 32 + lane;
+      const int row0 = (rt0 + i * per) * kTile;
+      const int r = row0 + lr;
       const float z0 = (zref && r < n_rows) ? zref[r] : 0.0f;
 #pragma unroll 1
-      for (int cc = 0; cc < 4; ++cc) {
+      for (int cc = 0; cc < 4; ++cc, ++piece) {
         float v[32];
         tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(s * kTile + cc * 32), v);
-        if (r < n_rows) {
+        float* buf = stage + (piece & 1) * (32 * 128);
+        // the store issued from this buffer two pieces ago has read it
+        if (threadIdx.x == 0) tc::bulk_wait_read<1>();
+        tc::named_bar_sync(1, 128);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int c = col0 + cc * 32 + q;
-            if (c < n_cols) out[static_cast<long long>(c) * ldo + r] = v[q] + z0;
-          }
+        for (int q = 0; q < 32; ++q) buf[q * 128 + lr] = v[q] + z0;
+        tc::fence_proxy_async_smem();
+        tc::named_bar_sync(1, 128);
+        if (threadIdx.x == 0) {
+          tc::tma_store_2d(&mapO, buf, row0, col0 + cc * 32);
+          tc::bulk_commit();
         }
       }
       tc::fence_before_sync();
       tc::mbar_arrive(&dempty[s]);
     }
+    // every store complete before the block ends (and its shared memory goes)
+    if (threadIdx.x == 0) tc::bulk_wait<0>();
   }
   // let any load or product still in flight land before shared and tensor
   // memory go away (after a wait that ran out; bounded)
@@ -688,18 +711,33 @@ cudaError_t setup_logits_attributes() {
   return cudaFuncSetAttribute(k_logits, cudaFuncAttributeMaxDynamicSharedMemorySize, kLogitsSmem);
 }
 
+// fp32 [n_cols][ld] output written by TMA stores of 128 rows x 32 columns
+// (rows past n_rows and columns past n_cols are not written)
+static bool make_map_out(CUtensorMap* map, float* base, long long ld, int n_rows, int n_cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (ld * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)n_rows, (cuuint64_t)n_cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t box[2] = {128, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 cudaError_t launch_logits(const CUtensorMap& mapX, const CUtensorMap& mapU, int rows_pad, int cols_pad, float* out,
                           long long ldo, int n_rows, int n_cols, int* err, const int* skip, const float* zref,
                           cudaStream_t s) {
-  if (n_cols < 1 || n_rows < 1 || n_rows > rows_pad) return cudaErrorInvalidValue;
+  if (n_cols < 1 || n_rows < 1 || n_rows > rows_pad || ldo < n_rows) return cudaErrorInvalidValue;
+  CUtensorMap mapO;
+  if (!make_map_out(&mapO, out, ldo, n_rows, n_cols)) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // one block per SM, a whole number of blocks per column tile
   const int nct = (n_cols + kTile - 1) / kTile, nrt = (n_rows + kTile - 1) / kTile;
   const int per = std::max(1, std::min(nrt, std::max(1, sms) / nct));
-  k_logits<<<nct * per, kLogitsThreads, kLogitsSmem, s>>>(mapX, mapU, cols_pad, out, ldo, n_rows, n_cols, err, skip,
-                                                          zref);
+  k_logits<<<nct * per, kLogitsThreads, kLogitsSmem, s>>>(mapX, mapU, mapO, cols_pad, n_rows, n_cols, err, skip, zref);
   return cudaGetLastError();
 }
 

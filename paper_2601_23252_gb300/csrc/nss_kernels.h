@@ -91,8 +91,6 @@ cudaError_t setup_kernel_attributes();
 cudaError_t setup_logits_attributes();
 
 bool make_map_bf16(CUtensorMap* map, void* base, unsigned long long rows);
-// out: fp32 [n_cols][ldo], written by TMA stores, so `out` 16-byte aligned and
-// ldo a multiple of 4 (else cudaErrorInvalidValue, nothing launched)
 cudaError_t launch_logits(const CUtensorMap& mapX, const CUtensorMap& mapU, int rows_pad, int cols_pad, float* out,
                           long long ldo, int n_rows, int n_cols, int* err, const int* skip, const float* zref,
                           cudaStream_t s);

@@ -725,6 +725,8 @@ static bool make_map_out(CUtensorMap* map, float* base, long long ld, int n_rows
          CUDA_SUCCESS;
 }
 
+// out: fp32 [n_cols][ldo], written by TMA stores, so `out` must be 16-byte
+// aligned and ldo a multiple of 4 (else cudaErrorInvalidValue, nothing launched)
 cudaError_t launch_logits(const CUtensorMap& mapX, const CUtensorMap& mapU, int rows_pad, int cols_pad, float* out,
                           long long ldo, int n_rows, int n_cols, int* err, const int* skip, const float* zref,
                           cudaStream_t s) {

@@ -15,8 +15,11 @@ namespace nss {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    // each product as one 32 x 32 -> 64-bit multiply (both halves at once)
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
@@ -34,8 +37,11 @@ __device__ __forceinline__ uint32_t pick(const uint4& b, uint32_t lane) {
 }
 
 // u = (2*(w >> 9) + 1) * 2^-24: an odd multiple of 2^-24 in (0, 1), exact in FP32.
+// Formed without an integer-to-float conversion: the bits (w >> 9) as the
+// mantissa of 1.m in [1, 2), minus (1 - 2^-24); the difference
+// m 2^-23 + 2^-24 is exactly representable, so the subtraction is exact.
 __device__ __forceinline__ float u24(uint32_t w) {
-  return __uint2float_rn(2u * (w >> 9) + 1u) * 0x1p-24f;
+  return __uint_as_float((w >> 9) | 0x3F800000u) - 0x1.fffffep-1f;
 }
 
 // 52-bit uniform (2*x + 1) * 2^-53 from two words, exact in FP64.

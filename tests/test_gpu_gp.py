@@ -154,3 +154,35 @@ def test_gp_full_size_run_completes(gpu_lib):
     print(f"\nGP full size (n=256, m=500, k=250, p=15): logZ {res['logZ']:.3f} +- {res['logZ_err']:.3f}, "
           f"{res['iters']} iterations, {res['evals']} evals, {res['nan_evals']} FP32 breakdowns")
     assert res["status"] == 0 and np.isfinite(res["logZ"])
+
+
+def _golden_value(name, key):
+    from conftest import golden_path
+    for line in open(golden_path(name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        if parts[0] == key:
+            return float(parts[1])
+    raise KeyError(key)
+
+
+def test_gp_full_size_evidence_matches_quadrature(gpu_lib):
+    """The full-size GP workload (n = 256 data of gp_d3 seed 0; m = 500,
+    k = 250, p = 15) over 8 sampling seeds against brute-force quadrature of
+    the checker's FP64 marginal likelihood (tests/golden/gp_d3_quadrature.txt:
+    Gauss-Legendre in the posterior's principal axes, converged to 1e-4):
+    every run within 3.5 of its own reported error, the mean within three
+    standard errors of the seeds."""
+    truth = _golden_value("gp_d3_quadrature.txt", "gp_d3_seed0_logZ")
+    wl = W.gp_d3(seed=0)
+    with native.Sampler([wl.with_(seed=s) for s in range(8)]) as smp:
+        res = smp.run()
+    lz = np.array([r["logZ"] for r in res])
+    err = np.array([r["logZ_err"] for r in res])
+    se = lz.std(ddof=1) / np.sqrt(len(lz))
+    print(f"\nGP n=256 evidence: quadrature {truth:.4f}, gpu mean {lz.mean():.4f} +- {se:.4f} "
+          f"(per-run err {err.mean():.3f}), worst |dlogZ|/err {np.max(np.abs(lz - truth) / err):.2f}")
+    assert all(r["status"] == 0 for r in res)
+    assert np.all(np.abs(lz - truth) < 3.5 * err + 0.02)
+    assert abs(lz.mean() - truth) < 3 * se + 0.05

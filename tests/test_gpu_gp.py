@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from conftest import golden_path
 from closed_forms import gp_quadrature_logZ
 from parity import (MAX_MISMATCH_FRACTION, MAX_TIE_FRACTION, compare_step, near_tie_mask, oracle_opts,
                     oracle_problem)
@@ -157,7 +158,6 @@ def test_gp_full_size_run_completes(gpu_lib):
 
 
 def _golden_value(name, key):
-    from conftest import golden_path
     for line in open(golden_path(name)):
         if line.startswith("#") or not line.strip():
             continue
@@ -173,7 +173,9 @@ def test_gp_full_size_evidence_matches_quadrature(gpu_lib):
     the checker's FP64 marginal likelihood (tests/golden/gp_d3_quadrature.txt:
     Gauss-Legendre in the posterior's principal axes, converged to 1e-4):
     every run within 3.5 of its own reported error, the mean within three
-    standard errors of the seeds."""
+    standard errors of the seeds; and paired with the FP64 checker's runs of
+    the same seeds (tests/golden/oracle_gp_d3_logz.txt): each pair within 3
+    combined errors, the mean difference within 3 standard errors."""
     truth = _golden_value("gp_d3_quadrature.txt", "gp_d3_seed0_logZ")
     wl = W.gp_d3(seed=0)
     with native.Sampler([wl.with_(seed=s) for s in range(8)]) as smp:
@@ -186,3 +188,10 @@ def test_gp_full_size_evidence_matches_quadrature(gpu_lib):
     assert all(r["status"] == 0 for r in res)
     assert np.all(np.abs(lz - truth) < 3.5 * err + 0.02)
     assert abs(lz.mean() - truth) < 3 * se + 0.05
+    ck = np.array([[float(x) for x in l.split()] for l in open(golden_path("oracle_gp_d3_logz.txt"))
+                   if not l.startswith("#") and l.strip()])
+    assert np.array_equal(ck[:, 0], np.arange(8))
+    dz = lz - ck[:, 1]
+    print(f"GPU - checker (paired seeds): {dz.mean():+.4f} +- {dz.std(ddof=1) / np.sqrt(8):.4f}")
+    assert np.all(np.abs(dz) < 3 * np.hypot(err, ck[:, 2]))
+    assert abs(dz.mean()) < 3 * dz.std(ddof=1) / np.sqrt(8)

@@ -1,15 +1,16 @@
 """Writes logreg_d100_is.txt: the evidence of the full-size logistic-regression
 workload (logreg_d100 seed 0 data: d = 100, N = 10000 bf16-exact rows, N(0, I)
 prior; the Sec. 4.2 shape) by importance sampling, independent of the nested
-sampler and of the checker:
+sampler:
 
     Z = E_q[ L(w) pi(w) / q(w) ],   q = multivariate t (nu degrees of freedom)
     centred on the posterior mode with scale matrix H^-1 (H the Hessian of the
     negative log posterior there, found by Newton's method),
 
-in FP64 with the plain definition of the Bernoulli-logit likelihood.  With
-10^4 rows the posterior is close to Gaussian, so the weights are well
-behaved; the estimate is repeated for two proposals (nu = 8 and 30, the scale
+with the weights' log L + log pi evaluated by the checker (oracle/, FP64; the
+mode and Hessian only shape the proposal and use numpy's restatement of the
+same log posterior).  With 10^4 rows the posterior is close to Gaussian, so
+the weights are well behaved; the estimate is repeated for two proposals (nu = 8 and 30, the scale
 inflated by 1.1 and 1.0) and its standard error (delta method over the
 weights) and effective sample size are written beside it.
 
@@ -17,6 +18,7 @@ weights) and effective sample size are written beside it.
 """
 import os
 import sys
+from multiprocessing import get_context
 
 import numpy as np
 from scipy import special
@@ -32,6 +34,20 @@ def log_post_many(X, y, W):
     ll = (y[:, None] * Z - np.logaddexp(0.0, Z)).sum(axis=0)
     d = W.shape[0]
     return ll - 0.5 * (W * W).sum(axis=0) - 0.5 * d * np.log(2.0 * np.pi)
+
+
+_PB = None
+
+
+def _checker_log_post(W):
+    """log L(w) + log pi(w) for the columns of W, by the checker."""
+    global _PB
+    if _PB is None:
+        import oracle as O
+        from paper_2601_23252_gb300 import workloads as Wk
+        wl = Wk.logreg_d100(seed=0)
+        _PB = O.Problem((wl.prior, wl.a, wl.b), wl.lik, **wl.oracle_kwargs())
+    return np.array([_PB.loglik(W[:, i]) + _PB.log_prior(W[:, i]) for i in range(W.shape[1])])
 
 
 def mode_and_hessian(X, y):
@@ -52,13 +68,13 @@ def mode_and_hessian(X, y):
     return w, H
 
 
-def importance(X, y, w0, H, nu, infl, n, seed, chunk=2000):
+def importance(pool, w0, H, nu, infl, n, seed, chunk=2000):
     d = len(w0)
     cov = infl * np.linalg.inv(H)
     L = np.linalg.cholesky(cov)
     logdet = 2.0 * np.sum(np.log(np.diag(L)))
     g = np.random.default_rng(seed)
-    lw = []
+    blocks, logqs = [], []
     for s in range(0, n, chunk):
         m = min(chunk, n - s)
         u = g.standard_normal((d, m))
@@ -69,8 +85,10 @@ def importance(X, y, w0, H, nu, infl, n, seed, chunk=2000):
         q2 = np.sum(np.linalg.solve(L, dev) ** 2, axis=0)
         logq = (special.gammaln((nu + d) / 2) - special.gammaln(nu / 2) - 0.5 * d * np.log(nu * np.pi)
                 - 0.5 * logdet - 0.5 * (nu + d) * np.log1p(q2 / nu))
-        lw.append(log_post_many(X, y, W) - logq)
-    lw = np.concatenate(lw)
+        blocks.append(W)
+        logqs.append(logq)
+    lp = pool.map(_checker_log_post, blocks)
+    lw = np.concatenate([a - b for a, b in zip(lp, logqs)])
     mx = lw.max()
     wt = np.exp(lw - mx)
     mean = wt.mean()
@@ -90,8 +108,9 @@ def main():
     d = X.shape[1]
     laplace = lp0 + 0.5 * d * np.log(2.0 * np.pi) - 0.5 * np.linalg.slogdet(H)[1]
     rows = []
-    for nu, infl, seed in ((8.0, 1.1, 1), (30.0, 1.0, 2)):
-        rows.append((nu, infl, 200000) + importance(X, y, w0, H, nu, infl, 200000, seed))
+    with get_context("spawn").Pool(os.cpu_count()) as pool:
+        for nu, infl, seed in ((8.0, 1.1, 1), (30.0, 1.0, 2)):
+            rows.append((nu, infl, 200000) + importance(pool, w0, H, nu, infl, 200000, seed))
     z = np.array([r[3] for r in rows])
     se = np.array([r[4] for r in rows])
     best = float(np.sum(z / se**2) / np.sum(1 / se**2))
@@ -99,7 +118,8 @@ def main():
     path = os.path.join(HERE, "logreg_d100_is.txt")
     with open(path, "w") as f:
         f.write("# evidence of the logreg_d100 workload, seed 0 data (d = 100, N = 10000 bf16-exact rows, N(0, I) prior),\n")
-        f.write("# by importance sampling (multivariate t proposals at the posterior mode, scale H^-1); FP64;\n")
+        f.write("# by importance sampling (multivariate t proposals at the posterior mode, scale H^-1), weights from\n")
+        f.write("# the FP64 checker's log likelihood and log prior;\n")
         f.write("# written by tests/golden/make_logreg_is.py\n")
         f.write(f"# mode: log posterior {lp0:.6f}; Laplace logZ {laplace:.6f}\n")
         for nu, infl, n, lz, s, ess in rows:

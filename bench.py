@@ -670,7 +670,7 @@ def p_sweep(wls, chosen, stream, flush, mults, base, base_value, base_c):
     ok = [r for r in rows if r["closed_form_pass"]]
     return {"rows": rows, "gated_operating_point": ok[0] if ok else None,
             "note": "closed-form gate over 4 seeds of the 64 problems (256 runs), paired with the FP64 "
-                    "checker's runs of seed 0 where they exist (p = 3d, 4d); one timed batch per p"}
+                    "checker's runs of seed 0 where they exist (p = 3d, 4d, 6d); one timed batch per p"}
 
 
 def leg_gmm(stream, flush):

@@ -56,3 +56,43 @@ def test_checker_pairing_is_part_of_pass(wls):
     assert bench.logz_gate(wls, res, checker=agree)["pass"]
     g = bench.logz_gate(wls, res, checker=off)
     assert g["checker_runs_within_3err"] and not g["checker_mean_within_3se"] and not g["pass"]
+
+
+class _FakeSampler:
+    """Stands in for the CUDA sampler: every run returns its closed form."""
+
+    def __init__(self, ws, stream=None):
+        self.ws = ws
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+    def autotune(self, iters=3):
+        return [{"id": 3, "lanes_per_chain": 8, "dims_per_lane": 4} for _ in self.ws]
+
+    def run(self):
+        return [{"logZ": bench.truth_of(w), "logZ_err": 0.3, "n_dead": 1000, "evals": 10**6} for w in self.ws]
+
+
+def test_gmm_leg_pairs_each_p_with_the_checker_where_it_exists(monkeypatch):
+    """The bench's gmm_d32 leg, driven by the stand-in sampler: every p row is
+    gated against the closed forms, and the rows whose checker file exists
+    (p = 3d always) carry the paired gate."""
+    import os
+    import types
+    from conftest import golden_path
+    from paper_2601_23252_gb300 import native
+    monkeypatch.setattr(native, "Sampler", _FakeSampler)
+    monkeypatch.setattr(bench, "timed_run", lambda s, stream, flush, fill=0.0: (10.0, s.run()))
+    out = bench.leg_gmm(types.SimpleNamespace(cuda_stream=0), None)
+    assert [r["p"] for r in out["rows"]] == [96, 192, 320, 640]
+    assert out["gated_p"] == 96 and all(r["closed_form_pass"] for r in out["rows"])
+    for r in out["rows"]:
+        c = r["p"] // 32
+        has = os.path.exists(golden_path("oracle_gmm_d32_logz.txt" if c == 3 else f"oracle_gmm_d32_p{c}d_logz.txt"))
+        assert ("gate" in r) == has
+        if has:
+            assert "mean_dlogZ_vs_checker" in r["gate"]

@@ -10,9 +10,10 @@
 // step of the run's direction store); row r of a tile belongs to threads r
 // and r + 128, each of which draws half of the row's Philox blocks:
 //   - the two threads draw the row's normals (Box-Muller pairs of the row's
-//     counter stream, as in the CUDA-core kernel; the upper thread also the
-//     step's first scalar words) and write them to shared memory as two TF32
-//     parts hi + lo in the K-major 128-byte swizzled layout;
+//     counter stream, as in the CUDA-core kernel; the row's blocks alternate
+//     between them, and the step's first scalar words are split so that the
+//     two threads' loads are closest) and write them to shared memory as two
+//     TF32 parts hi + lo in the K-major 128-byte swizzled layout;
 //   - the block stages L (rows n < N, zero above the diagonal and past d) in
 //     the same layout, also split hi + lo;
 //   - one thread issues tcgen05.mma kind::tf32 (M = 128, N = 32 KC, K = 8)
